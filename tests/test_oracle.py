@@ -1,0 +1,229 @@
+"""Pins for the CPU oracle against facts that do not come from the oracle.
+
+Each test checks the oracle against something other than its own formula:
+a textbook carry-less multiplication, field axioms, a hand-worked example,
+unit vectors, linearity, brute-force MDS recovery and the XOR counts the
+paper prints for RS(10,4) (Sec. 7.5).
+"""
+import json
+import os
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_02692_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def clmul_mod(a: int, b: int, poly: int = 0x11d) -> int:
+    """Shift-and-add polynomial product reduced modulo x^8+x^4+x^3+x^2+1."""
+    r = 0
+    for i in range(8):
+        if (b >> i) & 1:
+            r ^= a << i
+    for d in range(14, 7, -1):
+        if (r >> d) & 1:
+            r ^= poly << (d - 8)
+    return r
+
+
+@pytest.fixture(scope="module")
+def mul_table():
+    return np.array([[oracle.gf_mul(a, b) for b in range(256)]
+                     for a in range(256)], dtype=np.uint8)
+
+
+def test_mul_matches_carryless_product(mul_table):
+    ref = np.array([[clmul_mod(a, b) for b in range(256)] for a in range(256)],
+                   dtype=np.uint8)
+    assert np.array_equal(mul_table, ref)
+
+
+def test_field_axioms(mul_table):
+    T = mul_table.astype(np.int64)
+    a = np.arange(256)
+    assert np.array_equal(T, T.T)                       # commutative
+    assert np.array_equal(T[1], a)                      # identity
+    assert np.all(T[0] == 0)
+    A, Bm, C = np.meshgrid(a, a, a, indexing="ij")
+    assert np.array_equal(T[T[A, Bm], C], T[A, T[Bm, C]])       # associative
+    assert np.array_equal(T[A, Bm ^ C], T[A, Bm] ^ T[A, C])     # distributive
+    inv = np.array([oracle.gf_inv(int(x)) for x in range(256)])
+    assert np.all(T[a[1:], inv[1:]] == 1)                        # inverses
+
+
+def test_spot_values_and_primitive_element():
+    assert oracle.gf_mul(2, 0x80) == 0x1D
+    assert oracle.gf_inv(2) == 0x8E
+    assert oracle.gf_inv(3) == 0xF4
+    seq = [oracle.gf_pow2(e) for e in range(255)]
+    assert len(set(seq)) == 255 and 0 not in seq   # 2 generates GF(2^8)*
+    assert oracle.gf_pow2(255) == 1
+
+
+def test_element_slicing_layout():
+    # bit t of element e = bit (e mod 8) of byte floor(e/8) of strip t
+    B = 64
+    blk = np.zeros(B, np.uint8)
+    oracle.set_elem(blk, 13, 0b10000101)
+    S = B // 8
+    expect = np.zeros(B, np.uint8)
+    for t in (0, 2, 7):
+        expect[t * S + 13 // 8] = 1 << (13 % 8)
+    assert np.array_equal(blk, expect)
+    assert oracle.get_elem(blk, 13) == 0b10000101
+
+
+def _hand_rows():
+    rows = []
+    with open(os.path.join(GOLD, "rs21_hand.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(x, 16) for x in line.split()])
+    return rows
+
+
+def test_rs21_hand_worked():
+    P = oracle.cauchy(2, 1)
+    assert P.tolist() == [[0x8E, 0xF4]]
+    B = 8 * 4
+    rows = _hand_rows()
+    d0 = np.zeros(B, np.uint8)
+    d1 = np.zeros(B, np.uint8)
+    for e, (x0, x1, _) in enumerate(rows):
+        oracle.set_elem(d0, e, x0)
+        oracle.set_elem(d1, e, x1)
+    (par,) = oracle.encode(P, [d0, d1])
+    for e, (_, _, p) in enumerate(rows):
+        assert oracle.get_elem(par, e) == p
+    for e in range(len(rows), B):
+        assert oracle.get_elem(par, e) == 0
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (10, 4), (6, 3)])
+def test_unit_vectors_reproduce_columns(k, m):
+    P = oracle.cauchy(k, m)
+    B = 64
+    for j in range(k):
+        for e in (0, 9, 63):
+            data = [np.zeros(B, np.uint8) for _ in range(k)]
+            oracle.set_elem(data[j], e, 1)
+            par = oracle.encode(P, data)
+            for i in range(m):
+                vals = [oracle.get_elem(par[i], x) for x in range(B)]
+                assert vals[e] == P[i, j]
+                assert sum(1 for x in vals if x) == (1 if P[i, j] else 0)
+
+
+def test_linearity_and_zero():
+    k, m, B = 6, 3, 128
+    P = oracle.cauchy(k, m)
+    a = [synth.block_bytes(9, 0, j, B) for j in range(k)]
+    b = [synth.block_bytes(9, 1, j, B) for j in range(k)]
+    ea, eb = oracle.encode(P, a), oracle.encode(P, b)
+    eab = oracle.encode(P, [x ^ y for x, y in zip(a, b)])
+    for i in range(m):
+        assert np.array_equal(eab[i], ea[i] ^ eb[i])
+    ez = oracle.encode(P, [np.zeros(B, np.uint8)] * k)
+    assert all(not z.any() for z in ez)
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (6, 3)])
+def test_mds_bruteforce_recovery(k, m):
+    P = oracle.cauchy(k, m)
+    B = 64
+    data = [synth.block_bytes(7, k, j, B) for j in range(k)]
+    blocks = data + oracle.encode(P, data)
+    n_pat = 0
+    for ne in range(1, m + 1):
+        for er in itertools.combinations(range(k + m), ne):
+            avail = [None if i in er else blocks[i] for i in range(k + m)]
+            rec = oracle.decode(P, list(er), avail)
+            for i, e in enumerate(er):
+                assert np.array_equal(rec[i], blocks[e]), (er, e)
+            n_pat += 1
+    assert n_pat == {(4, 2): 21, (6, 3): 129}[(k, m)]
+
+
+def test_invert_against_carryless(mul_table):
+    rng = np.random.default_rng(1)
+    T = mul_table
+    for n in (1, 3, 10):
+        while True:
+            M = rng.integers(0, 256, size=(n, n), dtype=np.uint8)
+            Minv = oracle.invert(M)
+            if Minv is not None:
+                break
+        prod = np.zeros((n, n), np.uint8)
+        for i in range(n):
+            for j in range(n):
+                acc = 0
+                for x in range(n):
+                    acc ^= clmul_mod(int(M[i, x]), int(Minv[x, j]))
+                prod[i, j] = acc
+        assert np.array_equal(prod, np.eye(n, dtype=np.uint8))
+    assert oracle.invert(np.zeros((2, 2), np.uint8)) is None
+
+
+def test_bitmatrix_of_every_constant():
+    # x~ . B(y) == B(x*y) for all 256 x 256 pairs (Sec. 1, property (ii))
+    A = np.arange(256, dtype=np.uint8).reshape(256, 1)
+    bits = oracle.bitmatrix(A)                    # (8*256) x 8
+    ys = np.arange(256)
+    ybits = ((ys[None, :] >> np.arange(8)[:, None]) & 1)   # 8 x 256
+    for x in range(256):
+        M = bits[8 * x:8 * x + 8].astype(np.int64)
+        prod_bits = (M @ ybits) & 1
+        vals = (prod_bits << np.arange(8)[:, None]).sum(axis=0)
+        assert all(vals[y] == clmul_mod(x, y) for y in range(256)), x
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (10, 4)])
+def test_bitmatrix_xor_equals_table_product(k, m):
+    P = oracle.cauchy(k, m)
+    B = 256
+    data = [synth.block_bytes(8, 0, j, B) for j in range(k)]
+    ref = oracle.encode(P, data)
+    got = oracle.apply_bitmatrix(oracle.bitmatrix(P), data)
+    for i in range(m):
+        assert np.array_equal(ref[i], got[i])
+
+
+def test_paper_xor_counts_rs10_4():
+    gold = json.load(open(os.path.join(GOLD, "paper_counts.json")))
+    P = oracle.power(10, 4)
+    bits = oracle.bitmatrix(P)
+    assert int(bits.sum()) - bits.shape[0] == gold["P_enc"]["xors"]
+    er = gold["P_dec"]["erased"]
+    R = oracle.decode_matrix(P, er)
+    bits = oracle.bitmatrix(R)
+    assert int(bits.sum()) - bits.shape[0] == gold["P_dec"]["xors"]
+
+
+def test_decode_matrix_recovers_erased_data():
+    P = oracle.power(10, 4)
+    B = 64
+    data = [synth.block_bytes(6, 0, j, B) for j in range(10)]
+    blocks = data + oracle.encode(P, data)
+    er = [2, 4, 5, 6]
+    R = oracle.decode_matrix(P, er)
+    surv = [i for i in range(14) if i not in er][:10]
+    rec = oracle.apply(R, [blocks[i] for i in surv])
+    for i, e in enumerate(er):
+        assert np.array_equal(rec[i], blocks[e])
+
+
+def test_splitmix64_published_vector():
+    vals = [int(line, 16) for line in
+            open(os.path.join(GOLD, "splitmix64_seed0.txt"))
+            if line.strip() and not line.startswith("#")]
+    got = [int(x) for x in synth.stream_words(0, 0, 3)]
+    assert got == vals
+    # counter form: random access equals sequential order
+    w = synth.stream_words(12345, 0, 64)
+    assert np.array_equal(synth.stream_words(12345, 17, 5), w[17:22])
+    b = synth.stream_bytes(99, 0, 100)
+    assert np.array_equal(synth.stream_bytes(99, 13, 50), b[13:63])
