@@ -1,0 +1,218 @@
+/*
+ * xorec: XOR-based Reed-Solomon erasure coding on one GB300 GPU.
+ *
+ * C ABI of libxorec.so.  Plain pointers and sizes only.
+ *
+ * Method (paper: Uezato, "Accelerating XOR-based Erasure Coding using
+ * Program Optimization Techniques", SC'21):
+ *   - RS(k,m) encodes k data blocks into m parity blocks with the systematic
+ *     generator [I ; P] over GF(2^8), polynomial 0x11d (Sec. 1, Sec. 7.1).
+ *   - The m x k parity matrix is expanded into an (8m) x (8k) bitmatrix over
+ *     GF(2) (Sec. 1, properties (i)-(ii)); every output strip is the XOR of
+ *     the input strips its bitmatrix row selects.
+ *   - The bitmatrix becomes a straight-line program (Sec. 4.1) that is
+ *     compressed by XorRePair (Sec. 4.4), fused (Sec. 5.2) and scheduled by
+ *     a pebble game (Sec. 6.6) before it runs on the GPU.
+ *
+ * Data layout.  A block of B bytes (B % 128 == 0) is 8 strips of B/8 bytes;
+ * strip t is bytes [t*B/8, (t+1)*B/8).  Bit t of field element e is bit
+ * (e % 8) of byte e/8 of strip t (Sec. 6.1 "8 x n arrays of N/(8n) bytes").
+ * Block pointers must be 16-byte aligned.
+ *
+ * Ownership.  The caller owns every data buffer; a plan owns its host
+ * programs and device state and must outlive the GPU work queued with it.
+ * Calls that take a stream are asynchronous with respect to the host;
+ * argument errors are returned synchronously.  Errors found by kernels
+ * (a bounded wait that timed out) are reported by ec_device_status().
+ * ec_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef XOREC_H
+#define XOREC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EC_OK = 0,
+  EC_EINVAL = -1,      /* bad argument (sizes, alignment, ids)                */
+  EC_ENOMEM = -2,      /* host or device allocation failed                    */
+  EC_ESINGULAR = -3,   /* survivor submatrix not invertible (non-MDS matrix)  */
+  EC_ETOOMANY = -4,    /* more erasures than parity blocks                    */
+  EC_ECUDA = -5,       /* CUDA runtime / driver error                         */
+  EC_ETIMEOUT = -6,    /* a device-side bounded wait gave up                  */
+  EC_EBUSY = -7,       /* admission refused (serving)                         */
+  EC_ENOTSUP = -8      /* feature unavailable (e.g. no run-time compiler)     */
+} ec_status;
+
+typedef struct ec_plan ec_plan;
+
+/* Coding-matrix choice for ec_plan_create_ex. */
+enum {
+  EC_MATRIX_CAUCHY = 0, /* P[i][j] = 1 / ((k+i) XOR j): MDS for k+m <= 256   */
+  EC_MATRIX_POWER = 1,  /* P[r][j] = 2^(r*j): the matrix whose XOR counts the
+                           paper prints for RS(10,4) (Sec. 7.1, Sec. 7.5);
+                           not MDS in general                                 */
+  EC_MATRIX_USER = 2    /* caller-supplied m x k parity rows, used as given   */
+};
+
+/* Optimiser level (which passes run before fusion and scheduling). */
+enum {
+  EC_OPT_RAW = 0,       /* one fused statement per bitmatrix row              */
+  EC_OPT_REPAIR = 1,    /* RePair (Sec. 4.3)                                  */
+  EC_OPT_XORREPAIR = 2  /* XorRePair (Sec. 4.4), the default                  */
+};
+
+/* Pebble-game scheduler (Sec. 6.6). */
+enum { EC_SCHED_DFS = 0, EC_SCHED_GREEDY = 1 };
+
+/* Executor tier. */
+enum {
+  EC_EXEC_AUTO = 0,     /* compiled straight-line kernel when available       */
+  EC_EXEC_INTERP = 1,   /* instruction-stream interpreter                     */
+  EC_EXEC_COMPILED = 2  /* compiled straight-line kernel (NVRTC)              */
+};
+
+typedef struct {
+  int opt_level;        /* EC_OPT_*                                           */
+  int sched;            /* EC_SCHED_*                                         */
+  int greedy_cap;       /* cache capacity of the greedy scheduler             */
+  int executor;         /* EC_EXEC_*                                          */
+} ec_plan_opts;
+
+/* Create a plan for RS(k,m).  matrix: m*k row-major parity rows, or NULL for
+ * the Cauchy default.  1 <= k, 1 <= m, k + m <= 256.  Builds and optimises
+ * the encoding program on the host (Sec. 4-6).  *out receives the plan. */
+ec_status ec_plan_create(int k, int m, const uint8_t *matrix, ec_plan **out);
+
+/* Same with an explicit matrix kind (EC_MATRIX_*; matrix is read only for
+ * EC_MATRIX_USER) and options (NULL = defaults). */
+ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t *matrix,
+                            const ec_plan_opts *opts, ec_plan **out);
+
+/* Free the plan, its programs and its device state.  NULL is ignored. */
+void ec_plan_destroy(ec_plan *plan);
+
+/* Copy the m*k parity rows of the plan into out (host memory). */
+ec_status ec_plan_matrix(const ec_plan *plan, uint8_t *out);
+
+/* Statistics of one program of the plan. */
+typedef struct {
+  long xors, mem;       /* #XOR (sum of arity-1) and #_M (Sec. 4.1, 5.1)      */
+  int nvar, stmts;      /* variables and statements                           */
+} ec_slp_stats;
+
+typedef struct {
+  int n_in, n_out;      /* input / output strips                              */
+  int slots;            /* pebbles held in shared memory by the interpreter   */
+  int stmts;            /* statements of the lowered program                  */
+  int code_words;       /* 16-bit words of the instruction stream             */
+  int sched_nvar;       /* pebbles of the paper's game (goals hold)           */
+  ec_slp_stats raw;     /* unoptimised binary-chain program (Sec. 7.5)        */
+  ec_slp_stats compressed;  /* after (Xor)RePair                              */
+  ec_slp_stats fused;   /* after XOR fusion                                   */
+  int compiled;         /* 1 if a compiled straight-line kernel exists        */
+  int regs;             /* registers per thread of the compiled kernel        */
+} ec_program_info;
+
+/* Program of the encoder (erasures == NULL) or of the decoder for the given
+ * erasure set (built and cached on first use). */
+ec_status ec_plan_info(ec_plan *plan, const int *erasures, int n_erasures,
+                       ec_program_info *out);
+
+/* Copy the interpreter instruction stream of the encoder (erasures == NULL)
+ * or of a decoder into buf (len 16-bit words); *need receives the length.
+ * Stream format, statement by statement: n_args; n_outs | has_slot << 15;
+ * [slot]; output strip ids; operand ids (< n_in: input strip, else slot +
+ * n_in).  For inspection and host-side checks. */
+ec_status ec_plan_program(ec_plan *plan, const int *erasures, int n_erasures, uint16_t *buf,
+                          size_t len, size_t *need);
+
+/* Encode one stripe: parity_i = sum_j P[i][j] data_j (Sec. 1).
+ * data[k], parity[m]: device pointers to blocks of block_bytes bytes
+ * (block_bytes % 128 == 0, 16-byte aligned).  Enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream). */
+ec_status ec_encode(ec_plan *plan, const uint8_t *const *data, uint8_t *const *parity,
+                    size_t block_bytes, void *stream);
+
+/* Encode n_stripes stripes in one launch.  Block j of stripe s is at
+ * data + s*data_stripe_stride + j*data_block_stride; parity block i of stripe
+ * s at parity + s*par_stripe_stride + i*par_block_stride (bytes, device
+ * memory, multiples of 16). */
+ec_status ec_encode_strided(ec_plan *plan, const uint8_t *data, size_t data_stripe_stride,
+                            size_t data_block_stride, uint8_t *parity,
+                            size_t par_stripe_stride, size_t par_block_stride,
+                            int n_stripes, size_t block_bytes, void *stream);
+
+/* Decode one stripe (Sec. 1): recover the blocks listed in erasures (ids in
+ * [0, k+m), unique, any order, 1 <= n_erasures <= m) from the first k
+ * surviving blocks in ascending id order.  blocks[k+m] is indexed by block
+ * id (data blocks 0..k-1, parity blocks k..k+m-1); erased entries are
+ * ignored and may be NULL.  out[i] receives block erasures[i]; erased parity
+ * is re-encoded from the recovered data in the same program.  The decode
+ * matrix G[E] * G[S]^{-1} is inverted on the host and its program built and
+ * cached on first use of each erasure set. */
+ec_status ec_decode(ec_plan *plan, const int *erasures, int n_erasures,
+                    const uint8_t *const *blocks, uint8_t *const *out,
+                    size_t block_bytes, void *stream);
+
+/* Build (in parallel host threads) and cache the decode programs of
+ * n_sets erasure sets.  sets holds the ids of all sets back to back;
+ * counts[i] is the size of set i. */
+ec_status ec_decode_prepare(ec_plan *plan, const int *sets, const int *counts, int n_sets,
+                            int n_threads);
+
+/* Select the executor tier (EC_EXEC_*).  EC_EXEC_COMPILED fails with
+ * EC_ENOTSUP when no run-time compiler is present. */
+ec_status ec_plan_set_executor(ec_plan *plan, int executor);
+
+/* Device status word written by kernels whose bounded waits gave up:
+ * *status = 0 (ok) or EC_ETIMEOUT.  reset != 0 clears it.  Synchronises the
+ * current device. */
+ec_status ec_device_status(int *status, int reset);
+
+/* Thread-local message of the last failure ("" if none). */
+const char *ec_last_error(void);
+
+/* Library version string. */
+const char *ec_version(void);
+
+/* ---------------------------------------------------------------- inputs
+ * Fill n bytes at device pointer dst with bytes [offset, offset+n) of the
+ * SplitMix64 stream `seed` (Steele, Lea and Flood 2014, counter form:
+ * byte b is byte b%8 of mix(seed + (b/8 + 1) * 0x9E3779B97F4A7C15)).
+ * Synthetic input generation only; not part of the coding method. */
+ec_status ec_synth_fill(uint8_t *dst, size_t n, uint64_t seed, uint64_t offset, void *stream);
+
+/* --------------------------------------------------- straight-line programs
+ * Host-only access to the optimiser, for inspection and tests. */
+typedef struct ec_slp ec_slp;
+
+/* Parse the text form:  "const a b c" / "v = a b" / "ret v ..." lines. */
+ec_status ec_slp_parse(const char *text, ec_slp **out);
+/* Program of the bitmatrix of a rows x cols GF(2^8) matrix.  form 0: one
+ * statement per row; form 1: binary left-to-right chains.  Rows are emitted
+ * block by block, bit 7 down to bit 0 within a block. */
+ec_status ec_slp_from_matrix(int rows, int cols, const uint8_t *A, int form, ec_slp **out);
+ec_status ec_slp_repair(const ec_slp *in, int xor_cancel, ec_slp **out);
+ec_status ec_slp_fuse(const ec_slp *in, int cancel_pairs, ec_slp **out);
+/* kind: EC_SCHED_DFS or EC_SCHED_GREEDY (cap = cache capacity).  The result
+ * is the pebble program of the paper's game (goals keep their pebbles). */
+ec_status ec_slp_schedule(const ec_slp *in, int kind, int cap, ec_slp **out);
+ec_status ec_slp_stats_get(const ec_slp *p, ec_slp_stats *out);
+/* IOcost(P, cap) and CCap(P) of the abstract LRU cache (Sec. 6.2). */
+long ec_slp_iocost(const ec_slp *p, int cap);
+int ec_slp_ccap(const ec_slp *p);
+/* *eq = 1 when both programs return the same sets of constants (Sec. 4.1). */
+ec_status ec_slp_equivalent(const ec_slp *a, const ec_slp *b, int *eq);
+/* Text form into buf (NUL-terminated); *need receives the length + 1. */
+ec_status ec_slp_to_text(const ec_slp *p, char *buf, size_t len, size_t *need);
+void ec_slp_destroy(ec_slp *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XOREC_H */

@@ -1,0 +1,243 @@
+"""XOR-based Reed-Solomon erasure coding on one GB300 (sm_103a).
+
+Thin Python binding of the C ABI in include/xorec.h: every function here has
+the name of the C entry point it calls and only converts arguments.  Device
+buffers are passed as integer device pointers (e.g. ``tensor.data_ptr()``)
+and streams as integer ``cudaStream_t`` handles
+(``torch.cuda.current_stream().cuda_stream``); PyTorch only supplies memory
+and streams.  All computation runs in libxorec.so; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+
+EC_OK = _abi.EC_OK
+EC_EINVAL = _abi.EC_EINVAL
+EC_ENOMEM = _abi.EC_ENOMEM
+EC_ESINGULAR = _abi.EC_ESINGULAR
+EC_ETOOMANY = _abi.EC_ETOOMANY
+EC_ECUDA = _abi.EC_ECUDA
+EC_ETIMEOUT = _abi.EC_ETIMEOUT
+EC_EBUSY = _abi.EC_EBUSY
+EC_ENOTSUP = _abi.EC_ENOTSUP
+EC_MATRIX_CAUCHY = _abi.EC_MATRIX_CAUCHY
+EC_MATRIX_POWER = _abi.EC_MATRIX_POWER
+EC_MATRIX_USER = _abi.EC_MATRIX_USER
+EC_OPT_RAW = _abi.EC_OPT_RAW
+EC_OPT_REPAIR = _abi.EC_OPT_REPAIR
+EC_OPT_XORREPAIR = _abi.EC_OPT_XORREPAIR
+EC_SCHED_DFS = _abi.EC_SCHED_DFS
+EC_SCHED_GREEDY = _abi.EC_SCHED_GREEDY
+EC_EXEC_AUTO = _abi.EC_EXEC_AUTO
+EC_EXEC_INTERP = _abi.EC_EXEC_INTERP
+EC_EXEC_COMPILED = _abi.EC_EXEC_COMPILED
+
+
+class XorecError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"xorec status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    return _abi.load()
+
+
+def ec_last_error() -> str:
+    return (lib().ec_last_error() or b"").decode()
+
+
+def ec_version() -> str:
+    return lib().ec_version().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise XorecError(rc, ec_last_error())
+
+
+def _u8(arr):
+    if arr is None:
+        return None
+    a = np.ascontiguousarray(arr, dtype=np.uint8)
+    return a, a.ctypes.data_as(_abi.u8p)
+
+
+def _vp_array(ptrs):
+    arr = (ctypes.c_void_p * max(1, len(ptrs)))()
+    for i, p in enumerate(ptrs):
+        arr[i] = None if p is None else int(p)
+    return arr
+
+
+def _int_array(vals):
+    return (ctypes.c_int * max(1, len(vals)))(*[int(v) for v in vals])
+
+
+# ------------------------------------------------------------------- plans
+
+def ec_plan_create(k: int, m: int, matrix=None) -> int:
+    h = ctypes.c_void_p()
+    keep = _u8(matrix)
+    _check(lib().ec_plan_create(k, m, keep[1] if keep else None, ctypes.byref(h)))
+    return h.value
+
+
+def ec_plan_create_ex(k: int, m: int, matrix_kind: int = EC_MATRIX_CAUCHY, matrix=None,
+                      opt_level: int = EC_OPT_XORREPAIR, sched: int = EC_SCHED_DFS,
+                      greedy_cap: int = 128, executor: int = EC_EXEC_AUTO) -> int:
+    h = ctypes.c_void_p()
+    keep = _u8(matrix)
+    opts = _abi.PlanOpts(opt_level, sched, greedy_cap, executor)
+    _check(lib().ec_plan_create_ex(k, m, matrix_kind, keep[1] if keep else None,
+                                   ctypes.byref(opts), ctypes.byref(h)))
+    return h.value
+
+
+def ec_plan_destroy(plan: int) -> None:
+    lib().ec_plan_destroy(plan)
+
+
+def ec_plan_matrix(plan: int, k: int, m: int) -> np.ndarray:
+    out = np.zeros((m, k), np.uint8)
+    _check(lib().ec_plan_matrix(plan, out.ctypes.data_as(_abi.u8p)))
+    return out
+
+
+def _stats(s) -> dict:
+    return {"xors": s.xors, "mem": s.mem, "nvar": s.nvar, "stmts": s.stmts}
+
+
+def ec_plan_info(plan: int, erasures=None) -> dict:
+    info = _abi.ProgramInfo()
+    if erasures is None:
+        _check(lib().ec_plan_info(plan, None, 0, ctypes.byref(info)))
+    else:
+        _check(lib().ec_plan_info(plan, _int_array(erasures), len(erasures), ctypes.byref(info)))
+    return {"n_in": info.n_in, "n_out": info.n_out, "slots": info.slots, "stmts": info.stmts,
+            "code_words": info.code_words, "sched_nvar": info.sched_nvar,
+            "raw": _stats(info.raw), "compressed": _stats(info.compressed),
+            "fused": _stats(info.fused), "compiled": bool(info.compiled), "regs": info.regs}
+
+
+def ec_plan_program(plan: int, erasures=None) -> np.ndarray:
+    need = ctypes.c_size_t()
+    er = _int_array(erasures) if erasures is not None else None
+    ne = len(erasures) if erasures is not None else 0
+    _check(lib().ec_plan_program(plan, er, ne, None, 0, ctypes.byref(need)))
+    out = np.zeros(need.value, np.uint16)
+    _check(lib().ec_plan_program(plan, er, ne,
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)),
+                                 need.value, None))
+    return out
+
+
+def ec_plan_set_executor(plan: int, executor: int) -> None:
+    _check(lib().ec_plan_set_executor(plan, executor))
+
+
+# -------------------------------------------------------------- coding
+
+def ec_encode(plan: int, data_ptrs, parity_ptrs, block_bytes: int, stream: int = 0) -> None:
+    _check(lib().ec_encode(plan, _vp_array(data_ptrs), _vp_array(parity_ptrs), block_bytes,
+                           stream or None))
+
+
+def ec_encode_strided(plan: int, data_ptr: int, data_stripe_stride: int, data_block_stride: int,
+                      parity_ptr: int, par_stripe_stride: int, par_block_stride: int,
+                      n_stripes: int, block_bytes: int, stream: int = 0) -> None:
+    _check(lib().ec_encode_strided(plan, data_ptr, data_stripe_stride, data_block_stride,
+                                   parity_ptr, par_stripe_stride, par_block_stride, n_stripes,
+                                   block_bytes, stream or None))
+
+
+def ec_decode(plan: int, erasures, block_ptrs, out_ptrs, block_bytes: int,
+              stream: int = 0) -> None:
+    _check(lib().ec_decode(plan, _int_array(erasures), len(erasures), _vp_array(block_ptrs),
+                           _vp_array(out_ptrs), block_bytes, stream or None))
+
+
+def ec_decode_prepare(plan: int, sets, n_threads: int = 0) -> None:
+    flat = [int(x) for s in sets for x in s]
+    counts = [len(s) for s in sets]
+    _check(lib().ec_decode_prepare(plan, _int_array(flat), _int_array(counts), len(sets),
+                                   n_threads))
+
+
+def ec_device_status(reset: bool = False) -> int:
+    st = ctypes.c_int()
+    _check(lib().ec_device_status(ctypes.byref(st), 1 if reset else 0))
+    return st.value
+
+
+def ec_synth_fill(ptr: int, n: int, seed: int, offset: int = 0, stream: int = 0) -> None:
+    _check(lib().ec_synth_fill(ptr, n, seed, offset, stream or None))
+
+
+# ------------------------------------------------------ straight-line programs
+
+def ec_slp_parse(text: str) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ec_slp_parse(text.encode(), ctypes.byref(h)))
+    return h.value
+
+
+def ec_slp_from_matrix(A, form: int = 1) -> int:
+    a, p = _u8(A)
+    h = ctypes.c_void_p()
+    _check(lib().ec_slp_from_matrix(a.shape[0], a.shape[1], p, form, ctypes.byref(h)))
+    return h.value
+
+
+def ec_slp_repair(slp: int, xor_cancel: bool = True) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ec_slp_repair(slp, 1 if xor_cancel else 0, ctypes.byref(h)))
+    return h.value
+
+
+def ec_slp_fuse(slp: int, cancel_pairs: bool = True) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ec_slp_fuse(slp, 1 if cancel_pairs else 0, ctypes.byref(h)))
+    return h.value
+
+
+def ec_slp_schedule(slp: int, kind: int = EC_SCHED_DFS, cap: int = 8) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ec_slp_schedule(slp, kind, cap, ctypes.byref(h)))
+    return h.value
+
+
+def ec_slp_stats_get(slp: int) -> dict:
+    s = _abi.SlpStats()
+    _check(lib().ec_slp_stats_get(slp, ctypes.byref(s)))
+    return _stats(s)
+
+
+def ec_slp_iocost(slp: int, cap: int) -> int:
+    return int(lib().ec_slp_iocost(slp, cap))
+
+
+def ec_slp_ccap(slp: int) -> int:
+    return int(lib().ec_slp_ccap(slp))
+
+
+def ec_slp_equivalent(a: int, b: int) -> bool:
+    eq = ctypes.c_int()
+    _check(lib().ec_slp_equivalent(a, b, ctypes.byref(eq)))
+    return bool(eq.value)
+
+
+def ec_slp_to_text(slp: int) -> str:
+    need = ctypes.c_size_t()
+    _check(lib().ec_slp_to_text(slp, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().ec_slp_to_text(slp, buf, need.value, None))
+    return buf.value.decode()
+
+
+def ec_slp_destroy(slp: int) -> None:
+    lib().ec_slp_destroy(slp)

@@ -1,0 +1,105 @@
+"""ctypes declarations of the C ABI in include/xorec.h (argument marshalling
+only).  The library is the in-tree build ``_build/libxorec.so``; importing
+fails loudly when it is missing."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libxorec.so")
+
+c_int = ctypes.c_int
+c_long = ctypes.c_long
+c_size = ctypes.c_size_t
+c_u64 = ctypes.c_uint64
+c_vp = ctypes.c_void_p
+c_char_p = ctypes.c_char_p
+u8p = ctypes.POINTER(ctypes.c_uint8)
+intp = ctypes.POINTER(ctypes.c_int)
+vpp = ctypes.POINTER(ctypes.c_void_p)
+
+EC_OK = 0
+EC_EINVAL = -1
+EC_ENOMEM = -2
+EC_ESINGULAR = -3
+EC_ETOOMANY = -4
+EC_ECUDA = -5
+EC_ETIMEOUT = -6
+EC_EBUSY = -7
+EC_ENOTSUP = -8
+
+EC_MATRIX_CAUCHY, EC_MATRIX_POWER, EC_MATRIX_USER = 0, 1, 2
+EC_OPT_RAW, EC_OPT_REPAIR, EC_OPT_XORREPAIR = 0, 1, 2
+EC_SCHED_DFS, EC_SCHED_GREEDY = 0, 1
+EC_EXEC_AUTO, EC_EXEC_INTERP, EC_EXEC_COMPILED = 0, 1, 2
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("opt_level", c_int), ("sched", c_int), ("greedy_cap", c_int),
+                ("executor", c_int)]
+
+
+class SlpStats(ctypes.Structure):
+    _fields_ = [("xors", c_long), ("mem", c_long), ("nvar", c_int), ("stmts", c_int)]
+
+
+class ProgramInfo(ctypes.Structure):
+    _fields_ = [("n_in", c_int), ("n_out", c_int), ("slots", c_int), ("stmts", c_int),
+                ("code_words", c_int), ("sched_nvar", c_int), ("raw", SlpStats),
+                ("compressed", SlpStats), ("fused", SlpStats), ("compiled", c_int),
+                ("regs", c_int)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/xorec.h
+SIGNATURES = {
+    "ec_plan_create": (c_int, [c_int, c_int, u8p, ctypes.POINTER(c_vp)]),
+    "ec_plan_create_ex": (c_int, [c_int, c_int, c_int, u8p, ctypes.POINTER(PlanOpts),
+                                  ctypes.POINTER(c_vp)]),
+    "ec_plan_destroy": (None, [c_vp]),
+    "ec_plan_matrix": (c_int, [c_vp, u8p]),
+    "ec_plan_info": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ProgramInfo)]),
+    "ec_plan_program": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ctypes.c_uint16), c_size,
+                                ctypes.POINTER(c_size)]),
+    "ec_encode": (c_int, [c_vp, vpp, vpp, c_size, c_vp]),
+    "ec_encode_strided": (c_int, [c_vp, c_vp, c_size, c_size, c_vp, c_size, c_size, c_int,
+                                  c_size, c_vp]),
+    "ec_decode": (c_int, [c_vp, intp, c_int, vpp, vpp, c_size, c_vp]),
+    "ec_decode_prepare": (c_int, [c_vp, intp, intp, c_int, c_int]),
+    "ec_plan_set_executor": (c_int, [c_vp, c_int]),
+    "ec_device_status": (c_int, [intp, c_int]),
+    "ec_last_error": (c_char_p, []),
+    "ec_version": (c_char_p, []),
+    "ec_synth_fill": (c_int, [c_vp, c_size, c_u64, c_u64, c_vp]),
+    "ec_slp_parse": (c_int, [c_char_p, ctypes.POINTER(c_vp)]),
+    "ec_slp_from_matrix": (c_int, [c_int, c_int, u8p, c_int, ctypes.POINTER(c_vp)]),
+    "ec_slp_repair": (c_int, [c_vp, c_int, ctypes.POINTER(c_vp)]),
+    "ec_slp_fuse": (c_int, [c_vp, c_int, ctypes.POINTER(c_vp)]),
+    "ec_slp_schedule": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_vp)]),
+    "ec_slp_stats_get": (c_int, [c_vp, ctypes.POINTER(SlpStats)]),
+    "ec_slp_iocost": (c_long, [c_vp, c_int]),
+    "ec_slp_ccap": (c_int, [c_vp]),
+    "ec_slp_equivalent": (c_int, [c_vp, c_vp, intp]),
+    "ec_slp_to_text": (c_int, [c_vp, c_char_p, c_size, ctypes.POINTER(c_size)]),
+    "ec_slp_destroy": (None, [c_vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libxorec.so (the CUDA path).  Raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libxorec.so not found at {LIB_PATH}; run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,600 @@
+// C ABI of the library (declared in include/xorec.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/xorec.h"
+#include "gf.h"
+#include "internal.h"
+
+using xorec::Program;
+
+namespace xorec {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::mutex g_dev_mu;
+static DeviceInfo g_dev[64];
+
+bool device_info(DeviceInfo* out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    set_error("no CUDA device");
+    return false;
+  }
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DeviceInfo& d = g_dev[dev];
+  if (d.device < 0) {
+    int sms = 0, optin = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaDeviceGetAttribute failed");
+      return false;
+    }
+    int* st = nullptr;
+    if (cudaMalloc(&st, sizeof(int)) != cudaSuccess || cudaMemset(st, 0, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cannot allocate the device status word");
+      return false;
+    }
+    d.sms = sms;
+    d.smem_optin = static_cast<size_t>(optin);
+    d.status = st;
+    d.device = dev;
+  }
+  *out = d;
+  return true;
+}
+
+bool ensure_device_code(Program* p) {
+  if (p->d_code) return true;
+  const size_t bytes = std::max<size_t>(1, p->code.size()) * sizeof(uint16_t);
+  uint16_t* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of the program failed");
+    return false;
+  }
+  if (!p->code.empty() &&
+      cudaMemcpy(d, p->code.data(), p->code.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d);
+    set_error("upload of the program failed");
+    return false;
+  }
+  p->d_code = d;
+  return true;
+}
+
+static int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+static std::mutex g_jit_mu;
+
+bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t stream) {
+  DeviceInfo di;
+  if (!device_info(&di)) return false;
+  if (io.n_stripes == 0 || io.S == 0) return true;
+  bool compiled = false;
+  int threads = 0, nstage = 0;
+  if (executor != EC_EXEC_INTERP) {
+    threads = env_int("EC_JIT_THREADS", 256);
+    nstage = env_int("EC_JIT_NSTAGE", 2);
+    std::string err;
+    {
+      std::lock_guard<std::mutex> lk(g_jit_mu);
+      compiled = p->jit != nullptr || (jit_available() && jit_compile(p, threads, &err));
+    }
+    if (!compiled && executor == EC_EXEC_COMPILED) {
+      set_error("compiled tier unavailable: " + err);
+      return false;
+    }
+  }
+  xk::LaunchParams lp;
+  std::memset(&lp, 0, sizeof(lp));
+  lp.io = io;
+  lp.n_in = p->n_in;
+  lp.n_out = p->n_out;
+  lp.status = di.status;
+  size_t smem = 0;
+  int per_sm = 0;
+  if (compiled) {
+    lp.T = 4 * threads;
+    for (;; --nstage) {
+      smem = interp_smem_bytes(p->n_in, 0, lp.T, nstage);
+      if (smem <= di.smem_optin || nstage == 1) break;
+    }
+    if (smem > di.smem_optin) {
+      compiled = false;   // too many inputs for the compiled tile: interpret
+    } else {
+      per_sm = jit_max_ctas_per_sm(p, threads, smem);
+    }
+  }
+  if (!compiled) {
+    if (!ensure_device_code(p)) return false;
+    threads = env_int("EC_INTERP_THREADS", 128);
+    nstage = env_int("EC_INTERP_NSTAGE", 2);
+    for (;;) {
+      lp.T = 4 * threads;
+      smem = interp_smem_bytes(p->n_in, p->n_slots, lp.T, nstage);
+      if (smem <= di.smem_optin) break;
+      if (nstage > 1) { --nstage; continue; }
+      if (threads > 32) { threads /= 2; nstage = env_int("EC_INTERP_NSTAGE", 2); continue; }
+      set_error("program needs more shared memory than one CTA can hold");
+      return false;
+    }
+    lp.code = p->d_code;
+    lp.code_len = static_cast<int>(p->code.size());
+    lp.n_slots = p->n_slots;
+    per_sm = interp_max_ctas_per_sm(threads, smem);
+  }
+  lp.nstage = nstage;
+  lp.tiles_per_strip = (io.S + lp.T - 1) / lp.T;
+  lp.n_items = io.n_stripes * lp.tiles_per_strip;
+  if (per_sm < 1) per_sm = 1;
+  long long grid = static_cast<long long>(di.sms) * per_sm;
+  const int grid_env = env_int("EC_GRID", 0);
+  if (grid_env > 0) grid = grid_env;
+  if (grid > lp.n_items) grid = lp.n_items;
+  if (compiled) return jit_launch(p, lp, threads, static_cast<int>(grid), smem, stream);
+  return launch_interp(lp, threads, static_cast<int>(grid), smem, stream);
+}
+
+}  // namespace xorec
+
+// ------------------------------------------------------------------ helpers
+
+namespace {
+
+ec_status fail(ec_status s, const std::string& msg) {
+  xorec::set_error(msg);
+  return s;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+ec_status check_block_bytes(size_t B) {
+  if (B == 0 || B % 128 != 0) return fail(EC_EINVAL, "block_bytes must be a positive multiple of 128");
+  return EC_OK;
+}
+
+// Upload a per-call pointer table with a stream-ordered allocation and run.
+ec_status run_with_table(Program* p, const std::vector<uint64_t>& tab, int n_inblk, int n_outblk,
+                         long long n_stripes, size_t B, int executor, cudaStream_t st) {
+  const size_t bytes = tab.size() * sizeof(uint64_t);
+  void* d = nullptr;
+  if (cudaMallocAsync(&d, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EC_ENOMEM, "cudaMallocAsync of the block table failed");
+  }
+  if (cudaMemcpyAsync(d, tab.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(d, st);
+    return fail(EC_ECUDA, "copy of the block table failed");
+  }
+  xk::IoDesc io;
+  std::memset(&io, 0, sizeof(io));
+  io.tab = static_cast<const xk::u64*>(d);
+  io.n_inblk = n_inblk;
+  io.n_outblk = n_outblk;
+  io.S = static_cast<long long>(B / 8);
+  io.n_stripes = n_stripes;
+  const bool ok = xorec::launch_program(p, io, executor, st);
+  cudaFreeAsync(d, st);
+  return ok ? EC_OK : EC_ECUDA;
+}
+
+// Decode program for a sorted erasure set (built on first use).
+ec_status get_decode_program(ec_plan* plan, const std::vector<int>& er, Program** out) {
+  {
+    std::lock_guard<std::mutex> lk(plan->mu);
+    auto it = plan->dec.find(er);
+    if (it != plan->dec.end()) {
+      *out = it->second.get();
+      return EC_OK;
+    }
+  }
+  const int k = plan->k, m = plan->m;
+  std::vector<int> S;
+  for (int id = 0, j = 0; id < k + m && static_cast<int>(S.size()) < k; ++id) {
+    if (j < static_cast<int>(er.size()) && er[j] == id) { ++j; continue; }
+    S.push_back(id);
+  }
+  std::vector<uint8_t> R;
+  if (!xorec::decode_matrix(k, m, plan->P.data(), er, S, &R))
+    return fail(EC_ESINGULAR, "survivor submatrix is singular for this erasure set");
+  auto prog = std::make_unique<Program>();
+  std::string err;
+  if (!xorec::build_program(static_cast<int>(er.size()), k, R.data(), plan->opts, prog.get(), &err))
+    return fail(EC_EINVAL, err);
+  std::lock_guard<std::mutex> lk(plan->mu);
+  auto it = plan->dec.find(er);
+  if (it == plan->dec.end()) it = plan->dec.emplace(er, std::move(prog)).first;
+  *out = it->second.get();
+  return EC_OK;
+}
+
+ec_status canon_erasures(const ec_plan* plan, const int* erasures, int n, std::vector<int>* out) {
+  if (n < 1) return fail(EC_EINVAL, "at least one erasure is required");
+  if (n > plan->m) return fail(EC_ETOOMANY, "more erasures than parity blocks");
+  if (!erasures) return fail(EC_EINVAL, "erasures is NULL");
+  std::vector<int> e(erasures, erasures + n);
+  for (int x : e)
+    if (x < 0 || x >= plan->k + plan->m) return fail(EC_EINVAL, "erasure id out of range");
+  std::sort(e.begin(), e.end());
+  if (std::adjacent_find(e.begin(), e.end()) != e.end())
+    return fail(EC_EINVAL, "duplicate erasure id");
+  *out = e;
+  return EC_OK;
+}
+
+void release_program(Program* p) {
+  if (!p) return;
+  if (p->d_code) cudaFree(p->d_code);
+  p->d_code = nullptr;
+}
+
+}  // namespace
+
+
+// -------------------------------------------------------------- plan API
+
+extern "C" {
+
+const char* ec_last_error(void) { return xorec::g_last_error.c_str(); }
+
+const char* ec_version(void) { return "xorec 0.1 (sm_103a)"; }
+
+ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix,
+                            const ec_plan_opts* opts, ec_plan** out) {
+  if (!out) return fail(EC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (k < 1 || m < 1 || k + m > 256) return fail(EC_EINVAL, "need 1 <= k, 1 <= m, k + m <= 256");
+  auto plan = std::make_unique<ec_plan>();
+  plan->k = k;
+  plan->m = m;
+  plan->matrix_kind = matrix_kind;
+  switch (matrix_kind) {
+    case EC_MATRIX_CAUCHY: plan->P = xorec::cauchy_parity(k, m); break;
+    case EC_MATRIX_POWER: plan->P = xorec::power_parity(k, m); break;
+    case EC_MATRIX_USER:
+      if (!matrix) return fail(EC_EINVAL, "EC_MATRIX_USER needs a matrix");
+      plan->P.assign(matrix, matrix + static_cast<size_t>(k) * m);
+      break;
+    default: return fail(EC_EINVAL, "unknown matrix kind");
+  }
+  if (opts) {
+    if (opts->opt_level < EC_OPT_RAW || opts->opt_level > EC_OPT_XORREPAIR)
+      return fail(EC_EINVAL, "bad opt_level");
+    if (opts->sched != EC_SCHED_DFS && opts->sched != EC_SCHED_GREEDY)
+      return fail(EC_EINVAL, "bad sched");
+    if (opts->executor < EC_EXEC_AUTO || opts->executor > EC_EXEC_COMPILED)
+      return fail(EC_EINVAL, "bad executor");
+    plan->opts.opt_level = opts->opt_level;
+    plan->opts.sched = opts->sched;
+    plan->opts.greedy_cap = opts->greedy_cap > 0 ? opts->greedy_cap : 128;
+    plan->executor = opts->executor;
+  }
+  plan->enc = std::make_unique<Program>();
+  std::string err;
+  if (!xorec::build_program(m, k, plan->P.data(), plan->opts, plan->enc.get(), &err))
+    return fail(EC_EINVAL, err);
+  *out = plan.release();
+  return EC_OK;
+}
+
+ec_status ec_plan_create(int k, int m, const uint8_t* matrix, ec_plan** out) {
+  return ec_plan_create_ex(k, m, matrix ? EC_MATRIX_USER : EC_MATRIX_CAUCHY, matrix, nullptr, out);
+}
+
+void ec_plan_destroy(ec_plan* plan) {
+  if (!plan) return;
+  release_program(plan->enc.get());
+  xorec::jit_release(plan->enc.get());
+  for (auto& kv : plan->dec) {
+    release_program(kv.second.get());
+    xorec::jit_release(kv.second.get());
+  }
+  delete plan;
+}
+
+ec_status ec_plan_matrix(const ec_plan* plan, uint8_t* out) {
+  if (!plan || !out) return fail(EC_EINVAL, "NULL argument");
+  std::memcpy(out, plan->P.data(), plan->P.size());
+  return EC_OK;
+}
+
+ec_status ec_plan_set_executor(ec_plan* plan, int executor) {
+  if (!plan) return fail(EC_EINVAL, "NULL plan");
+  if (executor < EC_EXEC_AUTO || executor > EC_EXEC_COMPILED) return fail(EC_EINVAL, "bad executor");
+  if (executor == EC_EXEC_COMPILED && !xorec::jit_available())
+    return fail(EC_ENOTSUP, "no run-time compiler available");
+  plan->executor = executor;
+  return EC_OK;
+}
+
+static void fill_stats(const xorec::SlpMetrics& m, ec_slp_stats* s) {
+  s->xors = m.xors;
+  s->mem = m.mem;
+  s->nvar = m.nvar;
+  s->stmts = m.stmts;
+}
+
+ec_status ec_plan_info(ec_plan* plan, const int* erasures, int n_erasures, ec_program_info* out) {
+  if (!plan || !out) return fail(EC_EINVAL, "NULL argument");
+  Program* p = plan->enc.get();
+  if (erasures) {
+    std::vector<int> er;
+    ec_status s = canon_erasures(plan, erasures, n_erasures, &er);
+    if (s != EC_OK) return s;
+    s = get_decode_program(plan, er, &p);
+    if (s != EC_OK) return s;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->n_in = p->n_in;
+  out->n_out = p->n_out;
+  out->slots = p->n_slots;
+  out->stmts = p->n_stmts;
+  out->code_words = static_cast<int>(p->code.size());
+  out->sched_nvar = p->stats.sched_nvar;
+  fill_stats(p->stats.raw, &out->raw);
+  fill_stats(p->stats.compressed, &out->compressed);
+  fill_stats(p->stats.fused, &out->fused);
+  out->compiled = p->jit != nullptr;
+  out->regs = xorec::jit_regs(p);
+  return EC_OK;
+}
+
+ec_status ec_plan_program(ec_plan* plan, const int* erasures, int n_erasures, uint16_t* buf,
+                          size_t len, size_t* need) {
+  if (!plan) return fail(EC_EINVAL, "NULL plan");
+  Program* p = plan->enc.get();
+  if (erasures) {
+    std::vector<int> er;
+    ec_status s = canon_erasures(plan, erasures, n_erasures, &er);
+    if (s != EC_OK) return s;
+    s = get_decode_program(plan, er, &p);
+    if (s != EC_OK) return s;
+  }
+  if (need) *need = p->code.size();
+  if (buf) std::memcpy(buf, p->code.data(), std::min(len, p->code.size()) * sizeof(uint16_t));
+  return EC_OK;
+}
+
+ec_status ec_encode(ec_plan* plan, const uint8_t* const* data, uint8_t* const* parity,
+                    size_t block_bytes, void* stream) {
+  if (!plan || !data || !parity) return fail(EC_EINVAL, "NULL argument");
+  ec_status s = check_block_bytes(block_bytes);
+  if (s != EC_OK) return s;
+  std::vector<uint64_t> tab;
+  for (int j = 0; j < plan->k; ++j) {
+    if (!data[j] || !aligned16(data[j])) return fail(EC_EINVAL, "data block NULL or not 16-byte aligned");
+    tab.push_back(reinterpret_cast<uint64_t>(data[j]));
+  }
+  for (int i = 0; i < plan->m; ++i) {
+    if (!parity[i] || !aligned16(parity[i])) return fail(EC_EINVAL, "parity block NULL or not 16-byte aligned");
+    tab.push_back(reinterpret_cast<uint64_t>(parity[i]));
+  }
+  return run_with_table(plan->enc.get(), tab, plan->k, plan->m, 1, block_bytes, plan->executor,
+                        static_cast<cudaStream_t>(stream));
+}
+
+ec_status ec_encode_strided(ec_plan* plan, const uint8_t* data, size_t data_stripe_stride,
+                            size_t data_block_stride, uint8_t* parity, size_t par_stripe_stride,
+                            size_t par_block_stride, int n_stripes, size_t block_bytes,
+                            void* stream) {
+  if (!plan || !data || !parity) return fail(EC_EINVAL, "NULL argument");
+  if (n_stripes < 0) return fail(EC_EINVAL, "negative stripe count");
+  ec_status s = check_block_bytes(block_bytes);
+  if (s != EC_OK) return s;
+  if (!aligned16(data) || !aligned16(parity) || data_stripe_stride % 16 || data_block_stride % 16 ||
+      par_stripe_stride % 16 || par_block_stride % 16)
+    return fail(EC_EINVAL, "bases and strides must be multiples of 16 bytes");
+  if (n_stripes == 0) return EC_OK;
+  xk::IoDesc io;
+  std::memset(&io, 0, sizeof(io));
+  io.in_base = data;
+  io.in_sstride = static_cast<long long>(data_stripe_stride);
+  io.in_bstride = static_cast<long long>(data_block_stride);
+  io.out_base = parity;
+  io.out_sstride = static_cast<long long>(par_stripe_stride);
+  io.out_bstride = static_cast<long long>(par_block_stride);
+  io.n_inblk = plan->k;
+  io.n_outblk = plan->m;
+  io.S = static_cast<long long>(block_bytes / 8);
+  io.n_stripes = n_stripes;
+  return xorec::launch_program(plan->enc.get(), io, plan->executor,
+                               static_cast<cudaStream_t>(stream))
+             ? EC_OK
+             : EC_ECUDA;
+}
+
+ec_status ec_decode(ec_plan* plan, const int* erasures, int n_erasures,
+                    const uint8_t* const* blocks, uint8_t* const* out, size_t block_bytes,
+                    void* stream) {
+  if (!plan || !blocks || !out) return fail(EC_EINVAL, "NULL argument");
+  std::vector<int> er;
+  ec_status s = canon_erasures(plan, erasures, n_erasures, &er);
+  if (s != EC_OK) return s;
+  s = check_block_bytes(block_bytes);
+  if (s != EC_OK) return s;
+  Program* p = nullptr;
+  s = get_decode_program(plan, er, &p);
+  if (s != EC_OK) return s;
+  const int k = plan->k, m = plan->m;
+  std::vector<uint64_t> tab;
+  for (int id = 0, j = 0; id < k + m && static_cast<int>(tab.size()) < k; ++id) {
+    if (j < static_cast<int>(er.size()) && er[j] == id) { ++j; continue; }
+    if (!blocks[id] || !aligned16(blocks[id]))
+      return fail(EC_EINVAL, "surviving block NULL or not 16-byte aligned");
+    tab.push_back(reinterpret_cast<uint64_t>(blocks[id]));
+  }
+  for (int e : er) {   // program outputs follow the sorted erasure order
+    const int pos = static_cast<int>(std::find(erasures, erasures + n_erasures, e) - erasures);
+    if (!out[pos] || !aligned16(out[pos])) return fail(EC_EINVAL, "output block NULL or not 16-byte aligned");
+    tab.push_back(reinterpret_cast<uint64_t>(out[pos]));
+  }
+  return run_with_table(p, tab, k, static_cast<int>(er.size()), 1, block_bytes, plan->executor,
+                        static_cast<cudaStream_t>(stream));
+}
+
+ec_status ec_decode_prepare(ec_plan* plan, const int* sets, const int* counts, int n_sets,
+                            int n_threads) {
+  if (!plan || (n_sets > 0 && (!sets || !counts))) return fail(EC_EINVAL, "NULL argument");
+  std::vector<std::vector<int>> todo;
+  size_t off = 0;
+  for (int i = 0; i < n_sets; ++i) {
+    std::vector<int> er;
+    ec_status s = canon_erasures(plan, sets + off, counts[i], &er);
+    if (s != EC_OK) return s;
+    off += counts[i];
+    todo.push_back(er);
+  }
+  if (n_threads <= 0) n_threads = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+  std::atomic<size_t> next{0};
+  std::atomic<int> rc{EC_OK};
+  std::vector<std::thread> pool;
+  for (int t = 0; t < n_threads; ++t)
+    pool.emplace_back([&]() {
+      for (;;) {
+        const size_t i = next.fetch_add(1);
+        if (i >= todo.size()) return;
+        Program* p = nullptr;
+        const ec_status s = get_decode_program(plan, todo[i], &p);
+        if (s != EC_OK) rc.store(s);
+      }
+    });
+  for (auto& th : pool) th.join();
+  return static_cast<ec_status>(rc.load());
+}
+
+ec_status ec_device_status(int* status, int reset) {
+  if (!status) return fail(EC_EINVAL, "NULL argument");
+  xorec::DeviceInfo di;
+  if (!xorec::device_info(&di)) return EC_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EC_ECUDA, "cudaDeviceSynchronize failed");
+  }
+  int v = 0;
+  if (cudaMemcpy(&v, di.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(EC_ECUDA, "reading the status word failed");
+  *status = v == xk::XK_STATUS_TIMEOUT ? EC_ETIMEOUT : 0;
+  if (reset && cudaMemset(di.status, 0, sizeof(int)) != cudaSuccess)
+    return fail(EC_ECUDA, "resetting the status word failed");
+  return EC_OK;
+}
+
+ec_status ec_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset, void* stream) {
+  if (!dst && n) return fail(EC_EINVAL, "NULL destination");
+  return xorec::launch_synth_fill(dst, n, seed, offset, static_cast<cudaStream_t>(stream))
+             ? EC_OK
+             : EC_ECUDA;
+}
+
+// ---------------------------------------------------------------- SLP API
+
+struct ec_slp {
+  xorec::Slp p;
+};
+
+static ec_status wrap(const xorec::Slp& p, ec_slp** out) {
+  if (!out) return fail(EC_EINVAL, "out is NULL");
+  *out = new ec_slp{p};
+  return EC_OK;
+}
+
+ec_status ec_slp_parse(const char* text, ec_slp** out) {
+  if (!text) return fail(EC_EINVAL, "NULL text");
+  xorec::Slp p;
+  std::string err;
+  if (!xorec::parse_slp(text, &p, &err)) return fail(EC_EINVAL, err);
+  return wrap(p, out);
+}
+
+ec_status ec_slp_from_matrix(int rows, int cols, const uint8_t* A, int form, ec_slp** out) {
+  if (rows < 1 || cols < 1 || !A || (form != 0 && form != 1)) return fail(EC_EINVAL, "bad arguments");
+  std::vector<xorec::Bits> R = xorec::bitmatrix_rows(rows, cols, A);
+  std::vector<int> order;
+  for (int i = 0; i < rows; ++i)
+    for (int s = 7; s >= 0; --s) order.push_back(8 * i + s);
+  return wrap(form == 0 ? xorec::slp_rows_fused(8 * cols, R, order)
+                        : xorec::slp_rows_chains(8 * cols, R, order),
+              out);
+}
+
+ec_status ec_slp_repair(const ec_slp* in, int xor_cancel, ec_slp** out) {
+  if (!in) return fail(EC_EINVAL, "NULL program");
+  return wrap(xorec::repair(in->p, xor_cancel != 0), out);
+}
+
+static bool single_assignment(const xorec::Slp& p) {
+  std::vector<char> seen(p.n_var, 0);
+  for (const auto& s : p.body) {
+    if (seen[s.dst - p.n_const]) return false;
+    seen[s.dst - p.n_const] = 1;
+  }
+  return true;
+}
+
+ec_status ec_slp_fuse(const ec_slp* in, int cancel_pairs, ec_slp** out) {
+  if (!in) return fail(EC_EINVAL, "NULL program");
+  if (!single_assignment(in->p)) return fail(EC_EINVAL, "fusion needs a single-assignment program");
+  return wrap(xorec::fuse(in->p, cancel_pairs != 0), out);
+}
+
+ec_status ec_slp_schedule(const ec_slp* in, int kind, int cap, ec_slp** out) {
+  if (!in) return fail(EC_EINVAL, "NULL program");
+  if (!single_assignment(in->p)) return fail(EC_EINVAL, "scheduling needs a single-assignment program");
+  xorec::Schedule s = kind == EC_SCHED_GREEDY ? xorec::schedule_greedy(in->p, cap, true)
+                                              : xorec::schedule_dfs(in->p, true);
+  return wrap(xorec::schedule_to_slp(in->p, s), out);
+}
+
+ec_status ec_slp_stats_get(const ec_slp* p, ec_slp_stats* out) {
+  if (!p || !out) return fail(EC_EINVAL, "NULL argument");
+  fill_stats(xorec::metrics(p->p), out);
+  return EC_OK;
+}
+
+long ec_slp_iocost(const ec_slp* p, int cap) {
+  if (!p || cap < 1) return -1;
+  return xorec::lru_iocost(p->p, cap, nullptr);
+}
+
+int ec_slp_ccap(const ec_slp* p) { return p ? xorec::ccap(p->p) : -1; }
+
+ec_status ec_slp_equivalent(const ec_slp* a, const ec_slp* b, int* eq) {
+  if (!a || !b || !eq) return fail(EC_EINVAL, "NULL argument");
+  *eq = xorec::equivalent(a->p, b->p) ? 1 : 0;
+  return EC_OK;
+}
+
+ec_status ec_slp_to_text(const ec_slp* p, char* buf, size_t len, size_t* need) {
+  if (!p) return fail(EC_EINVAL, "NULL program");
+  const std::string s = xorec::slp_to_text(p->p);
+  if (need) *need = s.size() + 1;
+  if (buf && len) {
+    const size_t n = std::min(len - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = '\0';
+  }
+  return EC_OK;
+}
+
+void ec_slp_destroy(ec_slp* p) { delete p; }
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// GPU executors compiled into the library: the SLP interpreter and the
+// synthetic input generator.
+//
+// The interpreter runs the instruction stream of a scheduled, fused SLP
+// (Sec. 4-6 of the paper; the stream format is described in plan.h) over
+// the tiles staged by the shared pipeline (tile_pipeline.cuh).  Each thread
+// owns one 4-byte column of every strip of the tile: for each statement it
+// XORs its operands (input strips of the stage or pebble slots, both in
+// shared memory) in registers, stores the result into its slot when a later
+// statement reads it, and writes it to each output strip it is returned as.
+// Threads touch only their own column, so statements need no barrier.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "tile_pipeline.cuh"
+
+namespace {
+
+using namespace xk;
+
+struct InterpBody {
+  __device__ __forceinline__ void operator()(const LaunchParams& p, i64 s, i64 c0, int len,
+                                             const u8* stg, u8* slots) const {
+    const int col = threadIdx.x * 4;
+    if (col >= len) return;
+    const u16* __restrict__ code = p.code;
+    const int T = p.T;
+    const int n_in = p.n_in;
+    const u8* in_col = stg + col;
+    // operand id -> address: inputs live in the stage, slots after it
+    u8* slot_col = slots + col - static_cast<i64>(n_in) * T;
+    int pc = 0;
+    while (pc < p.code_len) {
+      const int na = __ldg(code + pc);
+      const int w1 = __ldg(code + pc + 1);
+      pc += 2;
+      const int no = w1 & 0x7fff;
+      int slot = -1;
+      if (w1 & 0x8000) slot = __ldg(code + pc++);
+      const int ob = pc;
+      pc += no;
+      u32 acc = 0;
+      int a = 0;
+      for (; a + 4 <= na; a += 4) {
+        const int o0 = __ldg(code + pc + a), o1 = __ldg(code + pc + a + 1);
+        const int o2 = __ldg(code + pc + a + 2), o3 = __ldg(code + pc + a + 3);
+        const u32 x0 = *reinterpret_cast<const u32*>((o0 < n_in ? in_col : slot_col) + static_cast<i64>(o0) * T);
+        const u32 x1 = *reinterpret_cast<const u32*>((o1 < n_in ? in_col : slot_col) + static_cast<i64>(o1) * T);
+        const u32 x2 = *reinterpret_cast<const u32*>((o2 < n_in ? in_col : slot_col) + static_cast<i64>(o2) * T);
+        const u32 x3 = *reinterpret_cast<const u32*>((o3 < n_in ? in_col : slot_col) + static_cast<i64>(o3) * T);
+        acc ^= x0 ^ x1 ^ x2 ^ x3;
+      }
+      for (; a < na; ++a) {
+        const int o = __ldg(code + pc + a);
+        acc ^= *reinterpret_cast<const u32*>((o < n_in ? in_col : slot_col) + static_cast<i64>(o) * T);
+      }
+      pc += na;
+      if (slot >= 0) *reinterpret_cast<u32*>(slots + static_cast<i64>(slot) * T + col) = acc;
+      for (int o = 0; o < no; ++o) {
+        const int r = __ldg(code + ob + o);
+        u8* dst = out_block(p.io, s, r >> 3) + static_cast<i64>(r & 7) * p.io.S + c0 + col;
+        *reinterpret_cast<u32*>(dst) = acc;
+      }
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256) interp_kernel(LaunchParams p) {
+  extern __shared__ __align__(128) u8 smem[];
+  run_pipeline(p, smem, InterpBody());
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) in counter form: byte n of stream
+// `seed` is byte n % 8 (little-endian) of mix(seed + (n/8 + 1) * gamma).
+__device__ __forceinline__ u64 mix64(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void synth_kernel(u8* dst, u64 n, u64 seed, u64 offset) {
+  const u64 gamma = 0x9E3779B97F4A7C15ull;
+  const u64 stride = static_cast<u64>(gridDim.x) * blockDim.x;
+  // aligned fast path: whole 8-byte words of the stream
+  if ((offset & 7) == 0 && (reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+    const u64 w0 = offset >> 3;
+    const u64 nw = n >> 3;
+    u64* d = reinterpret_cast<u64*>(dst);
+    for (u64 i = blockIdx.x * static_cast<u64>(blockDim.x) + threadIdx.x; i < nw; i += stride)
+      d[i] = mix64(seed + (w0 + i + 1) * gamma);
+    for (u64 i = (nw << 3) + blockIdx.x * static_cast<u64>(blockDim.x) + threadIdx.x; i < n;
+         i += stride) {
+      const u64 b = offset + i;
+      dst[i] = static_cast<u8>(mix64(seed + ((b >> 3) + 1) * gamma) >> (8 * (b & 7)));
+    }
+    return;
+  }
+  for (u64 i = blockIdx.x * static_cast<u64>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    const u64 b = offset + i;
+    dst[i] = static_cast<u8>(mix64(seed + ((b >> 3) + 1) * gamma) >> (8 * (b & 7)));
+  }
+}
+
+}  // namespace
+
+namespace xorec {
+
+size_t interp_smem_bytes(int n_in, int n_slots, int T, int nstage) {
+  return 128 + static_cast<size_t>(nstage) * n_in * T + static_cast<size_t>(n_slots) * T;
+}
+
+int interp_max_ctas_per_sm(int threads, size_t smem) {
+  if (cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, interp_kernel, threads, smem) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+bool launch_interp(const xk::LaunchParams& lp, int threads, int grid, size_t smem,
+                   cudaStream_t stream) {
+  if (cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess) {
+    set_error("cudaFuncSetAttribute(interp) failed");
+    return false;
+  }
+  interp_kernel<<<grid, threads, smem, stream>>>(lp);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("interpreter launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+bool launch_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset,
+                       cudaStream_t stream) {
+  if (n == 0) return true;
+  DeviceInfo di;
+  if (!device_info(&di)) return false;
+  const u64 words = (n + 7) / 8;
+  u64 blocks = (words + 255) / 256;
+  const u64 cap = static_cast<u64>(di.sms) * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  synth_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(dst, n, seed, offset);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("synth launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+}  // namespace xorec

@@ -1,0 +1,73 @@
+// Host-side internals shared by the C ABI, the executors and the compiled
+// tier.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+#include "tile_pipeline.cuh"
+
+struct ec_plan {
+  int k = 0, m = 0;
+  int matrix_kind = 0;
+  std::vector<uint8_t> P;                    // m x k parity rows
+  xorec::PlanOptions opts;
+  int executor = 0;                          // EC_EXEC_*
+  std::unique_ptr<xorec::Program> enc;
+  std::mutex mu;                             // guards dec
+  std::map<std::vector<int>, std::unique_ptr<xorec::Program>> dec;  // key: sorted erasures
+};
+
+namespace xorec {
+
+void set_error(const std::string& msg);
+
+// Per-device state: SM count, status word.
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  size_t smem_optin = 0;
+  int* status = nullptr;     // device word written by kernels on timeout
+};
+bool device_info(DeviceInfo* out);
+
+// Upload the program's interpreter stream to the device (once).
+bool ensure_device_code(Program* p);
+
+struct LaunchShape {
+  int threads = 128;   // threads per CTA; T = 4 * threads
+  int nstage = 2;
+  int grid = 0;        // 0 = one persistent wave
+};
+
+// Fill `io`-addressed launch parameters and run the interpreter or the
+// compiled kernel of `p` over n_stripes stripes of strip length S.
+bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t stream);
+
+// Interpreter launch (executor.cu).
+bool launch_interp(const xk::LaunchParams& lp, int threads, int grid, size_t smem,
+                   cudaStream_t stream);
+size_t interp_smem_bytes(int n_in, int n_slots, int T, int nstage);
+int interp_max_ctas_per_sm(int threads, size_t smem);
+
+// Compiled tier (jit.cc).
+bool jit_available();
+bool jit_compile(Program* p, int threads, std::string* err);
+bool jit_launch(Program* p, const xk::LaunchParams& lp, int threads, int grid, size_t smem,
+                cudaStream_t stream);
+int jit_max_ctas_per_sm(Program* p, int threads, size_t smem);
+void jit_release(Program* p);
+int jit_regs(const Program* p);
+std::string jit_source(const Program& p, int threads);
+
+// Synthetic input generator (executor.cu).
+bool launch_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset,
+                       cudaStream_t stream);
+
+}  // namespace xorec

@@ -1,0 +1,227 @@
+// Compiled tier: the scheduled, fused SLP of a plan is emitted as a
+// straight-line CUDA body (one SSA register per statement, operands read
+// from the shared-memory stage) and compiled for sm_103a with NVRTC when the
+// plan is built.  The pebble schedule (Sec. 6.6) orders the statements so
+// that each value dies soon after it is produced, which bounds the registers
+// the compiler needs; temporaries never leave the register file.  The tile
+// pipeline around the body is the same one the interpreter uses.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+const char* kPipelineSrc =
+#include "tile_pipeline_src.inc"
+    ;
+
+struct JitKernel {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+  int threads = 0;
+  int regs = 0;
+  size_t smem_set = 0;
+  int device = -1;
+};
+
+std::string gen_body(const xorec::Program& p, int threads) {
+  const xorec::Slp& q = p.fused;
+  const int nc = q.n_const;
+  const int T = 4 * threads;
+  std::ostringstream os;
+  os << "struct SlpBody {\n"
+        "  __device__ __forceinline__ void operator()(const xk::LaunchParams& p, xk::i64 s,\n"
+        "      xk::i64 c0, int len, const xk::u8* stg, xk::u8*) const {\n"
+        "    const int col = threadIdx.x * 4;\n"
+        "    if (col >= len) return;\n"
+        "    const xk::u8* in = stg + col;\n"
+        "    const xk::i64 S = p.io.S;\n";
+  // output block bases
+  std::vector<char> used(p.n_out / 8 + 1, 0);
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r) used[r >> 3] = 1;
+  for (int b = 0; b < p.n_out / 8; ++b)
+    if (used[b])
+      os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
+  os << "#define I(c) xk_lds(in + (c) * " << T << ")\n";
+  os << "#define O(b, t, v) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
+  std::vector<std::vector<int>> outs_of(q.n_var);
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
+    if (q.ret[r] >= nc) outs_of[q.ret[r] - nc].push_back(r);
+  for (const auto& st : p.sched.steps) {
+    os << "    const xk::u32 v" << st.node << " = ";
+    if (st.args.empty()) os << "0u";
+    for (size_t i = 0; i < st.args.size(); ++i) {
+      const int a = st.args[i];
+      if (i) os << " ^ ";
+      if (a < nc) os << "I(" << a << ")";
+      else os << "v" << (a - nc);
+    }
+    os << ";\n";
+    for (int r : outs_of[st.node]) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", v" << st.node << ");\n";
+  }
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r) {
+    const int t = q.ret[r];
+    if (t < 0) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", 0u);\n";
+    else if (t < nc) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", I(" << t << "));\n";
+  }
+  os << "#undef I\n#undef O\n  }\n};\n";
+  return os.str();
+}
+
+std::string gen_source(const xorec::Program& p, int threads) {
+  std::ostringstream os;
+  os << kPipelineSrc << "\n";
+  // Shared-memory load kept as an explicit instruction per use so that the
+  // compiler re-reads inputs from the stage instead of holding all of them
+  // in registers across the whole program.
+  os << "__device__ __forceinline__ xk::u32 xk_lds(const xk::u8* a) {\n"
+        "  xk::u32 v;\n"
+        "  asm volatile(\"ld.shared.u32 %0, [%1];\" : \"=r\"(v) : \"r\"(xk::smem_addr(a)));\n"
+        "  return v;\n"
+        "}\n";
+  os << gen_body(p, threads);
+  os << "extern \"C\" __global__ void __launch_bounds__(" << threads
+     << ", 1) xorec_slp(xk::LaunchParams p) {\n"
+        "  extern __shared__ __align__(128) xk::u8 smem[];\n"
+        "  xk::run_pipeline(p, smem, SlpBody());\n"
+        "}\n";
+  return os.str();
+}
+
+}  // namespace
+
+namespace xorec {
+
+bool jit_available() {
+  int major = 0, minor = 0;
+  return nvrtcVersion(&major, &minor) == NVRTC_SUCCESS;
+}
+
+// Compile `p` for the current device's architecture.  Stores a JitKernel in
+// p->jit on success.
+bool jit_compile(Program* p, int threads, std::string* err) {
+  if (p->jit) return true;
+  DeviceInfo di;
+  if (!device_info(&di)) {
+    *err = "no CUDA device";
+    return false;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, di.device) != cudaSuccess) {
+    *err = "cudaGetDeviceProperties failed";
+    return false;
+  }
+  const std::string src = gen_source(*p, threads);
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "xorec_slp.cu", 0, nullptr, nullptr) !=
+      NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return false;
+  }
+  char arch[64];
+  std::snprintf(arch, sizeof(arch), "-arch=sm_%d%da", prop.major, prop.minor);
+  const char* opts[] = {arch, "-std=c++17", "-default-device", "--extra-device-vectorization"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
+  if (rc != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    nvrtcGetProgramLog(prog, &log[0]);
+    nvrtcDestroyProgram(&prog);
+    *err = "NVRTC compile failed: " + log.substr(0, 2000);
+    return false;
+  }
+  size_t nbin = 0;
+  nvrtcGetCUBINSize(prog, &nbin);
+  std::vector<char> cubin(nbin);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  auto* jk = new JitKernel();
+  if (cudaLibraryLoadData(&jk->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
+          cudaSuccess ||
+      cudaLibraryGetKernel(&jk->kern, jk->lib, "xorec_slp") != cudaSuccess) {
+    cudaGetLastError();
+    delete jk;
+    *err = "loading the compiled SLP kernel failed";
+    return false;
+  }
+  jk->threads = threads;
+  jk->device = di.device;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(jk->kern)) == cudaSuccess)
+    jk->regs = fa.numRegs;
+  else
+    cudaGetLastError();
+  p->jit = jk;
+  return true;
+}
+
+static bool jit_set_smem(JitKernel* jk, size_t smem) {
+  if (jk->smem_set >= smem) return true;
+  if (cudaKernelSetAttributeForDevice(jk->kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem), jk->device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  jk->smem_set = smem;
+  return true;
+}
+
+int jit_max_ctas_per_sm(Program* p, int threads, size_t smem) {
+  auto* jk = static_cast<JitKernel*>(p->jit);
+  if (!jk || !jit_set_smem(jk, smem)) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, reinterpret_cast<const void*>(jk->kern),
+                                                    threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n;
+}
+
+bool jit_launch(Program* p, const xk::LaunchParams& lp, int threads, int grid, size_t smem,
+                cudaStream_t stream) {
+  auto* jk = static_cast<JitKernel*>(p->jit);
+  if (!jk || jk->threads != threads) {
+    set_error("compiled kernel missing or built for another block size");
+    return false;
+  }
+  if (!jit_set_smem(jk, smem)) {
+    set_error("cannot set shared memory size of the compiled kernel");
+    return false;
+  }
+  xk::LaunchParams copy = lp;
+  void* args[] = {&copy};
+  const cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(jk->kern), dim3(grid),
+                                         dim3(threads), args, smem, stream);
+  if (e != cudaSuccess) {
+    set_error(std::string("compiled kernel launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+// Source of the straight-line kernel (for inspection and tests).
+std::string jit_source(const Program& p, int threads) { return gen_source(p, threads); }
+
+void jit_release(Program* p) {
+  auto* jk = static_cast<JitKernel*>(p ? p->jit : nullptr);
+  if (!jk) return;
+  cudaLibraryUnload(jk->lib);
+  delete jk;
+  p->jit = nullptr;
+}
+
+int jit_regs(const Program* p) {
+  const auto* jk = static_cast<const JitKernel*>(p ? p->jit : nullptr);
+  return jk ? jk->regs : 0;
+}
+
+}  // namespace xorec

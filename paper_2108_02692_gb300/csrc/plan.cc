@@ -1,0 +1,124 @@
+#include "plan.h"
+
+#include "gf.h"
+
+namespace xorec {
+
+std::vector<Bits> bitmatrix_rows(int rows, int cols, const uint8_t* A) {
+  std::vector<Bits> R(static_cast<size_t>(8) * rows, Bits(8 * cols));
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j)
+      for (int t = 0; t < 8; ++t) {
+        const uint8_t c = gf_mul(A[static_cast<size_t>(i) * cols + j], static_cast<uint8_t>(1u << t));
+        for (int s = 0; s < 8; ++s)
+          if ((c >> s) & 1u) R[8 * i + s].set(8 * j + t);
+      }
+  return R;
+}
+
+namespace {
+
+uint64_t fnv1a(uint64_t h, uint64_t v) {
+  for (int i = 0; i < 8; ++i) {
+    h ^= (v >> (8 * i)) & 0xff;
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+// Lower a GPU schedule of the fused program into the interpreter stream.
+bool lower(const Slp& q, const Schedule& s, int n_in, int n_out, Program* p,
+           std::string* err) {
+  const int nc = q.n_const;
+  std::vector<std::vector<int>> outs_of(q.n_var);
+  std::vector<int> copy_rows, zero_rows;
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r) {
+    const int t = q.ret[r];
+    if (t < 0) zero_rows.push_back(r);
+    else if (t < nc) copy_rows.push_back(r);
+    else outs_of[t - nc].push_back(r);
+  }
+  std::vector<int> slot_of(q.n_var, -1);
+  std::vector<uint16_t> code;
+  int n_stmts = 0;
+  auto emit = [&](const std::vector<int>& args, const std::vector<int>& outs, int slot) {
+    if (args.size() > 0x7fff || outs.size() > 0x7fff) return false;
+    code.push_back(static_cast<uint16_t>(args.size()));
+    code.push_back(static_cast<uint16_t>(outs.size() | (slot >= 0 ? 0x8000u : 0u)));
+    if (slot >= 0) code.push_back(static_cast<uint16_t>(slot));
+    for (int o : outs) code.push_back(static_cast<uint16_t>(o));
+    for (int a : args) code.push_back(static_cast<uint16_t>(a));
+    ++n_stmts;
+    return true;
+  };
+  for (const auto& st : s.steps) {
+    std::vector<int> args;
+    for (int a : st.args) {
+      if (a < nc) {
+        args.push_back(a);
+      } else {
+        const int sl = slot_of[a - nc];
+        if (sl < 0) { *err = "schedule reads a value that holds no slot"; return false; }
+        args.push_back(n_in + sl);
+      }
+    }
+    slot_of[st.node] = st.pebble;
+    if (!emit(args, outs_of[st.node], st.pebble)) { *err = "statement too large"; return false; }
+  }
+  for (int r : copy_rows)
+    if (!emit({q.ret[r]}, {r}, -1)) return false;
+  for (int r : zero_rows)
+    if (!emit({}, {r}, -1)) return false;
+  if (n_in + s.n_pebbles > 0xffff) { *err = "program too large"; return false; }
+  p->code = code;
+  p->n_in = n_in;
+  p->n_out = n_out;
+  p->n_slots = s.n_pebbles;
+  p->n_stmts = n_stmts;
+  uint64_t h = 0xcbf29ce484222325ull;
+  h = fnv1a(h, static_cast<uint64_t>(n_in) << 32 | static_cast<uint32_t>(n_out));
+  for (uint16_t w : code) h = fnv1a(h, w);
+  p->hash = h;
+  return true;
+}
+
+}  // namespace
+
+bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
+                   Program* out, std::string* err) {
+  const int n_in = 8 * cols, n_out = 8 * rows;
+  std::vector<Bits> R = bitmatrix_rows(rows, cols, A);
+  std::vector<int> order;
+  for (int i = 0; i < rows; ++i)
+    for (int s = 7; s >= 0; --s) order.push_back(8 * i + s);
+  Slp chains = slp_rows_chains(n_in, R, order);
+  Program p;
+  p.stats.raw = metrics(chains);
+  Slp fused;
+  if (o.opt_level == kOptRaw) {
+    fused = slp_rows_fused(n_in, R, order);
+    p.stats.compressed = p.stats.raw;
+  } else {
+    Slp co = repair(chains, o.opt_level == kOptXorRePair);
+    p.stats.compressed = metrics(co);
+    fused = fuse(co, o.cancel_pairs);
+  }
+  p.stats.fused = metrics(fused);
+  if (!equivalent(chains, fused)) {
+    *err = "internal: optimised program is not equivalent to the bitmatrix";
+    return false;
+  }
+  Schedule paper = o.sched == kSchedGreedy ? schedule_greedy(fused, o.greedy_cap, true)
+                                           : schedule_dfs(fused, true);
+  p.stats.sched_nvar = paper.n_pebbles;
+  Schedule gpu = o.sched == kSchedGreedy ? schedule_greedy(fused, o.greedy_cap, false)
+                                         : schedule_dfs(fused, false);
+  p.stats.slots = gpu.n_pebbles;
+  if (!lower(fused, gpu, n_in, n_out, &p, err)) return false;
+  p.fused = fused;
+  p.sched = gpu;
+  *out = std::move(p);
+  return true;
+}
+
+}  // namespace xorec

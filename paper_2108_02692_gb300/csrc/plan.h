@@ -1,0 +1,61 @@
+// Plan construction: coding matrix -> bitmatrix -> SLP -> optimiser passes
+// -> executable program for the GPU executors (host side).
+#pragma once
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "slp.h"
+
+namespace xorec {
+
+// Bitmatrix of a rows x cols matrix over GF(2^8): row 8i+s, column 8j+t is
+// bit s of A[i][j] * 2^t (Sec. 1, property (ii)).
+std::vector<Bits> bitmatrix_rows(int rows, int cols, const uint8_t* A);
+
+enum OptLevel { kOptRaw = 0, kOptRePair = 1, kOptXorRePair = 2 };
+enum SchedKind { kSchedDfs = 0, kSchedGreedy = 1 };
+
+struct PipelineStats {
+  SlpMetrics raw, compressed, fused;
+  int raw_ccap = 0;
+  int sched_nvar = 0;      // pebbles of the paper's game (goals hold)
+  int slots = 0;           // pebbles when outputs stream out (GPU setting)
+};
+
+// An executable program for one linear map from n_in input strips to n_out
+// output strips.  `code` is the interpreter's instruction stream:
+//   word 0: number of arguments a
+//   word 1: number of outputs o | (has_slot << 15)
+//   [slot]               if has_slot
+//   out_0 .. out_{o-1}   output strip indices
+//   arg_0 .. arg_{a-1}   operand ids: < n_in input strip, else slot + n_in
+// `sched` keeps the scheduled fused program for code generation.
+struct Program {
+  int n_in = 0, n_out = 0, n_slots = 0, n_stmts = 0;
+  std::vector<uint16_t> code;
+  PipelineStats stats;
+  Slp fused;                 // single-assignment fused program
+  Schedule sched;            // GPU schedule of `fused`
+  uint64_t hash = 0;         // content hash of the fused program
+  // device copy of `code` (owned; freed by the plan)
+  uint16_t* d_code = nullptr;
+  // compiled tier (set once a straight-line kernel exists for this program)
+  void* jit = nullptr;
+};
+
+struct PlanOptions {
+  int opt_level = kOptXorRePair;
+  int sched = kSchedDfs;
+  int greedy_cap = 128;
+  bool cancel_pairs = true;
+};
+
+// Build the program for the linear map A (rows x cols over GF(2^8)).
+bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
+                   Program* out, std::string* err);
+
+}  // namespace xorec

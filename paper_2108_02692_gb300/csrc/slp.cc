@@ -1,0 +1,699 @@
+#include "slp.h"
+
+#include <algorithm>
+#include <functional>
+#include <list>
+#include <map>
+#include <sstream>
+#include <unordered_map>
+
+namespace xorec {
+
+// ------------------------------------------------------------------ Bits
+
+int Bits::count() const {
+  int c = 0;
+  for (uint64_t x : w) c += __builtin_popcountll(x);
+  return c;
+}
+int Bits::xor_count(const Bits& o) const {
+  int c = 0;
+  for (size_t i = 0; i < w.size(); ++i) c += __builtin_popcountll(w[i] ^ o.w[i]);
+  return c;
+}
+int Bits::and_count(const Bits& o) const {
+  int c = 0;
+  for (size_t i = 0; i < w.size(); ++i) c += __builtin_popcountll(w[i] & o.w[i]);
+  return c;
+}
+Bits& Bits::operator^=(const Bits& o) {
+  for (size_t i = 0; i < w.size(); ++i) w[i] ^= o.w[i];
+  return *this;
+}
+bool Bits::any() const {
+  for (uint64_t x : w)
+    if (x) return true;
+  return false;
+}
+
+// ------------------------------------------------------ semantics, metrics
+
+std::vector<Bits> semantics(const Slp& p) {
+  std::vector<Bits> val(p.n_var, Bits(p.n_const));
+  auto value_of = [&](int t) {
+    if (p.is_const(t)) {
+      Bits b(p.n_const);
+      b.set(t);
+      return b;
+    }
+    return val[t - p.n_const];
+  };
+  for (const Stmt& s : p.body) {
+    Bits acc(p.n_const);
+    for (int a : s.args) acc ^= value_of(a);
+    val[s.dst - p.n_const] = acc;
+  }
+  std::vector<Bits> out;
+  out.reserve(p.ret.size());
+  for (int r : p.ret) out.push_back(r < 0 ? Bits(p.n_const) : value_of(r));
+  return out;
+}
+
+bool equivalent(const Slp& a, const Slp& b) {
+  if (a.n_const != b.n_const) return false;
+  return semantics(a) == semantics(b);
+}
+
+SlpMetrics metrics(const Slp& p) {
+  SlpMetrics m{0, 0, 0, 0};
+  std::vector<char> seen(p.n_var, 0);
+  for (const Stmt& s : p.body) {
+    const long n = static_cast<long>(s.args.size());
+    m.xors += n > 0 ? n - 1 : 0;
+    m.mem += n + 1;
+    m.stmts += 1;
+    if (!seen[s.dst - p.n_const]) {
+      seen[s.dst - p.n_const] = 1;
+      m.nvar += 1;
+    }
+  }
+  return m;
+}
+
+// ------------------------------------------------------------- LRU cache
+
+namespace {
+
+struct Lru {
+  int cap;
+  std::list<int> order;  // front = least recently used
+  std::unordered_map<int, std::list<int>::iterator> pos;
+  std::vector<char> evicted;
+  long io = 0, reloads = 0;
+  Lru(int c, int universe) : cap(c), evicted(universe, 0) {}
+  bool has(int x) const { return pos.count(x) != 0; }
+  void touch(int x) {
+    order.erase(pos[x]);
+    order.push_back(x);
+    pos[x] = std::prev(order.end());
+  }
+  void make_room() {
+    if (static_cast<int>(order.size()) >= cap && !order.empty()) {
+      const int v = order.front();
+      order.pop_front();
+      pos.erase(v);
+      evicted[v] = 1;
+      ++io;
+    }
+  }
+  void insert(int x) {
+    order.push_back(x);
+    pos[x] = std::prev(order.end());
+  }
+  // Argument access: load on miss.
+  void use(int x) {
+    if (has(x)) {
+      touch(x);
+      return;
+    }
+    make_room();
+    ++io;
+    if (evicted[x]) ++reloads;
+    insert(x);
+  }
+  // Destination: allocate on miss (no transfer), else update position.
+  void def(int x) {
+    if (has(x)) {
+      touch(x);
+      return;
+    }
+    make_room();
+    insert(x);
+  }
+};
+
+}  // namespace
+
+long lru_iocost(const Slp& p, int cap, long* reloads) {
+  Lru c(cap, p.n_const + p.n_var);
+  for (const Stmt& s : p.body) {
+    for (int a : s.args) c.use(a);
+    c.def(s.dst);
+  }
+  if (reloads) *reloads = c.reloads;
+  return c.io;
+}
+
+int ccap(const Slp& p) {
+  const int hi = p.n_const + p.n_var + 1;
+  for (int cap = 1; cap <= hi; ++cap) {
+    long rel = 0;
+    lru_iocost(p, cap, &rel);
+    if (rel == 0) return cap;
+  }
+  return hi;
+}
+
+// --------------------------------------------------------------- text I/O
+
+bool parse_slp(const std::string& text, Slp* out, std::string* err) {
+  Slp p;
+  std::map<std::string, int> cid, vid;
+  std::vector<std::pair<std::string, std::vector<std::string>>> stmts;
+  std::vector<std::string> ret;
+  std::istringstream in(text);
+  std::string line;
+  while (std::getline(in, line)) {
+    for (char& ch : line)
+      if (ch == ';' || ch == ',' || ch == '(' || ch == ')' || ch == '^' || ch == '+') ch = ' ';
+    std::istringstream ls(line);
+    std::vector<std::string> tok;
+    std::string t;
+    while (ls >> t) tok.push_back(t);
+    if (tok.empty() || tok[0][0] == '#') continue;
+    if (tok[0] == "const") {
+      for (size_t i = 1; i < tok.size(); ++i) {
+        if (cid.count(tok[i])) { *err = "duplicate constant " + tok[i]; return false; }
+        const int id = static_cast<int>(cid.size());
+        cid[tok[i]] = id;
+        p.const_names.push_back(tok[i]);
+      }
+    } else if (tok[0] == "ret") {
+      ret.assign(tok.begin() + 1, tok.end());
+    } else {
+      if (tok.size() < 2 || (tok[1] != "=" && tok[1] != "<-")) {
+        *err = "bad statement: " + line;
+        return false;
+      }
+      std::vector<std::string> args(tok.begin() + 2, tok.end());
+      if (!args.empty() && args[0] == "xor") args.erase(args.begin());
+      stmts.emplace_back(tok[0], args);
+    }
+  }
+  p.n_const = static_cast<int>(cid.size());
+  for (auto& st : stmts) {
+    if (cid.count(st.first)) { *err = "assignment to constant " + st.first; return false; }
+    if (!vid.count(st.first)) {
+      const int id = static_cast<int>(vid.size());
+      vid[st.first] = id;
+      p.var_names.push_back(st.first);
+    }
+  }
+  p.n_var = static_cast<int>(vid.size());
+  auto term = [&](const std::string& s, int* t) {
+    if (cid.count(s)) { *t = cid[s]; return true; }
+    if (vid.count(s)) { *t = p.n_const + vid[s]; return true; }
+    if (s == "0") { *t = -1; return true; }
+    *err = "unknown name " + s;
+    return false;
+  };
+  for (auto& st : stmts) {
+    Stmt s;
+    s.dst = p.n_const + vid[st.first];
+    for (auto& a : st.second) {
+      int t;
+      if (!term(a, &t) || t < 0) { if (err->empty()) *err = "bad argument"; return false; }
+      s.args.push_back(t);
+    }
+    p.body.push_back(s);
+  }
+  for (auto& r : ret) {
+    int t;
+    if (!term(r, &t)) return false;
+    p.ret.push_back(t);
+  }
+  *out = p;
+  return true;
+}
+
+std::string slp_to_text(const Slp& p) {
+  auto name = [&](int t) -> std::string {
+    if (t < 0) return "0";
+    if (p.is_const(t))
+      return t < static_cast<int>(p.const_names.size()) ? p.const_names[t] : "c" + std::to_string(t);
+    const int v = t - p.n_const;
+    return v < static_cast<int>(p.var_names.size()) ? p.var_names[v] : "v" + std::to_string(v);
+  };
+  std::ostringstream os;
+  os << "const";
+  for (int c = 0; c < p.n_const; ++c) os << ' ' << name(c);
+  os << '\n';
+  for (const Stmt& s : p.body) {
+    os << name(s.dst) << " =";
+    for (int a : s.args) os << ' ' << name(a);
+    os << '\n';
+  }
+  os << "ret";
+  for (int r : p.ret) os << ' ' << name(r);
+  os << '\n';
+  return os.str();
+}
+
+// ------------------------------------------------------- raw programs
+
+Slp slp_rows_fused(int n_const, const std::vector<Bits>& rows,
+                   const std::vector<int>& row_order) {
+  Slp p;
+  p.n_const = n_const;
+  p.n_var = static_cast<int>(rows.size());
+  p.ret.assign(rows.size(), -1);
+  for (int r : row_order) {
+    Stmt s;
+    s.dst = n_const + r;
+    for (int c = 0; c < n_const; ++c)
+      if (rows[r].test(c)) s.args.push_back(c);
+    if (s.args.empty()) continue;      // zero row: returns the zero array
+    p.ret[r] = s.dst;
+    p.body.push_back(s);
+  }
+  return p;
+}
+
+Slp slp_rows_chains(int n_const, const std::vector<Bits>& rows,
+                    const std::vector<int>& row_order) {
+  Slp p;
+  p.n_const = n_const;
+  p.n_var = static_cast<int>(rows.size());
+  p.ret.assign(rows.size(), -1);
+  for (int r : row_order) {
+    std::vector<int> cols;
+    for (int c = 0; c < n_const; ++c)
+      if (rows[r].test(c)) cols.push_back(c);
+    if (cols.empty()) continue;
+    const int v = n_const + r;
+    p.ret[r] = v;
+    if (cols.size() == 1) {
+      p.body.push_back(Stmt{v, {cols[0]}});
+      continue;
+    }
+    p.body.push_back(Stmt{v, {cols[0], cols[1]}});
+    for (size_t i = 2; i < cols.size(); ++i) p.body.push_back(Stmt{v, {v, cols[i]}});
+  }
+  return p;
+}
+
+// --------------------------------------------------- RePair / XorRePair
+
+namespace {
+
+// Term order (Sec. 4.3): temporals in generation order precede constants;
+// constants are in index order.  Term ids: constant c -> c, temporal i ->
+// n_const + i.
+struct Ranker {
+  int nc;
+  long rank(int t) const { return t < nc ? (1L << 40) + t : static_cast<long>(t - nc); }
+};
+
+}  // namespace
+
+Slp repair(const Slp& in, bool xor_cancel) {
+  const int nc = in.n_const;
+  const Ranker rk{nc};
+  const std::vector<Bits> goal = semantics(in);
+  const int n_orig = static_cast<int>(goal.size());
+
+  std::vector<std::vector<int>> def(n_orig);   // current definitions
+  std::vector<char> active(n_orig, 0);
+  for (int o = 0; o < n_orig; ++o) {
+    for (int c = 0; c < nc; ++c)
+      if (goal[o].test(c)) def[o].push_back(c);
+    active[o] = def[o].size() >= 2;
+  }
+  std::vector<std::pair<int, int>> tdef;       // temporal definitions
+  std::vector<Bits> tval;                      // their values
+  std::vector<Bits> occ;                       // term -> active originals containing it
+  auto ensure_occ = [&](int t) {
+    if (static_cast<int>(occ.size()) <= t) occ.resize(t + 1, Bits(n_orig));
+  };
+  auto value_of = [&](int t) {
+    if (t < nc) {
+      Bits b(nc);
+      b.set(t);
+      return b;
+    }
+    return tval[t - nc];
+  };
+  auto sort_def = [&](std::vector<int>& d) {
+    std::sort(d.begin(), d.end(), [&](int a, int b) { return rk.rank(a) < rk.rank(b); });
+  };
+  auto attach = [&](int o) {
+    for (int t : def[o]) { ensure_occ(t); occ[t].set(o); }
+  };
+  auto detach = [&](int o) {
+    for (int t : def[o]) { ensure_occ(t); if (occ[t].test(o)) occ[t].flip(o); }
+  };
+  for (int o = 0; o < n_orig; ++o)
+    if (active[o]) attach(o);
+
+  // Rebuild(v): greedily XOR existing temporals into rem = [[v]] while that
+  // shrinks rem; ties go to the earliest temporal (Sec. 4.4).
+  auto rebuild = [&](int o) {
+    Bits rem = goal[o];
+    int rem_size = rem.count();
+    std::vector<char> in_s(tdef.size(), 0);
+    for (;;) {
+      int best = -1, best_size = rem_size;
+      for (size_t t = 0; t < tval.size(); ++t) {
+        const int sz = rem.xor_count(tval[t]);
+        if (sz < best_size) { best_size = sz; best = static_cast<int>(t); }
+      }
+      if (best < 0) break;
+      rem ^= tval[best];
+      rem_size = best_size;
+      in_s[best] ^= 1;
+    }
+    std::vector<int> d;
+    for (size_t t = 0; t < in_s.size(); ++t)
+      if (in_s[t]) d.push_back(nc + static_cast<int>(t));
+    for (int c = 0; c < nc; ++c)
+      if (rem.test(c)) d.push_back(c);
+    sort_def(d);
+    return d;
+  };
+
+  for (;;) {
+    bool any = false;
+    for (int o = 0; o < n_orig; ++o) any |= active[o] != 0;
+    if (!any) break;
+    // Terms present in active definitions, in term order.
+    std::vector<int> present;
+    for (int t = 0; t < static_cast<int>(occ.size()); ++t)
+      if (occ[t].any()) present.push_back(t);
+    std::sort(present.begin(), present.end(),
+              [&](int a, int b) { return rk.rank(a) < rk.rank(b); });
+    // Most frequent pair; the first maximum in lexicographic order wins.
+    int bx = -1, by = -1, bf = 0;
+    for (size_t i = 0; i < present.size(); ++i)
+      for (size_t j = i + 1; j < present.size(); ++j) {
+        const int f = occ[present[i]].and_count(occ[present[j]]);
+        if (f > bf) { bf = f; bx = present[i]; by = present[j]; }
+      }
+    if (bx < 0) break;  // cannot happen: an active definition has >= 2 terms
+    // Pair(bx, by)
+    const int t = nc + static_cast<int>(tdef.size());
+    tdef.emplace_back(bx, by);
+    Bits v = value_of(bx);
+    v ^= value_of(by);
+    tval.push_back(v);
+    ensure_occ(t);
+    Bits both = occ[bx];
+    for (size_t i = 0; i < both.w.size(); ++i) both.w[i] &= occ[by].w[i];
+    for (int o = 0; o < n_orig; ++o) {
+      if (!both.test(o)) continue;
+      detach(o);
+      std::vector<int> nd;
+      for (int x : def[o])
+        if (x != bx && x != by) nd.push_back(x);
+      nd.push_back(t);
+      sort_def(nd);
+      def[o] = nd;
+      active[o] = def[o].size() >= 2;
+      if (active[o]) attach(o);
+    }
+    if (xor_cancel) {
+      for (int o = 0; o < n_orig; ++o) {
+        if (!active[o]) continue;
+        std::vector<int> nd = rebuild(o);
+        if (nd.size() < def[o].size()) {
+          detach(o);
+          def[o] = nd;
+          active[o] = def[o].size() >= 2;
+          if (active[o]) attach(o);
+        }
+      }
+    }
+  }
+
+  Slp out;
+  out.n_const = nc;
+  out.const_names = in.const_names;
+  out.n_var = static_cast<int>(tdef.size());
+  for (size_t i = 0; i < tdef.size(); ++i) {
+    out.body.push_back(Stmt{nc + static_cast<int>(i), {tdef[i].first, tdef[i].second}});
+    out.var_names.push_back("t" + std::to_string(i + 1));
+  }
+  out.ret.resize(n_orig);
+  for (int o = 0; o < n_orig; ++o) out.ret[o] = def[o].empty() ? -1 : def[o][0];
+  return out;
+}
+
+// ------------------------------------------------------------ XOR fusion
+
+Slp fuse(const Slp& p, bool cancel_pairs) {
+  const int nc = p.n_const;
+  std::vector<int> def_idx(p.n_var, -1);
+  for (size_t i = 0; i < p.body.size(); ++i) def_idx[p.body[i].dst - nc] = static_cast<int>(i);
+  // Live variables: reachable from the returned terms.
+  std::vector<char> live(p.n_var, 0), in_ret(p.n_var, 0);
+  std::vector<int> stack;
+  for (int r : p.ret)
+    if (r >= nc) {
+      in_ret[r - nc] = 1;
+      if (!live[r - nc]) { live[r - nc] = 1; stack.push_back(r - nc); }
+    }
+  while (!stack.empty()) {
+    const int v = stack.back();
+    stack.pop_back();
+    for (int a : p.body[def_idx[v]].args)
+      if (a >= nc && !live[a - nc]) { live[a - nc] = 1; stack.push_back(a - nc); }
+  }
+  std::vector<int> uses(p.n_var, 0);
+  for (const Stmt& s : p.body)
+    if (live[s.dst - nc])
+      for (int a : s.args)
+        if (a >= nc) uses[a - nc] += 1;
+  for (int r : p.ret)
+    if (r >= nc) uses[r - nc] += 1;
+  std::vector<char> keep(p.n_var, 0);
+  for (int v = 0; v < p.n_var; ++v) keep[v] = live[v] && (uses[v] != 1 || in_ret[v]);
+
+  std::function<void(int, std::vector<int>&)> expand = [&](int t, std::vector<int>& out) {
+    if (t < nc || keep[t - nc]) { out.push_back(t); return; }
+    for (int a : p.body[def_idx[t - nc]].args) expand(a, out);
+  };
+  Slp q;
+  q.n_const = nc;
+  q.n_var = p.n_var;
+  q.const_names = p.const_names;
+  q.var_names = p.var_names;
+  q.ret = p.ret;
+  for (const Stmt& s : p.body) {
+    if (!keep[s.dst - nc]) continue;
+    std::vector<int> args;
+    for (int a : s.args) expand(a, args);
+    if (cancel_pairs) {
+      std::unordered_map<int, int> cnt;
+      for (int a : args) cnt[a] += 1;
+      std::vector<int> kept;
+      for (int a : args) {
+        auto it = cnt.find(a);
+        if (it != cnt.end() && (it->second & 1)) kept.push_back(a);
+        if (it != cnt.end()) cnt.erase(it);
+      }
+      args.swap(kept);
+    }
+    q.body.push_back(Stmt{s.dst, args});
+  }
+  return q;
+}
+
+// ------------------------------------------------------- pebble schedules
+
+namespace {
+
+struct Graph {
+  int nc = 0;
+  int nv = 0;
+  std::vector<int> def_idx;              // var -> statement
+  std::vector<std::vector<int>> kids;    // var -> ordered children (terms)
+  std::vector<int> n_parents;            // distinct parent statements
+  std::vector<char> goal;
+};
+
+Graph build_graph(const Slp& p) {
+  Graph g;
+  g.nc = p.n_const;
+  g.nv = p.n_var;
+  g.def_idx.assign(p.n_var, -1);
+  g.kids.assign(p.n_var, {});
+  g.n_parents.assign(p.n_var, 0);
+  g.goal.assign(p.n_var, 0);
+  for (size_t i = 0; i < p.body.size(); ++i) {
+    const int v = p.body[i].dst - p.n_const;
+    g.def_idx[v] = static_cast<int>(i);
+    std::vector<int> k = p.body[i].args;
+    // children in term order: variables (generation order) then constants
+    std::stable_sort(k.begin(), k.end(), [&](int a, int b) {
+      const bool va = a >= p.n_const, vb = b >= p.n_const;
+      if (va != vb) return va;
+      return a < b;
+    });
+    g.kids[v] = k;
+    std::vector<int> seen;
+    for (int a : k)
+      if (a >= p.n_const && std::find(seen.begin(), seen.end(), a) == seen.end()) {
+        seen.push_back(a);
+        g.n_parents[a - p.n_const] += 1;
+      }
+  }
+  for (int r : p.ret)
+    if (r >= p.n_const) g.goal[r - p.n_const] = 1;
+  return g;
+}
+
+std::vector<int> distinct_vars(const std::vector<int>& args, int nc) {
+  std::vector<int> out;
+  for (int a : args)
+    if (a >= nc && std::find(out.begin(), out.end(), a) == out.end()) out.push_back(a);
+  return out;
+}
+
+}  // namespace
+
+Schedule schedule_dfs(const Slp& p, bool goals_hold) {
+  Graph g = build_graph(p);
+  const int nc = g.nc;
+  std::vector<int> order;
+  std::vector<char> visited(g.nv, 0);
+  std::function<void(int)> visit = [&](int v) {
+    if (visited[v]) return;
+    visited[v] = 1;
+    for (int a : g.kids[v])
+      if (a >= nc) visit(a - nc);
+    order.push_back(v);
+  };
+  for (int v = 0; v < g.nv; ++v)  // roots in term order
+    if (g.def_idx[v] >= 0 && g.n_parents[v] == 0) visit(v);
+
+  Schedule s;
+  std::vector<int> remaining = g.n_parents, pebble(g.nv, -1), when(g.nv, -1);
+  std::vector<std::pair<int, int>> free_list;  // (time its node was computed, pebble)
+  for (size_t i = 0; i < order.size(); ++i) {
+    const int n = order[i];
+    // children whose last parent is n give their pebble back
+    for (int c : distinct_vars(g.kids[n], nc)) {
+      const int cv = c - nc;
+      if (--remaining[cv] == 0 && !(g.goal[cv] && goals_hold) && pebble[cv] >= 0)
+        free_list.emplace_back(when[cv], pebble[cv]);
+    }
+    int peb = -1;
+    const bool needs = goals_hold ? true : (g.n_parents[n] > 0);
+    if (needs) {
+      if (!free_list.empty()) {
+        // reuse the pebble of the most recently computed dead node
+        auto it = std::max_element(free_list.begin(), free_list.end());
+        peb = it->second;
+        free_list.erase(it);
+      } else {
+        peb = s.n_pebbles++;
+      }
+    }
+    pebble[n] = peb;
+    when[n] = static_cast<int>(i);
+    s.steps.push_back(Schedule::Step{n, peb, g.kids[n]});
+  }
+  return s;
+}
+
+Schedule schedule_greedy(const Slp& p, int cap, bool goals_hold) {
+  Graph g = build_graph(p);
+  const int nc = g.nc;
+  // The cache holds constants (ids [0,nc)) and pebbles (ids nc + pebble).
+  Lru cache(cap, nc + g.nv + 1);
+  std::vector<int> remaining = g.n_parents, pebble(g.nv, -1), kids_left(g.nv, 0);
+  std::vector<char> done(g.nv, 0);
+  int total = 0;
+  for (int v = 0; v < g.nv; ++v)
+    if (g.def_idx[v] >= 0) {
+      ++total;
+      kids_left[v] = static_cast<int>(distinct_vars(g.kids[v], nc).size());
+    }
+  std::vector<int> parents_of_count;
+  std::vector<std::vector<int>> parents(g.nv);
+  for (int v = 0; v < g.nv; ++v)
+    if (g.def_idx[v] >= 0)
+      for (int c : distinct_vars(g.kids[v], nc)) parents[c - nc].push_back(v);
+  std::vector<int> free_peb;  // pebbles of dead nodes: (node id) owners
+  std::vector<int> owner;     // pebble -> node currently on it
+  Schedule s;
+  auto block_of = [&](int t) { return t < nc ? t : nc + pebble[t - nc]; };
+  for (int step = 0; step < total; ++step) {
+    int best = -1;
+    long bh = -1, bc = 1;
+    for (int v = 0; v < g.nv; ++v) {
+      if (g.def_idx[v] < 0 || done[v] || kids_left[v] != 0) continue;
+      std::vector<int> C;
+      for (int a : g.kids[v])
+        if (std::find(C.begin(), C.end(), a) == C.end()) C.push_back(a);
+      long h = 0;
+      for (int a : C) h += cache.has(block_of(a)) ? 1 : 0;
+      const long c = C.empty() ? 1 : static_cast<long>(C.size());
+      if (C.empty()) h = 1;
+      if (best < 0 || h * bc > bh * c) { best = v; bh = h; bc = c; }
+    }
+    const int n = best;
+    std::vector<int> C, H, M;
+    for (int a : g.kids[n])
+      if (std::find(C.begin(), C.end(), a) == C.end()) C.push_back(a);
+    for (int a : C) (cache.has(block_of(a)) ? H : M).push_back(a);
+    for (int a : H) cache.use(block_of(a));
+    for (int a : M) cache.use(block_of(a));
+    std::vector<int> args = H;
+    args.insert(args.end(), M.begin(), M.end());
+    // children whose last parent is n become movable
+    for (int c : distinct_vars(g.kids[n], nc)) {
+      const int cv = c - nc;
+      if (--remaining[cv] == 0 && !(g.goal[cv] && goals_hold) && pebble[cv] >= 0)
+        free_peb.push_back(cv);
+    }
+    int peb = -1;
+    const bool needs = goals_hold ? true : (g.n_parents[n] > 0);
+    if (needs) {
+      // prefer a movable pebble that is cached, then any movable one; ties by
+      // node order; else a fresh pebble
+      int pick = -1;
+      for (int pass = 0; pass < 2 && pick < 0; ++pass) {
+        int bestv = -1;
+        for (int v : free_peb) {
+          if (pass == 0 && !cache.has(nc + pebble[v])) continue;
+          if (bestv < 0 || v < bestv) bestv = v;
+        }
+        pick = bestv;
+      }
+      if (pick >= 0) {
+        peb = pebble[pick];
+        free_peb.erase(std::find(free_peb.begin(), free_peb.end(), pick));
+      } else {
+        peb = s.n_pebbles++;
+      }
+    }
+    pebble[n] = peb;
+    if (peb >= 0) cache.def(nc + peb);
+    done[n] = 1;
+    for (int par : parents[n]) kids_left[par] -= 1;
+    // map args to input ids (constants or variable ids of p)
+    s.steps.push_back(Schedule::Step{n, peb, args});
+  }
+  return s;
+}
+
+Slp schedule_to_slp(const Slp& p, const Schedule& s) {
+  const int nc = p.n_const;
+  Slp q;
+  q.n_const = nc;
+  q.const_names = p.const_names;
+  q.n_var = s.n_pebbles;
+  for (int i = 0; i < s.n_pebbles; ++i) q.var_names.push_back("p" + std::to_string(i + 1));
+  std::vector<int> pebble(p.n_var, -1);
+  for (const auto& st : s.steps) {
+    Stmt x;
+    x.dst = nc + st.pebble;
+    for (int a : st.args) x.args.push_back(a < nc ? a : nc + pebble[a - nc]);
+    pebble[st.node] = st.pebble;
+    q.body.push_back(x);
+  }
+  for (int r : p.ret) q.ret.push_back(r < nc ? r : nc + pebble[r - nc]);
+  return q;
+}
+
+}  // namespace xorec

@@ -1,0 +1,119 @@
+// Straight-line programs over XOR and the optimiser passes of the paper,
+// retargeted to a GPU executor (host side).
+//
+//   SLP / MultiSLP and set semantics ........ Sec. 4.1, Sec. 5.1
+//   RePair, XorRePair (Rebuild) .............. Sec. 4.3, Sec. 4.4
+//   XOR fusion (deforestation) ............... Sec. 5.2
+//   abstract LRU cache, CCap, IOcost ......... Sec. 6.2
+//   pebble game, DFS and greedy schedulers ... Sec. 6.4, Sec. 6.6
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace xorec {
+
+// Growable bitset used for set semantics (sets of constants) and for
+// "which originals contain this term" indices.
+struct Bits {
+  std::vector<uint64_t> w;
+  Bits() = default;
+  explicit Bits(int n) : w((n + 63) / 64, 0) {}
+  void set(int i) { w[i >> 6] |= (1ull << (i & 63)); }
+  void flip(int i) { w[i >> 6] ^= (1ull << (i & 63)); }
+  bool test(int i) const { return (w[i >> 6] >> (i & 63)) & 1ull; }
+  int count() const;
+  int xor_count(const Bits& o) const;   // |this (+) o|
+  int and_count(const Bits& o) const;   // |this & o|
+  Bits& operator^=(const Bits& o);
+  bool operator==(const Bits& o) const { return w == o.w; }
+  bool any() const;
+};
+
+// A statement dst <- XOR(args).  Terms are ints: constants are
+// [0, n_const), variables are [n_const, n_const + n_var).  A variable may
+// be assigned more than once (register-allocated programs such as P_reg or
+// pebble strategies); RePair and fusion require single assignment.
+struct Stmt {
+  int dst;
+  std::vector<int> args;
+};
+
+struct Slp {
+  int n_const = 0;
+  int n_var = 0;
+  std::vector<Stmt> body;
+  std::vector<int> ret;   // returned terms; -1 = the zero array
+  std::vector<std::string> const_names;
+  std::vector<std::string> var_names;
+  bool is_const(int t) const { return t >= 0 && t < n_const; }
+};
+
+struct SlpMetrics {
+  long xors;   // sum over statements of (arity - 1)                [Sec. 4.1]
+  long mem;    // #_M: sum over statements of (arity + 1)            [Sec. 5.1]
+  int nvar;    // number of distinct assigned variables              [Sec. 4.1]
+  int stmts;   // number of statements (the paper's #XOR after fusion)
+};
+
+// Set semantics: the value of each returned term as a set of constants.
+std::vector<Bits> semantics(const Slp& p);
+bool equivalent(const Slp& a, const Slp& b);
+SlpMetrics metrics(const Slp& p);
+
+// Abstract LRU cache (Sec. 6.2): for each statement, access the arguments
+// in order (load on miss, else move to most-recent), then allocate or
+// update the destination; evict the least recently used element when full.
+// IOcost = loads + evictions.  reloads counts loads of evicted elements.
+long lru_iocost(const Slp& p, int cap, long* reloads = nullptr);
+// CCap: minimum capacity with no reload.
+int ccap(const Slp& p);
+
+// Text form (for the paper's worked examples and debugging):
+//   const a b c d
+//   v1 = a b
+//   v2 = b c d
+//   ret v2 v3 v1
+bool parse_slp(const std::string& text, Slp* out, std::string* err);
+std::string slp_to_text(const Slp& p);
+
+// One statement per row: v_r <- XOR(columns set in row r), in column order.
+Slp slp_rows_fused(int n_const, const std::vector<Bits>& rows,
+                   const std::vector<int>& row_order);
+// Binary left-to-right chains per row (v <- c1 + c2; v <- v + c3; ...),
+// the unoptimised program whose counts the paper prints (Sec. 7.5).
+Slp slp_rows_chains(int n_const, const std::vector<Bits>& rows,
+                    const std::vector<int>& row_order);
+
+// RePair (xor_cancel = false) or XorRePair (true) on the flattened
+// semantics of p.  Returns a single-assignment program of binary
+// temporals; returned terms become the temporal, constant or zero that
+// each original reduces to (Sec. 4.3, Sec. 4.4).
+Slp repair(const Slp& p, bool xor_cancel);
+
+// XOR fusion: repeatedly unfold variables used exactly once into their
+// user; dead variables are dropped.  cancel_pairs removes arguments that
+// occur twice in one fused statement (x + x = 0).  Requires single
+// assignment (Sec. 5.2).
+Slp fuse(const Slp& p, bool cancel_pairs);
+
+// Pebble-game schedules of a single-assignment MultiSLP (Sec. 6.4, 6.6).
+// goals_hold: goal nodes keep their pebble to the end (the paper's game);
+// otherwise a goal's pebble is freed after its last use, which is the GPU
+// setting where outputs stream to memory as soon as they are computed.
+struct Schedule {
+  struct Step {
+    int node;                 // variable id in the input program
+    int pebble;               // pebble (register or slot) receiving it
+    std::vector<int> args;    // constants, or variable ids of the input
+  };
+  std::vector<Step> steps;
+  int n_pebbles = 0;
+};
+Schedule schedule_dfs(const Slp& p, bool goals_hold);
+Schedule schedule_greedy(const Slp& p, int cap, bool goals_hold);
+// The program of a schedule, with variables renamed to pebbles.  Requires
+// goals_hold schedules so that returned values are still on their pebble.
+Slp schedule_to_slp(const Slp& p, const Schedule& s);
+
+}  // namespace xorec

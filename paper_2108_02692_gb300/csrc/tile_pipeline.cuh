@@ -1,0 +1,195 @@
+// Device-side tile pipeline shared by the SLP interpreter (compiled into the
+// library) and the straight-line SLP kernels compiled per plan at run time.
+// This header includes nothing so that it compiles both under nvcc and NVRTC.
+//
+// Work decomposition (blocking, Sec. 6.1, retargeted): every stripe's strips
+// are cut into tiles of T bytes; one work item = (stripe, tile).  A CTA walks
+// items blockIdx.x, blockIdx.x + gridDim.x, ...; for each item one warp
+// issues one 1-D bulk copy (cp.async.bulk, TMA) per input strip into a shared
+// memory stage, completion is tracked by an mbarrier with a transaction
+// count, and every thread then runs the XOR program on its own 4-byte column
+// of the tile.  `nstage` stages form a ring so that the copies of the next
+// items overlap the computation of the current one.  Every input byte is
+// read from HBM once and every output byte written once.
+//
+// Waits are bounded: an mbarrier wait that exceeds ~2 s of %globaltimer sets
+// the status word to XK_STATUS_TIMEOUT, waits (bounded again) for the CTA's
+// copies still in flight and returns.
+#pragma once
+
+namespace xk {
+
+typedef unsigned char u8;
+typedef unsigned short u16;
+typedef unsigned int u32;
+typedef unsigned long long u64;
+typedef long long i64;
+
+enum { XK_STATUS_OK = 0, XK_STATUS_TIMEOUT = 1 };
+
+// Block addressing for a launch.  Either a device table with, per stripe,
+// n_inblk input block addresses followed by n_outblk output block
+// addresses, or (tab == 0) strided bases.
+struct IoDesc {
+  const u64* tab;
+  const u8* in_base;
+  i64 in_sstride, in_bstride;
+  u8* out_base;
+  i64 out_sstride, out_bstride;
+  int n_inblk, n_outblk;
+  i64 S;          // strip bytes (block bytes / 8)
+  i64 n_stripes;
+};
+
+struct LaunchParams {
+  IoDesc io;
+  int n_in, n_out;       // input / output strips (8 per block)
+  int T;                 // tile bytes per strip (multiple of 16)
+  int nstage;            // stages in the shared-memory ring
+  i64 tiles_per_strip;
+  i64 n_items;
+  const u16* code;       // interpreter stream (unused by compiled kernels)
+  int code_len;
+  int n_slots;
+  int* status;
+};
+
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+
+__device__ __forceinline__ const u8* in_block(const IoDesc& io, i64 s, int b) {
+  if (io.tab) return reinterpret_cast<const u8*>(io.tab[s * (io.n_inblk + io.n_outblk) + b]);
+  return io.in_base + s * io.in_sstride + b * io.in_bstride;
+}
+
+__device__ __forceinline__ u8* out_block(const IoDesc& io, i64 s, int b) {
+  if (io.tab)
+    return reinterpret_cast<u8*>(io.tab[s * (io.n_inblk + io.n_outblk) + io.n_inblk + b]);
+  return io.out_base + s * io.out_sstride + b * io.out_bstride;
+}
+
+__device__ __forceinline__ u32 smem_addr(const void* p) {
+  u32 r;
+  asm("{ .reg .u64 t; cvta.to.shared.u64 t, %1; cvt.u32.u64 %0, t; }" : "=r"(r) : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ u64 now_ns() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(u32 bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(u32 bar, u32 bytes) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }"
+               ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(u32 dst, const void* src, u32 bytes, u32 bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u32 bar, u32 parity) {
+  u32 ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase with `parity` completed, false after
+// about two seconds.
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const u64 t0 = now_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (now_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+// Warp 0 issues the copies of one work item into stage `dst`.
+__device__ __forceinline__ void issue_item(const LaunchParams& p, i64 item, u8* dst, u32 bar) {
+  const i64 s = item / p.tiles_per_strip;
+  const i64 c0 = (item % p.tiles_per_strip) * p.T;
+  const i64 rest = p.io.S - c0;
+  const int len = rest < p.T ? static_cast<int>(rest) : p.T;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(p.n_in) * static_cast<u32>(len));
+  __syncwarp();
+  for (int c = lane; c < p.n_in; c += 32) {
+    const u8* src = in_block(p.io, s, c >> 3) + static_cast<i64>(c & 7) * p.io.S + c0;
+    tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), src, static_cast<u32>(len), bar);
+  }
+}
+
+// Shared memory: [mbarriers, 128 B][nstage stages of n_in * T][slots].
+// Body: void operator()(const LaunchParams&, i64 stripe, i64 c0, int len,
+//                       const u8* stage, u8* slots) const
+template <class Body>
+__device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, const Body& body) {
+  u64* bars = reinterpret_cast<u64*>(smem);
+  u8* stages = smem + 128;
+  const i64 stage_bytes = static_cast<i64>(p.n_in) * p.T;
+  u8* slots = stages + p.nstage * stage_bytes;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < p.nstage; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const i64 first = blockIdx.x, step = gridDim.x;
+  if (tid < 32) {
+    for (int s = 0; s < p.nstage; ++s) {
+      const i64 it = first + s * step;
+      if (it < p.n_items) issue_item(p, it, stages + s * stage_bytes, smem_addr(&bars[s]));
+    }
+  }
+  for (i64 i = 0;; ++i) {
+    const i64 item = first + i * step;
+    if (item >= p.n_items) break;
+    const int st = static_cast<int>(i % p.nstage);
+    const u32 par = static_cast<u32>((i / p.nstage) & 1);
+    const bool ok = mbar_wait(smem_addr(&bars[st]), par);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(p.status, XK_STATUS_TIMEOUT);
+        for (int d = 0; d < p.nstage; ++d) {
+          const i64 j = i + d;
+          if (first + j * step < p.n_items)
+            mbar_wait(smem_addr(&bars[j % p.nstage]), static_cast<u32>((j / p.nstage) & 1));
+        }
+      }
+      return;
+    }
+    const i64 s = item / p.tiles_per_strip;
+    const i64 c0 = (item % p.tiles_per_strip) * p.T;
+    const i64 rest = p.io.S - c0;
+    const int len = rest < p.T ? static_cast<int>(rest) : p.T;
+    body(p, s, c0, len, stages + st * stage_bytes, slots);
+    __syncthreads();
+    const i64 nxt = item + p.nstage * step;
+    if (tid < 32 && nxt < p.n_items) {
+      if (tid == 0) fence_proxy_async();
+      __syncwarp();
+      issue_item(p, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
+    }
+  }
+}
+
+#endif  // __CUDACC__ || __CUDACC_RTC__
+
+}  // namespace xk

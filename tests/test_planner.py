@@ -1,0 +1,350 @@
+"""Host planner (C++ in libxorec.so, called through the C ABI) against the
+paper's worked examples and printed RS(10,4) counts.  CPU only."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import paper_2108_02692_gb300 as xo
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+EX = json.load(open(os.path.join(GOLD, "slp_examples.json")))
+COUNTS = json.load(open(os.path.join(GOLD, "paper_counts.json")))
+
+
+class Slp:
+    def __init__(self, h):
+        self.h = h
+
+    @classmethod
+    def parse(cls, text):
+        return cls(xo.ec_slp_parse(text))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            xo.ec_slp_destroy(self.h)
+
+    def stats(self):
+        return xo.ec_slp_stats_get(self.h)
+
+    def text(self):
+        return xo.ec_slp_to_text(self.h)
+
+    def repair(self, xc):
+        return Slp(xo.ec_slp_repair(self.h, xc))
+
+    def fuse(self, cancel=True):
+        return Slp(xo.ec_slp_fuse(self.h, cancel))
+
+    def sched(self, kind, cap=8):
+        return Slp(xo.ec_slp_schedule(self.h, kind, cap))
+
+    def io(self, c):
+        return xo.ec_slp_iocost(self.h, c)
+
+    def ccap(self):
+        return xo.ec_slp_ccap(self.h)
+
+    def eq(self, other):
+        return xo.ec_slp_equivalent(self.h, other.h)
+
+
+def body(text):
+    """Statements of a text program as (dst, [args]) with the const line and
+    ret line dropped."""
+    out = []
+    for line in text.strip().splitlines():
+        t = line.split()
+        if t[0] in ("const",):
+            continue
+        if t[0] == "ret":
+            out.append(("ret", t[1:]))
+        else:
+            out.append((t[0], t[2:]))
+    return out
+
+
+def test_set_semantics_example():
+    e = EX["P_sem"]
+    p = Slp.parse(e["text"])
+    s = p.stats()
+    assert s["xors"] == e["xors"] and s["nvar"] == e["nvar"]
+    # compare against a program that returns the expected sets directly
+    sets = " ".join("x%d" % i for i in range(3))
+    direct = "const a b c d\n" + "".join(
+        "x%d = %s\n" % (i, " ".join(st)) for i, st in enumerate(e["sets"])) + "ret " + sets + "\n"
+    assert p.eq(Slp.parse(direct))
+
+
+def test_cancellation_example_counts():
+    p0, p1, p2 = (Slp.parse(EX[k]["text"]) for k in ("P0", "P1", "P2"))
+    assert p0.stats()["xors"] == 8 and p1.stats()["xors"] == 5 and p2.stats()["xors"] == 4
+    assert p0.eq(p1) and p0.eq(p2)
+
+
+def test_repair_reproduces_trace_and_P1():
+    p0 = Slp.parse(EX["P0"]["text"])
+    r = p0.repair(False)
+    st = body(r.text())
+    pairs = [args for dst, args in st if dst != "ret"]
+    assert pairs == [list(x) for x in EX["repair_trace"]["pairs"]]
+    assert r.stats()["xors"] == 5
+    assert r.eq(Slp.parse(EX["P1"]["text"]))
+
+
+def test_xorrepair_uses_cancellation():
+    p0 = Slp.parse(EX["P0"]["text"])
+    x = p0.repair(True)
+    pairs = [args for dst, args in body(x.text()) if dst != "ret"]
+    assert pairs == [list(p) for p in EX["xorrepair_trace"]["pairs"]]
+    assert x.stats()["xors"] == 4
+    assert x.eq(p0)
+
+
+def test_fusion_chain_and_memory_counts():
+    e = EX["chain3"]
+    p = Slp.parse(e["text"])
+    assert p.stats()["mem"] == e["mem"]
+    f = p.fuse(False)
+    assert f.stats()["mem"] == e["fused_mem"]
+    assert body(f.text()) == body(e["fused_text"])
+
+
+def test_fusion_restriction_counts():
+    e = EX["fusion_restriction"]
+    A, B, C = (Slp.parse(e[k]) for k in "ABC")
+    assert A.stats()["mem"] == e["mem_A"]
+    assert B.stats()["mem"] == e["mem_B"]
+    assert C.stats()["mem"] == e["mem_C"]
+    assert A.eq(B) and A.eq(C)
+    # fusion keeps the multi-use v1 of B: the result is B itself
+    assert B.fuse().stats()["mem"] == e["mem_B"]
+
+
+@pytest.mark.parametrize("name", ["P_eg", "P_reg", "Q"])
+def test_lru_cost_model(name):
+    e = EX[name]
+    p = Slp.parse(e["text"])
+    if "ccap" in e:
+        assert p.ccap() == e["ccap"]
+    if "io10" in e:
+        assert p.io(10) == e["io10"]
+    if "io8" in e:
+        assert p.io(8) == e["io8"]
+    if "nvar" in e:
+        assert p.stats()["nvar"] == e["nvar"]
+
+
+def test_all_strategies_compute_G_eg():
+    g = Slp.parse(EX["G_eg"]["text"])
+    for k in ("Q", "Q_DFS", "Q_greedy"):
+        assert Slp.parse(EX[k]["text"]).eq(g), k
+
+
+@pytest.mark.parametrize("kind,name", [(xo.EC_SCHED_DFS, "Q_DFS"),
+                                       (xo.EC_SCHED_GREEDY, "Q_greedy")])
+def test_schedulers_reproduce_paper_strategies(kind, name):
+    g = Slp.parse(EX["G_eg"]["text"])
+    q = g.sched(kind, 8)
+    e = EX[name]
+    assert body(q.text()) == body(e["text"])
+    assert q.stats()["nvar"] == e["nvar"]
+    assert q.ccap() == e["ccap"]
+    assert q.io(8) == e["io8"]
+    assert q.eq(g)
+
+
+def _rs_programs(which):
+    P = oracle.power(10, 4)
+    if which == "P_enc":
+        return P
+    return oracle.decode_matrix(P, COUNTS["P_dec"]["erased"])
+
+
+@pytest.mark.parametrize("which", ["P_enc", "P_dec"])
+def test_rs10_4_raw_program_counts(which):
+    gold = COUNTS[which]
+    A = _rs_programs(which)
+    raw = Slp(xo.ec_slp_from_matrix(A, 1))
+    s = raw.stats()
+    assert s["xors"] == gold["xors"]
+    assert s["mem"] == gold["mem"]
+    assert s["nvar"] == gold["nvar"]
+    assert raw.ccap() == gold["ccap"]
+
+
+@pytest.mark.parametrize("which", ["P_enc", "P_dec"])
+def test_rs10_4_optimised_counts_near_paper(which):
+    """Tie-breaks of RePair and the schedulers are not fully specified, so
+    the optimised counts are checked within 5 % of the printed values (10 %
+    for the scheduled program); the raw counts above are exact."""
+    gold = COUNTS[which]
+    A = _rs_programs(which)
+    raw = Slp(xo.ec_slp_from_matrix(A, 1))
+    co = raw.repair(True)
+    fu = co.fuse()
+    dfs = fu.sched(xo.EC_SCHED_DFS)
+
+    def near(x, y, tol=0.05):
+        return abs(x - y) <= tol * y
+
+    assert near(co.stats()["xors"], gold["co_xors"])
+    assert fu.stats()["xors"] == co.stats()["xors"]          # fusion keeps XORs
+    assert near(fu.stats()["stmts"], gold["fu_co_xors"])
+    assert near(fu.stats()["mem"], gold["fu_co_mem"])
+    # the schedule inherits the differences of its input program: 10 %
+    assert near(dfs.stats()["nvar"], gold["dfs_nvar"], 0.10)
+    assert near(dfs.ccap(), gold["dfs_ccap"], 0.10)
+    for p in (co, fu, dfs):
+        assert p.eq(raw)
+
+
+def test_average_ratios_over_rs10_4_sample():
+    """Sec. 7.3 averages over the 1002 RS(10,4) SLPs: XorRePair keeps about
+    40.8 % of the XORs and Fu(Co) about 24.1 % of the memory accesses.  A
+    seeded sample of 40 decode patterns plus the encoder is checked within
+    3 points."""
+    P = oracle.power(10, 4)
+    rng = np.random.default_rng(5)
+    import itertools
+    pats = list(itertools.combinations(range(14), 4))
+    chosen = [pats[i] for i in rng.choice(len(pats), 40, replace=False)]
+    mats = [P] + [oracle.decode_matrix(P, list(e)) for e in chosen]
+    xr, mr = [], []
+    for A in mats:
+        raw = Slp(xo.ec_slp_from_matrix(A, 1))
+        co = raw.repair(True)
+        fu = co.fuse()
+        xr.append(co.stats()["xors"] / raw.stats()["xors"])
+        mr.append(fu.stats()["mem"] / raw.stats()["mem"])
+    assert abs(np.mean(xr) - COUNTS["ratios"]["xorrepair_xor"]) < 0.03
+    assert abs(np.mean(mr) - COUNTS["ratios"]["fu_co_mem"]) < 0.03
+
+
+def emulate_stream(code, n_in, n_out, inputs, n_slots_hint=4096):
+    """Run an instruction stream on host strips (numpy XOR)."""
+    L = inputs[0].size
+    slots = {}
+    outs = [None] * n_out
+    pc = 0
+    while pc < len(code):
+        na = int(code[pc]); w1 = int(code[pc + 1]); pc += 2
+        no = w1 & 0x7FFF
+        slot = None
+        if w1 & 0x8000:
+            slot = int(code[pc]); pc += 1
+        orows = [int(x) for x in code[pc:pc + no]]; pc += no
+        acc = np.zeros(L, np.uint8)
+        for a in code[pc:pc + na]:
+            a = int(a)
+            acc ^= inputs[a] if a < n_in else slots[a - n_in]
+        pc += na
+        if slot is not None:
+            slots[slot] = acc
+        for r in orows:
+            assert outs[r] is None, "output written twice"
+            outs[r] = acc.copy()
+    assert all(o is not None for o in outs), "output never written"
+    return outs
+
+
+def _strips(blocks):
+    out = []
+    for b in blocks:
+        S = b.size // 8
+        out.extend(b[t * S:(t + 1) * S] for t in range(8))
+    return out
+
+
+def _unstrip(strips, nblk):
+    return [np.concatenate(strips[8 * i:8 * i + 8]) for i in range(nblk)]
+
+
+@pytest.mark.parametrize("k,m,opt", [(4, 2, 2), (10, 4, 2), (10, 4, 0), (10, 4, 1),
+                                     (6, 3, 2), (12, 4, 2), (3, 1, 2)])
+def test_lowered_encoder_stream_matches_oracle(k, m, opt):
+    from paper_2108_02692_gb300 import synth
+    plan = xo.ec_plan_create_ex(k, m, opt_level=opt)
+    try:
+        code = xo.ec_plan_program(plan)
+        B = 256
+        data = [synth.block_bytes(11, 0, j, B) for j in range(k)]
+        got = _unstrip(emulate_stream(code, 8 * k, 8 * m, _strips(data)), m)
+        ref = oracle.encode(oracle.cauchy(k, m), data)
+        for i in range(m):
+            assert np.array_equal(got[i], ref[i])
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (6, 3), (10, 4)])
+def test_lowered_decoder_streams_match_oracle(k, m):
+    from paper_2108_02692_gb300 import synth
+    import itertools
+    plan = xo.ec_plan_create(k, m)
+    try:
+        P = oracle.cauchy(k, m)
+        B = 128
+        data = [synth.block_bytes(12, 0, j, B) for j in range(k)]
+        blocks = data + oracle.encode(P, data)
+        pats = [p for ne in range(1, m + 1) for p in itertools.combinations(range(k + m), ne)]
+        if len(pats) > 60:
+            rng = np.random.default_rng(k)
+            pats = [pats[i] for i in rng.choice(len(pats), 60, replace=False)]
+        for er in pats:
+            code = xo.ec_plan_program(plan, list(er))
+            surv = [i for i in range(k + m) if i not in er][:k]
+            got = _unstrip(emulate_stream(code, 8 * k, 8 * len(er),
+                                          _strips([blocks[i] for i in surv])), len(er))
+            for i, e in enumerate(er):
+                assert np.array_equal(got[i], blocks[e]), (er, e)
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+def test_plan_info_rs10_4():
+    plan = xo.ec_plan_create_ex(10, 4, matrix_kind=xo.EC_MATRIX_POWER)
+    try:
+        info = xo.ec_plan_info(plan)
+        assert info["n_in"] == 80 and info["n_out"] == 32
+        assert info["raw"]["xors"] == 755 and info["raw"]["mem"] == 2265
+        assert info["fused"]["xors"] == info["compressed"]["xors"]
+        dinfo = xo.ec_plan_info(plan, [6, 2, 5, 4])
+        assert dinfo["raw"]["xors"] == 1368
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+def test_plan_argument_errors():
+    with pytest.raises(xo.XorecError) as e:
+        xo.ec_plan_create(0, 2)
+    assert e.value.status == xo.EC_EINVAL
+    with pytest.raises(xo.XorecError):
+        xo.ec_plan_create(200, 57)
+    plan = xo.ec_plan_create(4, 2)
+    try:
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_plan_info(plan, [0, 1, 2])
+        assert e.value.status == xo.EC_ETOOMANY
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_plan_info(plan, [1, 1])
+        assert e.value.status == xo.EC_EINVAL
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_plan_info(plan, [6])
+        assert e.value.status == xo.EC_EINVAL
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+def test_singular_user_matrix_detected():
+    # all-ones rows: erasing two data blocks leaves a singular submatrix
+    P = np.ones((2, 4), np.uint8)
+    plan = xo.ec_plan_create(4, 2, P)
+    try:
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_plan_info(plan, [0, 1])
+        assert e.value.status == xo.EC_ESINGULAR
+    finally:
+        xo.ec_plan_destroy(plan)
