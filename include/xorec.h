@@ -138,6 +138,26 @@ ec_status ec_plan_program(ec_plan *plan, const int *erasures, int n_erasures, ui
 ec_status ec_encode(ec_plan *plan, const uint8_t *const *data, uint8_t *const *parity,
                     size_t block_bytes, void *stream);
 
+/* Limits of ec_encode_noalloc. */
+#define EC_NOALLOC_MAX_BLOCKS 256        /* k + m                            */
+#define EC_NOALLOC_MAX_CODE_WORDS 32768  /* 16-bit words of the program      */
+
+/* Encode one stripe like ec_encode, without allocating any memory.  The
+ * paper has no counterpart: this is for callers that are not allowed to
+ * allocate device memory when they encode (code running inside another
+ * runtime's allocator, or under a fixed device-memory budget planned in
+ * advance).  Its scratch (status word, block table and instruction stream,
+ * about 66 KiB) lives in one static device array that every GPU loading the
+ * library keeps until the process exits.  All calls share that array and
+ * each call overwrites it, so calls whose GPU work overlaps race.  The
+ * first call on each device performs that device's set-up (looks up the
+ * array's address, clears its status word) and should come before any
+ * stream capture.  Always uses the interpreter executor.  Fails with
+ * EC_EINVAL when k + m > EC_NOALLOC_MAX_BLOCKS or the encoding program is
+ * longer than EC_NOALLOC_MAX_CODE_WORDS.  Same arguments as ec_encode. */
+ec_status ec_encode_noalloc(ec_plan *plan, const uint8_t *const *data, uint8_t *const *parity,
+                            size_t block_bytes, void *stream);
+
 /* Encode n_stripes stripes in one launch.  Block j of stripe s is at
  * data + s*data_stripe_stride + j*data_block_stride; parity block i of stripe
  * s at parity + s*par_stripe_stride + i*par_block_stride (bytes, device

@@ -147,6 +147,13 @@ def ec_encode(plan: int, data_ptrs, parity_ptrs, block_bytes: int, stream: int =
                            stream or None))
 
 
+def ec_encode_noalloc(plan: int, data_ptrs, parity_ptrs, block_bytes: int,
+                      stream: int = 0) -> None:
+    """ec_encode without any memory allocation (see include/xorec.h)."""
+    _check(lib().ec_encode_noalloc(plan, _vp_array(data_ptrs), _vp_array(parity_ptrs),
+                                   block_bytes, stream or None))
+
+
 def ec_encode_strided(plan: int, data_ptr: int, data_stripe_stride: int, data_block_stride: int,
                       parity_ptr: int, par_stripe_stride: int, par_block_stride: int,
                       n_stripes: int, block_bytes: int, stream: int = 0) -> None:

@@ -62,6 +62,7 @@ SIGNATURES = {
     "ec_plan_program": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ctypes.c_uint16), c_size,
                                 ctypes.POINTER(c_size)]),
     "ec_encode": (c_int, [c_vp, vpp, vpp, c_size, c_vp]),
+    "ec_encode_noalloc": (c_int, [c_vp, vpp, vpp, c_size, c_vp]),
     "ec_encode_strided": (c_int, [c_vp, c_vp, c_size, c_size, c_vp, c_size, c_size, c_int,
                                   c_size, c_vp]),
     "ec_decode": (c_int, [c_vp, intp, c_int, vpp, vpp, c_size, c_vp]),
