@@ -48,6 +48,12 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="encode", choices=["encode", "decode"])
     ap.add_argument("--executor", default="auto", choices=["auto", "interp", "compiled"])
+    ap.add_argument("--opt", default="xorrepair", choices=["raw", "repair", "xorrepair"],
+                    help="optimiser level of the encoding program")
+    ap.add_argument("--max-temps", type=int, default=-2,
+                    help="RePair temporaries budget (-1 = unlimited, -2 = automatic)")
+    ap.add_argument("--stripes", type=int, default=N_STRIPES,
+                    help="stripes per step (profiling runs use fewer)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -198,11 +204,14 @@ def run_ours(args):
 
     executor = {"auto": xo.EC_EXEC_AUTO, "interp": xo.EC_EXEC_INTERP,
                 "compiled": xo.EC_EXEC_COMPILED}[args.executor]
-    k, m, B, n = K_DATA, M_PAR, BLOCK, N_STRIPES
+    k, m, B, n = K_DATA, M_PAR, BLOCK, args.stripes
     S = B // 8
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
-    plan = xo.ec_plan_create_ex(k, m, executor=executor)
+    opt = {"raw": xo.EC_OPT_RAW, "repair": xo.EC_OPT_REPAIR,
+           "xorrepair": xo.EC_OPT_XORREPAIR}[args.opt]
+    plan = xo.ec_plan_create_ex(k, m, executor=executor, opt_level=opt,
+                                max_temps=args.max_temps)
     data = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
     par = torch.empty((n, m, B), dtype=torch.uint8, device="cuda")
     for s in range(n):
@@ -271,7 +280,7 @@ def run_ours(args):
     kind = "compiled" if info["compiled"] else "interp"
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and n == N_STRIPES:
         e2e = run_e2e(args, xo, plan, data, par, stream, torch)
     status = xo.ec_device_status()
 
@@ -288,8 +297,10 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "u8",
         "data": "synthetic (SplitMix64 bytes generated on the device)",
-        "config": {"workload": WORKLOAD, "k": k, "m": m, "n_stripes": n, "block_bytes": B,
-                   "matrix": "cauchy", "executor": kind,
+        "config": {"workload": WORKLOAD if n == N_STRIPES else WORKLOAD.replace("256", str(n)),
+                   "k": k, "m": m, "n_stripes": n, "block_bytes": B,
+                   "matrix": "cauchy", "executor": kind, "opt": args.opt,
+                   "max_temps": args.max_temps,
                    "l2": "inputs (2.5 GiB) larger than L2 (129 MB); no flush",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -304,7 +315,8 @@ def run_ours(args):
         "device_status": status,
         "program": {"slots": info["slots"], "stmts": info["stmts"],
                     "xors": info["fused"]["xors"], "mem": info["fused"]["mem"],
-                    "raw_xors": info["raw"]["xors"], "regs": info["regs"]},
+                    "raw_xors": info["raw"]["xors"], "regs": info["regs"],
+                    "temps": info["temps"], "max_live": info["max_live"]},
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline_obj()

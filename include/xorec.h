@@ -81,6 +81,14 @@ typedef struct {
   int sched;            /* EC_SCHED_*                                         */
   int greedy_cap;       /* cache capacity of the greedy scheduler             */
   int executor;         /* EC_EXEC_*                                          */
+  int max_temps;        /* (Xor)RePair temporaries budget: -1 = unlimited
+                           (the paper's full run), -2 = automatic, >= 0 =
+                           explicit (0 = one fused statement per row).  The
+                           most frequent pairs are factored first, so a
+                           budget keeps the most valuable temporaries while
+                           bounding the registers the program needs          */
+  int reg_budget;       /* registers per thread the automatic budget aims at
+                           (all input words preloaded); 0 = 128             */
 } ec_plan_opts;
 
 /* Create a plan for RS(k,m).  matrix: m*k row-major parity rows, or NULL for
@@ -116,6 +124,8 @@ typedef struct {
   ec_slp_stats fused;   /* after XOR fusion                                   */
   int compiled;         /* 1 if a compiled straight-line kernel exists        */
   int regs;             /* registers per thread of the compiled kernel        */
+  int temps;            /* temporaries kept by (Xor)RePair                    */
+  int max_live;         /* values live at once with inputs preloaded          */
 } ec_program_info;
 
 /* Program of the encoder (erasures == NULL) or of the decoder for the given

@@ -89,10 +89,11 @@ def ec_plan_create(k: int, m: int, matrix=None) -> int:
 
 def ec_plan_create_ex(k: int, m: int, matrix_kind: int = EC_MATRIX_CAUCHY, matrix=None,
                       opt_level: int = EC_OPT_XORREPAIR, sched: int = EC_SCHED_DFS,
-                      greedy_cap: int = 128, executor: int = EC_EXEC_AUTO) -> int:
+                      greedy_cap: int = 128, executor: int = EC_EXEC_AUTO,
+                      max_temps: int = -2, reg_budget: int = 0) -> int:
     h = ctypes.c_void_p()
     keep = _u8(matrix)
-    opts = _abi.PlanOpts(opt_level, sched, greedy_cap, executor)
+    opts = _abi.PlanOpts(opt_level, sched, greedy_cap, executor, max_temps, reg_budget)
     _check(lib().ec_plan_create_ex(k, m, matrix_kind, keep[1] if keep else None,
                                    ctypes.byref(opts), ctypes.byref(h)))
     return h.value
@@ -121,7 +122,8 @@ def ec_plan_info(plan: int, erasures=None) -> dict:
     return {"n_in": info.n_in, "n_out": info.n_out, "slots": info.slots, "stmts": info.stmts,
             "code_words": info.code_words, "sched_nvar": info.sched_nvar,
             "raw": _stats(info.raw), "compressed": _stats(info.compressed),
-            "fused": _stats(info.fused), "compiled": bool(info.compiled), "regs": info.regs}
+            "fused": _stats(info.fused), "compiled": bool(info.compiled), "regs": info.regs,
+            "temps": info.temps, "max_live": info.max_live}
 
 
 def ec_plan_program(plan: int, erasures=None) -> np.ndarray:

@@ -37,7 +37,7 @@ EC_EXEC_AUTO, EC_EXEC_INTERP, EC_EXEC_COMPILED = 0, 1, 2
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("opt_level", c_int), ("sched", c_int), ("greedy_cap", c_int),
-                ("executor", c_int)]
+                ("executor", c_int), ("max_temps", c_int), ("reg_budget", c_int)]
 
 
 class SlpStats(ctypes.Structure):
@@ -48,7 +48,7 @@ class ProgramInfo(ctypes.Structure):
     _fields_ = [("n_in", c_int), ("n_out", c_int), ("slots", c_int), ("stmts", c_int),
                 ("code_words", c_int), ("sched_nvar", c_int), ("raw", SlpStats),
                 ("compressed", SlpStats), ("fused", SlpStats), ("compiled", c_int),
-                ("regs", c_int)]
+                ("regs", c_int), ("temps", c_int), ("max_live", c_int)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/xorec.h

@@ -91,8 +91,8 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   bool compiled = false;
   int threads = 0, nstage = 0;
   if (executor != EC_EXEC_INTERP) {
-    threads = env_int("EC_JIT_THREADS", 256);
-    nstage = env_int("EC_JIT_NSTAGE", 2);
+    threads = env_int("EC_JIT_THREADS", 128);
+    nstage = env_int("EC_JIT_NSTAGE", 1);
     std::string err;
     {
       std::lock_guard<std::mutex> lk(g_jit_mu);
@@ -287,6 +287,9 @@ ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix
     plan->opts.sched = opts->sched;
     plan->opts.greedy_cap = opts->greedy_cap > 0 ? opts->greedy_cap : 128;
     plan->executor = opts->executor;
+    if (opts->max_temps < -2) return fail(EC_EINVAL, "bad max_temps");
+    plan->opts.max_temps = opts->max_temps;
+    plan->opts.reg_budget = opts->reg_budget > 0 ? opts->reg_budget : 128;
   }
   plan->enc = std::make_unique<Program>();
   std::string err;
@@ -355,6 +358,8 @@ ec_status ec_plan_info(ec_plan* plan, const int* erasures, int n_erasures, ec_pr
   fill_stats(p->stats.fused, &out->fused);
   out->compiled = p->jit != nullptr;
   out->regs = xorec::jit_regs(p);
+  out->temps = p->stats.temps;
+  out->max_live = p->stats.max_live;
   return EC_OK;
 }
 

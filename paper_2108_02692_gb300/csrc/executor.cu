@@ -21,6 +21,10 @@ namespace {
 using namespace xk;
 
 struct InterpBody {
+  static constexpr bool kEarlyRelease = false;
+  struct Regs {};
+  __device__ void load(const LaunchParams&, int, const u8*, Regs&) const {}
+  __device__ void compute(const LaunchParams&, i64, i64, int, Regs&) const {}
   __device__ __forceinline__ void operator()(const LaunchParams& p, i64 s, i64 c0, int len,
                                              const u8* stg, u8* slots) const {
     const int col = threadIdx.x * 4;

@@ -9,6 +9,7 @@
 #include <nvrtc.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <sstream>
 #include <string>
@@ -31,25 +32,34 @@ struct JitKernel {
   int device = -1;
 };
 
+// The straight-line body.  load(): each thread copies its 4-byte column of
+// every input strip from the stage into registers.  compute(): one SSA
+// register per scheduled statement, stores to the output strips as soon as
+// a returned value is ready.
 std::string gen_body(const xorec::Program& p, int threads) {
   const xorec::Slp& q = p.fused;
   const int nc = q.n_const;
   const int T = 4 * threads;
   std::ostringstream os;
   os << "struct SlpBody {\n"
-        "  __device__ __forceinline__ void operator()(const xk::LaunchParams& p, xk::i64 s,\n"
-        "      xk::i64 c0, int len, const xk::u8* stg, xk::u8*) const {\n"
+        "  static constexpr bool kEarlyRelease = true;\n"
+        "  struct Regs { xk::u32 x[" << (nc > 0 ? nc : 1) << "]; };\n"
+        "  __device__ __forceinline__ void load(const xk::LaunchParams&, int len,\n"
+        "      const xk::u8* stg, Regs& r) const {\n"
         "    const int col = threadIdx.x * 4;\n"
         "    if (col >= len) return;\n"
-        "    const xk::u8* in = stg + col;\n"
+        "    const xk::u8* in = stg + col;\n";
+  for (int c = 0; c < nc; ++c)
+    os << "    r.x[" << c << "] = *reinterpret_cast<const xk::u32*>(in + " << c * T << ");\n";
+  os << "  }\n"
+        "  __device__ __forceinline__ void compute(const xk::LaunchParams& p, xk::i64 s,\n"
+        "      xk::i64 c0, int len, Regs& r) const {\n"
+        "    const int col = threadIdx.x * 4;\n"
+        "    if (col >= len) return;\n"
         "    const xk::i64 S = p.io.S;\n";
-  // output block bases
-  std::vector<char> used(p.n_out / 8 + 1, 0);
-  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r) used[r >> 3] = 1;
   for (int b = 0; b < p.n_out / 8; ++b)
-    if (used[b])
-      os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
-  os << "#define I(c) xk_lds(in + (c) * " << T << ")\n";
+    os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
+  os << "#define I(c) r.x[c]\n";
   os << "#define O(b, t, v) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
   std::vector<std::vector<int>> outs_of(q.n_var);
   for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
@@ -75,20 +85,17 @@ std::string gen_body(const xorec::Program& p, int threads) {
   return os.str();
 }
 
+int env_or(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
 std::string gen_source(const xorec::Program& p, int threads) {
   std::ostringstream os;
   os << kPipelineSrc << "\n";
-  // Shared-memory load kept as an explicit instruction per use so that the
-  // compiler re-reads inputs from the stage instead of holding all of them
-  // in registers across the whole program.
-  os << "__device__ __forceinline__ xk::u32 xk_lds(const xk::u8* a) {\n"
-        "  xk::u32 v;\n"
-        "  asm volatile(\"ld.shared.u32 %0, [%1];\" : \"=r\"(v) : \"r\"(xk::smem_addr(a)));\n"
-        "  return v;\n"
-        "}\n";
   os << gen_body(p, threads);
-  os << "extern \"C\" __global__ void __launch_bounds__(" << threads
-     << ", 1) xorec_slp(xk::LaunchParams p) {\n"
+  os << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
+     << env_or("EC_JIT_MINB", 4) << ") xorec_slp(xk::LaunchParams p) {\n"
         "  extern __shared__ __align__(128) xk::u8 smem[];\n"
         "  xk::run_pipeline(p, smem, SlpBody());\n"
         "}\n";

@@ -1,5 +1,7 @@
 #include "plan.h"
 
+#include <algorithm>
+
 #include "gf.h"
 
 namespace xorec {
@@ -99,7 +101,27 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
     fused = slp_rows_fused(n_in, R, order);
     p.stats.compressed = p.stats.raw;
   } else {
-    Slp co = repair(chains, o.opt_level == kOptXorRePair);
+    RepairTrace tr(chains, o.opt_level == kOptXorRePair);
+    int b = tr.n_temps();
+    if (o.max_temps >= 0) {
+      b = std::min(o.max_temps, tr.n_temps());
+    } else if (o.max_temps == -2) {
+      // largest budget whose DFS schedule fits the register budget
+      auto live_at = [&](int x) {
+        Slp f = fuse(tr.at(x), o.cancel_pairs);
+        return max_live_preloaded(f, schedule_dfs(f, false));
+      };
+      if (live_at(b) > o.reg_budget) {
+        int lo = 0, hi = b;   // live_at(lo) assumed to fit, live_at(hi) does not
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) / 2;
+          if (live_at(mid) <= o.reg_budget) lo = mid; else hi = mid;
+        }
+        b = lo;
+      }
+    }
+    Slp co = tr.at(b);
+    p.stats.temps = b;
     p.stats.compressed = metrics(co);
     fused = fuse(co, o.cancel_pairs);
   }
@@ -114,6 +136,7 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   Schedule gpu = o.sched == kSchedGreedy ? schedule_greedy(fused, o.greedy_cap, false)
                                          : schedule_dfs(fused, false);
   p.stats.slots = gpu.n_pebbles;
+  p.stats.max_live = max_live_preloaded(fused, gpu);
   if (!lower(fused, gpu, n_in, n_out, &p, err)) return false;
   p.fused = fused;
   p.sched = gpu;

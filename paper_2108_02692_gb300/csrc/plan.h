@@ -24,6 +24,8 @@ struct PipelineStats {
   int raw_ccap = 0;
   int sched_nvar = 0;      // pebbles of the paper's game (goals hold)
   int slots = 0;           // pebbles when outputs stream out (GPU setting)
+  int temps = 0;           // temporaries kept by (Xor)RePair
+  int max_live = 0;        // registers with all inputs preloaded
 };
 
 // An executable program for one linear map from n_in input strips to n_out
@@ -52,6 +54,11 @@ struct PlanOptions {
   int sched = kSchedDfs;
   int greedy_cap = 128;
   bool cancel_pairs = true;
+  // Temporaries budget of (Xor)RePair: -1 = none (the paper's full run),
+  // -2 = automatic (largest budget whose schedule needs at most reg_budget
+  // registers with all inputs preloaded), >= 0 = explicit.
+  int max_temps = -2;
+  int reg_budget = 128;
 };
 
 // Build the program for the linear map A (rows x cols over GF(2^8)).

@@ -306,22 +306,28 @@ struct Ranker {
 
 }  // namespace
 
-Slp repair(const Slp& in, bool xor_cancel) {
-  const int nc = in.n_const;
+// One run of (Xor)RePair to completion.  Every iteration adds exactly one
+// temporal, so the program after b temporals (a budget) is a prefix of this
+// run; the run records the definition changes of every iteration so that
+// any prefix can be rebuilt without running the algorithm again.
+RepairTrace::RepairTrace(const Slp& in, bool xor_cancel)
+    : nc_(in.n_const), const_names_(in.const_names) {
+  const int nc = nc_;
   const Ranker rk{nc};
   const std::vector<Bits> goal = semantics(in);
-  const int n_orig = static_cast<int>(goal.size());
+  n_orig_ = static_cast<int>(goal.size());
+  const int n_orig = n_orig_;
 
-  std::vector<std::vector<int>> def(n_orig);   // current definitions
+  std::vector<std::vector<int>> def(n_orig);
   std::vector<char> active(n_orig, 0);
   for (int o = 0; o < n_orig; ++o) {
     for (int c = 0; c < nc; ++c)
       if (goal[o].test(c)) def[o].push_back(c);
     active[o] = def[o].size() >= 2;
   }
-  std::vector<std::pair<int, int>> tdef;       // temporal definitions
-  std::vector<Bits> tval;                      // their values
-  std::vector<Bits> occ;                       // term -> active originals containing it
+  init_ = def;
+  std::vector<Bits> tval;
+  std::vector<Bits> occ;  // term -> active originals containing it
   auto ensure_occ = [&](int t) {
     if (static_cast<int>(occ.size()) <= t) occ.resize(t + 1, Bits(n_orig));
   };
@@ -334,7 +340,7 @@ Slp repair(const Slp& in, bool xor_cancel) {
     return tval[t - nc];
   };
   auto sort_def = [&](std::vector<int>& d) {
-    std::sort(d.begin(), d.end(), [&](int a, int b) { return rk.rank(a) < rk.rank(b); });
+    std::sort(d.begin(), d.end(), [&](int x, int y) { return rk.rank(x) < rk.rank(y); });
   };
   auto attach = [&](int o) {
     for (int t : def[o]) { ensure_occ(t); occ[t].set(o); }
@@ -345,28 +351,54 @@ Slp repair(const Slp& in, bool xor_cancel) {
   for (int o = 0; o < n_orig; ++o)
     if (active[o]) attach(o);
 
-  // Rebuild(v): greedily XOR existing temporals into rem = [[v]] while that
-  // shrinks rem; ties go to the earliest temporal (Sec. 4.4).
-  auto rebuild = [&](int o) {
-    Bits rem = goal[o];
-    int rem_size = rem.count();
-    std::vector<char> in_s(tdef.size(), 0);
+  // Rebuild(v) (Sec. 4.4): greedily XOR existing temporals into
+  // rem = [[v]] while that strictly shrinks rem; ties go to the earliest
+  // temporal.  The greedy path of every original is cached: a temporal
+  // created later changes the path only at the first step where it is
+  // strictly better than the choice made there, so the path is recomputed
+  // from that step on, which gives the same result as starting over.
+  struct Path {
+    std::vector<int> pick;   // temporal chosen at each step
+    std::vector<Bits> rem;   // rem before each step; back() = final rem
+  };
+  std::vector<Path> path(n_orig);
+  for (int o = 0; o < n_orig; ++o) path[o].rem.push_back(goal[o]);
+  auto extend = [&](Path& P, size_t k) {
+    P.pick.resize(k);
+    P.rem.resize(k + 1);
+    Bits rem = P.rem[k];
+    int size = rem.count();
     for (;;) {
-      int best = -1, best_size = rem_size;
+      int best = -1, best_size = size;
       for (size_t t = 0; t < tval.size(); ++t) {
         const int sz = rem.xor_count(tval[t]);
         if (sz < best_size) { best_size = sz; best = static_cast<int>(t); }
       }
       if (best < 0) break;
       rem ^= tval[best];
-      rem_size = best_size;
-      in_s[best] ^= 1;
+      size = best_size;
+      P.pick.push_back(best);
+      P.rem.push_back(rem);
     }
+  };
+  auto note_new_temporal = [&](Path& P, int t) {
+    for (size_t k = 0; k < P.rem.size(); ++k) {
+      const int cand = P.rem[k].xor_count(tval[t]);
+      const int cur = k < P.pick.size() ? P.rem[k + 1].count() : P.rem[k].count();
+      if (cand < cur) {
+        extend(P, k);
+        return;
+      }
+    }
+  };
+  auto rebuilt_def = [&](const Path& P) {
+    std::vector<char> in_s(tval.size(), 0);
+    for (int t : P.pick) in_s[t] ^= 1;
     std::vector<int> d;
     for (size_t t = 0; t < in_s.size(); ++t)
       if (in_s[t]) d.push_back(nc + static_cast<int>(t));
     for (int c = 0; c < nc; ++c)
-      if (rem.test(c)) d.push_back(c);
+      if (P.rem.back().test(c)) d.push_back(c);
     sort_def(d);
     return d;
   };
@@ -380,7 +412,7 @@ Slp repair(const Slp& in, bool xor_cancel) {
     for (int t = 0; t < static_cast<int>(occ.size()); ++t)
       if (occ[t].any()) present.push_back(t);
     std::sort(present.begin(), present.end(),
-              [&](int a, int b) { return rk.rank(a) < rk.rank(b); });
+              [&](int x, int y) { return rk.rank(x) < rk.rank(y); });
     // Most frequent pair; the first maximum in lexicographic order wins.
     int bx = -1, by = -1, bf = 0;
     for (size_t i = 0; i < present.size(); ++i)
@@ -390,8 +422,9 @@ Slp repair(const Slp& in, bool xor_cancel) {
       }
     if (bx < 0) break;  // cannot happen: an active definition has >= 2 terms
     // Pair(bx, by)
-    const int t = nc + static_cast<int>(tdef.size());
-    tdef.emplace_back(bx, by);
+    std::vector<std::pair<int, std::vector<int>>> changes;
+    const int t = nc + static_cast<int>(tdef_.size());
+    tdef_.emplace_back(bx, by);
     Bits v = value_of(bx);
     v ^= value_of(by);
     tval.push_back(v);
@@ -409,32 +442,58 @@ Slp repair(const Slp& in, bool xor_cancel) {
       def[o] = nd;
       active[o] = def[o].size() >= 2;
       if (active[o]) attach(o);
+      changes.emplace_back(o, nd);
     }
     if (xor_cancel) {
       for (int o = 0; o < n_orig; ++o) {
         if (!active[o]) continue;
-        std::vector<int> nd = rebuild(o);
+        note_new_temporal(path[o], t - nc);
+        std::vector<int> nd = rebuilt_def(path[o]);
         if (nd.size() < def[o].size()) {
           detach(o);
           def[o] = nd;
           active[o] = def[o].size() >= 2;
           if (active[o]) attach(o);
+          changes.emplace_back(o, nd);
         }
       }
     }
+    changes_.push_back(std::move(changes));
   }
+}
 
+Slp RepairTrace::at(int b) const {
+  const int nc = nc_;
+  const int T = std::max(0, std::min(b, n_temps()));
+  std::vector<std::vector<int>> def = init_;
+  for (int i = 0; i < T; ++i)
+    for (const auto& ch : changes_[i]) def[ch.first] = ch.second;
   Slp out;
   out.n_const = nc;
-  out.const_names = in.const_names;
-  out.n_var = static_cast<int>(tdef.size());
-  for (size_t i = 0; i < tdef.size(); ++i) {
-    out.body.push_back(Stmt{nc + static_cast<int>(i), {tdef[i].first, tdef[i].second}});
+  out.const_names = const_names_;
+  out.n_var = T;
+  for (int i = 0; i < T; ++i) {
+    out.body.push_back(Stmt{nc + i, {tdef_[i].first, tdef_[i].second}});
     out.var_names.push_back("t" + std::to_string(i + 1));
   }
-  out.ret.resize(n_orig);
-  for (int o = 0; o < n_orig; ++o) out.ret[o] = def[o].empty() ? -1 : def[o][0];
+  out.ret.resize(n_orig_);
+  for (int o = 0; o < n_orig_; ++o) {
+    if (def[o].size() <= 1) {
+      out.ret[o] = def[o].empty() ? -1 : def[o][0];
+      continue;
+    }
+    // budget reached: the remaining definition becomes one n-ary statement
+    const int v = nc + out.n_var++;
+    out.var_names.push_back("o" + std::to_string(o));
+    out.body.push_back(Stmt{v, def[o]});
+    out.ret[o] = v;
+  }
   return out;
+}
+
+Slp repair(const Slp& in, bool xor_cancel, int max_temps) {
+  RepairTrace tr(in, xor_cancel);
+  return tr.at(max_temps < 0 ? tr.n_temps() : max_temps);
 }
 
 // ------------------------------------------------------------ XOR fusion
@@ -675,6 +734,34 @@ Schedule schedule_greedy(const Slp& p, int cap, bool goals_hold) {
     s.steps.push_back(Schedule::Step{n, peb, args});
   }
   return s;
+}
+
+int max_live_preloaded(const Slp& q, const Schedule& s) {
+  const int nc = q.n_const;
+  std::vector<int> last_in(nc, -1), last_v(q.n_var, -1);
+  for (size_t i = 0; i < s.steps.size(); ++i)
+    for (int a : s.steps[i].args) {
+      if (a < nc) last_in[a] = static_cast<int>(i);
+      else last_v[a - nc] = static_cast<int>(i);
+    }
+  int live = 0;
+  for (int c = 0; c < nc; ++c) live += last_in[c] >= 0;
+  int peak = live;
+  for (size_t i = 0; i < s.steps.size(); ++i) {
+    const int n = s.steps[i].node;
+    const bool kept = last_v[n] > static_cast<int>(i);
+    peak = std::max(peak, live + 1);   // the result is written while operands are live
+    if (kept) ++live;
+    for (int a : s.steps[i].args) {
+      if (a < nc) {
+        if (last_in[a] == static_cast<int>(i)) { --live; last_in[a] = -2; }
+      } else if (last_v[a - nc] == static_cast<int>(i)) {
+        --live;
+        last_v[a - nc] = -2;
+      }
+    }
+  }
+  return peak;
 }
 
 Slp schedule_to_slp(const Slp& p, const Schedule& s) {

@@ -89,7 +89,27 @@ Slp slp_rows_chains(int n_const, const std::vector<Bits>& rows,
 // semantics of p.  Returns a single-assignment program of binary
 // temporals; returned terms become the temporal, constant or zero that
 // each original reduces to (Sec. 4.3, Sec. 4.4).
-Slp repair(const Slp& p, bool xor_cancel);
+// max_temps >= 0 stops after that many temporals (the most frequent pairs
+// come first, so a budget keeps the most valuable ones); definitions not yet
+// reduced stay as n-ary statements.
+Slp repair(const Slp& p, bool xor_cancel, int max_temps = -1);
+
+// A complete (Xor)RePair run from which the program under any temporaries
+// budget can be taken: each iteration adds one temporal, so budget b is the
+// first b iterations of the run.
+class RepairTrace {
+ public:
+  RepairTrace(const Slp& p, bool xor_cancel);
+  int n_temps() const { return static_cast<int>(tdef_.size()); }
+  Slp at(int b) const;   // program after b temporals (b >= n_temps: all)
+
+ private:
+  int nc_ = 0, n_orig_ = 0;
+  std::vector<std::string> const_names_;
+  std::vector<std::vector<int>> init_;                        // initial definitions
+  std::vector<std::pair<int, int>> tdef_;                     // temporal i = (x, y)
+  std::vector<std::vector<std::pair<int, std::vector<int>>>> changes_;  // per iteration
+};
 
 // XOR fusion: repeatedly unfold variables used exactly once into their
 // user; dead variables are dropped.  cancel_pairs removes arguments that
@@ -112,6 +132,12 @@ struct Schedule {
 };
 Schedule schedule_dfs(const Slp& p, bool goals_hold);
 Schedule schedule_greedy(const Slp& p, int cap, bool goals_hold);
+// Registers a thread needs to run schedule s of q when every input word is
+// loaded into a register first: inputs live until their last use, values
+// from their statement until their last use (Sec. 6.2's cache capacity with
+// the register file as the cache and no reloading).
+int max_live_preloaded(const Slp& q, const Schedule& s);
+
 // The program of a schedule, with variables renamed to pebbles.  Requires
 // goals_hold schedules so that returned values are still on their pebble.
 Slp schedule_to_slp(const Slp& p, const Schedule& s);

@@ -137,8 +137,15 @@ __device__ __forceinline__ void issue_item(const LaunchParams& p, i64 item, u8* 
 }
 
 // Shared memory: [mbarriers, 128 B][nstage stages of n_in * T][slots].
-// Body: void operator()(const LaunchParams&, i64 stripe, i64 c0, int len,
-//                       const u8* stage, u8* slots) const
+// A Body either reads its operands from the stage while it computes
+// (kEarlyRelease = false):
+//   void operator()(const LaunchParams&, i64 stripe, i64 c0, int len,
+//                   const u8* stage, u8* slots) const
+// or first copies its column of every input strip into registers and
+// computes from there (kEarlyRelease = true), which frees the stage for the
+// next copy before the XOR work starts:
+//   void load(const LaunchParams&, int len, const u8* stage, Regs&) const
+//   void compute(const LaunchParams&, i64 stripe, i64 c0, int len, Regs&) const
 template <class Body>
 __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, const Body& body) {
   u64* bars = reinterpret_cast<u64*>(smem);
@@ -179,13 +186,27 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
     const i64 c0 = (item % p.tiles_per_strip) * p.T;
     const i64 rest = p.io.S - c0;
     const int len = rest < p.T ? static_cast<int>(rest) : p.T;
-    body(p, s, c0, len, stages + st * stage_bytes, slots);
-    __syncthreads();
     const i64 nxt = item + p.nstage * step;
-    if (tid < 32 && nxt < p.n_items) {
-      if (tid == 0) fence_proxy_async();
-      __syncwarp();
-      issue_item(p, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
+    if constexpr (Body::kEarlyRelease) {
+      // Copy this thread's input words into registers, hand the stage back
+      // to the copy engine at once, then run the program from registers.
+      typename Body::Regs r;
+      body.load(p, len, stages + st * stage_bytes, r);
+      __syncthreads();
+      if (tid < 32 && nxt < p.n_items) {
+        if (tid == 0) fence_proxy_async();
+        __syncwarp();
+        issue_item(p, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
+      }
+      body.compute(p, s, c0, len, r);
+    } else {
+      body(p, s, c0, len, stages + st * stage_bytes, slots);
+      __syncthreads();
+      if (tid < 32 && nxt < p.n_items) {
+        if (tid == 0) fence_proxy_async();
+        __syncwarp();
+        issue_item(p, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
+      }
     }
   }
 }
