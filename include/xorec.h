@@ -199,6 +199,51 @@ ec_status ec_decode_prepare(ec_plan *plan, const int *sets, const int *counts, i
  * EC_ENOTSUP when no run-time compiler is present. */
 ec_status ec_plan_set_executor(ec_plan *plan, int executor);
 
+/* ------------------------------------------------------------------ batches
+ * Many stripes with mixed codes, block sizes and encode/decode jobs run in a
+ * few persistent launches.  The plans referenced by a batch must outlive
+ * it; the job arrays only need to live until ec_batch_create returns. */
+enum { EC_OP_ENCODE = 0, EC_OP_DECODE = 1 };
+
+typedef struct {
+  ec_plan *plan;
+  int op;                          /* EC_OP_ENCODE or EC_OP_DECODE                */
+  const int *erasures;             /* decode: erased block ids (caller order)     */
+  int n_erasures;                  /* decode: 1 .. m                              */
+  const uint8_t *const *blocks;    /* encode: k data blocks; decode: k+m blocks
+                                      indexed by id (erased entries ignored)     */
+  uint8_t *const *out;             /* encode: m parity blocks; decode:
+                                      n_erasures blocks in the caller's order    */
+  size_t block_bytes;              /* multiple of 128                             */
+} ec_job;
+
+typedef struct ec_batch ec_batch;
+
+typedef struct {
+  long long stripes, items;        /* jobs and 512-byte work items               */
+  long long bytes_in, bytes_out;   /* block bytes read and written per run       */
+  int programs;                    /* distinct programs                          */
+  int compiled_programs;           /* of which run by compiled modules           */
+  int launches;                    /* kernel launches per ec_batch_run           */
+  int modules_built;               /* modules compiled by ec_batch_create        */
+  double prepare_ms;               /* host time of ec_batch_create               */
+} ec_batch_info;
+
+/* Build the programs the jobs need (decode programs in parallel host
+ * threads), compile those without a compiled form into multi-program
+ * modules owned by their plan (executor EC_EXEC_AUTO / EC_EXEC_COMPILED),
+ * and upload the stripe descriptors and work-item list (device memory owned
+ * by the batch).  Block pointers are captured; the buffers must stay valid
+ * while the batch runs. */
+ec_status ec_batch_create(const ec_job *jobs, int n_jobs, int executor, ec_batch **out);
+/* Enqueue the batch on `stream`: one persistent launch per module plus at
+ * most one interpreter launch.  Allocates nothing (capturable). */
+ec_status ec_batch_run(ec_batch *batch, void *stream);
+ec_status ec_batch_info_get(const ec_batch *batch, ec_batch_info *out);
+void ec_batch_destroy(ec_batch *batch);
+/* create + run + synchronise + destroy. */
+ec_status ec_run_batch(const ec_job *jobs, int n_jobs, void *stream);
+
 /* Device status word written by kernels whose bounded waits gave up:
  * *status = 0 (ok) or EC_ETIMEOUT.  reset != 0 clears it.  Synchronises the
  * current device. */

@@ -177,6 +177,55 @@ def ec_decode_prepare(plan: int, sets, n_threads: int = 0) -> None:
                                    n_threads))
 
 
+EC_OP_ENCODE = _abi.EC_OP_ENCODE
+EC_OP_DECODE = _abi.EC_OP_DECODE
+
+
+def _jobs(jobs):
+    """jobs: dicts with plan, op, blocks (pointer list), out (pointer list),
+    block_bytes and, for decodes, erasures.  Returns the ctypes array and
+    the objects that must stay alive while it is used."""
+    arr = (_abi.Job * max(1, len(jobs)))()
+    keep = []
+    for i, j in enumerate(jobs):
+        er = j.get("erasures") or []
+        era = _int_array(er)
+        bl = _vp_array(j["blocks"])
+        ou = _vp_array(j["out"])
+        keep += [era, bl, ou]
+        arr[i] = _abi.Job(j["plan"], j.get("op", EC_OP_ENCODE),
+                          ctypes.cast(era, _abi.intp), len(er),
+                          ctypes.cast(bl, _abi.vpp), ctypes.cast(ou, _abi.vpp),
+                          j["block_bytes"])
+    return arr, keep
+
+
+def ec_batch_create(jobs, executor: int = EC_EXEC_AUTO) -> int:
+    arr, keep = _jobs(jobs)
+    h = ctypes.c_void_p()
+    _check(lib().ec_batch_create(arr, len(jobs), executor, ctypes.byref(h)))
+    return h.value
+
+
+def ec_batch_run(batch: int, stream: int = 0) -> None:
+    _check(lib().ec_batch_run(batch, stream or None))
+
+
+def ec_batch_info_get(batch: int) -> dict:
+    i = _abi.BatchInfo()
+    _check(lib().ec_batch_info_get(batch, ctypes.byref(i)))
+    return {f: getattr(i, f) for f, _ in _abi.BatchInfo._fields_}
+
+
+def ec_batch_destroy(batch: int) -> None:
+    lib().ec_batch_destroy(batch)
+
+
+def ec_run_batch(jobs, stream: int = 0) -> None:
+    arr, keep = _jobs(jobs)
+    _check(lib().ec_run_batch(arr, len(jobs), stream or None))
+
+
 def ec_device_status(reset: bool = False) -> int:
     st = ctypes.c_int()
     _check(lib().ec_device_status(ctypes.byref(st), 1 if reset else 0))

@@ -51,6 +51,21 @@ class ProgramInfo(ctypes.Structure):
                 ("regs", c_int), ("temps", c_int), ("max_live", c_int)]
 
 
+EC_OP_ENCODE, EC_OP_DECODE = 0, 1
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("plan", c_vp), ("op", c_int), ("erasures", intp), ("n_erasures", c_int),
+                ("blocks", vpp), ("out", vpp), ("block_bytes", c_size)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("stripes", ctypes.c_longlong), ("items", ctypes.c_longlong),
+                ("bytes_in", ctypes.c_longlong), ("bytes_out", ctypes.c_longlong),
+                ("programs", c_int), ("compiled_programs", c_int), ("launches", c_int),
+                ("modules_built", c_int), ("prepare_ms", ctypes.c_double)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/xorec.h
 SIGNATURES = {
     "ec_plan_create": (c_int, [c_int, c_int, u8p, ctypes.POINTER(c_vp)]),
@@ -68,6 +83,11 @@ SIGNATURES = {
     "ec_decode": (c_int, [c_vp, intp, c_int, vpp, vpp, c_size, c_vp]),
     "ec_decode_prepare": (c_int, [c_vp, intp, intp, c_int, c_int]),
     "ec_plan_set_executor": (c_int, [c_vp, c_int]),
+    "ec_batch_create": (c_int, [ctypes.POINTER(Job), c_int, c_int, ctypes.POINTER(c_vp)]),
+    "ec_batch_run": (c_int, [c_vp, c_vp]),
+    "ec_batch_info_get": (c_int, [c_vp, ctypes.POINTER(BatchInfo)]),
+    "ec_batch_destroy": (None, [c_vp]),
+    "ec_run_batch": (c_int, [ctypes.POINTER(Job), c_int, c_vp]),
     "ec_device_status": (c_int, [intp, c_int]),
     "ec_last_error": (c_char_p, []),
     "ec_version": (c_char_p, []),

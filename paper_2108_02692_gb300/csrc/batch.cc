@@ -1,0 +1,399 @@
+// Batched execution: many stripes with mixed codes, block sizes and
+// encode/decode programs in a few persistent launches.
+//
+// ec_batch_create builds every program the jobs need (decode programs in
+// parallel host threads, Sec. 1 inversion + Sec. 4-6 optimisation), compiles
+// the ones without a compiled form into multi-program modules (one module
+// per plan and input width, NVRTC, in parallel), and lays out in device
+// memory one descriptor per stripe and one record per work item (a 512-byte
+// tile of every strip of a stripe).  ec_batch_run then only launches: one
+// persistent launch per module plus one interpreter launch for programs
+// left to the interpreter; it allocates nothing and can be captured in a
+// CUDA graph.  Items are ordered stripe by stripe, largest stripes first
+// inside each launch, and CTAs take them round robin.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+using xorec::Program;
+
+namespace {
+
+constexpr int kThreads = 128;          // threads per CTA; tile = 4 * threads bytes
+constexpr int kTile = 4 * kThreads;
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+struct Launch {
+  void* mod = nullptr;                 // compiled module, or nullptr = interpreter
+  long long item_begin = 0, n_items = 0;
+  int max_in = 0, max_slots = 0;
+  size_t smem = 0;
+  int grid = 0;
+};
+
+template <class F>
+void parallel_for(size_t n, F f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(n, hw);
+  std::atomic<size_t> next{0};
+  std::vector<std::thread> pool;
+  for (size_t t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      for (;;) {
+        const size_t i = next.fetch_add(1);
+        if (i >= n) return;
+        f(i);
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
+}  // namespace
+
+struct ec_batch {
+  int device = -1;
+  std::vector<Launch> launches;
+  xk::StripeDesc* d_descs = nullptr;
+  unsigned* d_items = nullptr;
+  xk::u64* d_blocks = nullptr;
+  int* status = nullptr;
+  ec_batch_info info{};
+};
+
+namespace {
+
+struct Entry {
+  const ec_job* job;
+  ec_plan* plan;
+  Program* prog = nullptr;
+  std::vector<int> er;                 // sorted erasures (decode)
+  std::vector<uint64_t> ptrs;          // inputs then outputs (program order)
+  long long S = 0, tiles = 0;
+  int launch = -1;
+};
+
+ec_status check_job(const ec_job& j) {
+  if (!j.plan || !j.blocks || !j.out) return fail(EC_EINVAL, "job with NULL plan, blocks or out");
+  if (j.op != EC_OP_ENCODE && j.op != EC_OP_DECODE) return fail(EC_EINVAL, "bad job op");
+  if (j.block_bytes == 0 || j.block_bytes % 128 != 0)
+    return fail(EC_EINVAL, "block_bytes must be a positive multiple of 128");
+  return EC_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Block pointer list in program order (the same order ec_encode/ec_decode use).
+ec_status job_pointers(Entry* e) {
+  const ec_job& j = *e->job;
+  const int k = e->plan->k, m = e->plan->m;
+  if (j.op == EC_OP_ENCODE) {
+    for (int i = 0; i < k; ++i) {
+      if (!j.blocks[i] || !aligned16(j.blocks[i])) return fail(EC_EINVAL, "data block NULL or not 16-byte aligned");
+      e->ptrs.push_back(reinterpret_cast<uint64_t>(j.blocks[i]));
+    }
+    for (int i = 0; i < m; ++i) {
+      if (!j.out[i] || !aligned16(j.out[i])) return fail(EC_EINVAL, "parity block NULL or not 16-byte aligned");
+      e->ptrs.push_back(reinterpret_cast<uint64_t>(j.out[i]));
+    }
+    return EC_OK;
+  }
+  for (int id = 0, x = 0; id < k + m && static_cast<int>(e->ptrs.size()) < k; ++id) {
+    if (x < static_cast<int>(e->er.size()) && e->er[x] == id) { ++x; continue; }
+    if (!j.blocks[id] || !aligned16(j.blocks[id]))
+      return fail(EC_EINVAL, "surviving block NULL or not 16-byte aligned");
+    e->ptrs.push_back(reinterpret_cast<uint64_t>(j.blocks[id]));
+  }
+  for (int id : e->er) {
+    const int pos = static_cast<int>(std::find(j.erasures, j.erasures + j.n_erasures, id) - j.erasures);
+    if (!j.out[pos] || !aligned16(j.out[pos])) return fail(EC_EINVAL, "output block NULL or not 16-byte aligned");
+    e->ptrs.push_back(reinterpret_cast<uint64_t>(j.out[pos]));
+  }
+  return EC_OK;
+}
+
+void free_batch(ec_batch* b) {
+  if (b->d_descs) cudaFree(b->d_descs);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_blocks) cudaFree(b->d_blocks);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch** out) {
+  if (!out) return fail(EC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(EC_EINVAL, "bad job list");
+  if (executor < EC_EXEC_AUTO || executor > EC_EXEC_COMPILED) return fail(EC_EINVAL, "bad executor");
+  const auto t0 = std::chrono::steady_clock::now();
+  xorec::DeviceInfo di;
+  if (!xorec::device_info(&di)) return EC_ECUDA;
+
+  // 1. validate, canonicalise erasures
+  std::vector<Entry> ents(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    ec_status s = check_job(jobs[i]);
+    if (s != EC_OK) return s;
+    ents[i].job = &jobs[i];
+    ents[i].plan = jobs[i].plan;
+    if (jobs[i].op == EC_OP_DECODE) {
+      s = canon_erasures(jobs[i].plan, jobs[i].erasures, jobs[i].n_erasures, &ents[i].er);
+      if (s != EC_OK) return s;
+    }
+  }
+  // 2. programs (decode programs built in parallel, cached by the plan)
+  std::map<std::pair<ec_plan*, std::vector<int>>, Program*> dec;
+  for (auto& e : ents)
+    if (e.job->op == EC_OP_DECODE) dec[{e.plan, e.er}] = nullptr;
+  std::vector<std::pair<ec_plan*, std::vector<int>>> keys;
+  for (auto& kv : dec) keys.push_back(kv.first);
+  std::vector<Program*> built(keys.size(), nullptr);
+  std::atomic<int> rc{EC_OK};
+  parallel_for(keys.size(), [&](size_t i) {
+    Program* p = nullptr;
+    const ec_status s = get_decode_program(keys[i].first, keys[i].second, &p);
+    if (s != EC_OK) rc.store(s);
+    built[i] = p;
+  });
+  if (rc.load() != EC_OK) return static_cast<ec_status>(rc.load());
+  for (size_t i = 0; i < keys.size(); ++i) dec[keys[i]] = built[i];
+  for (auto& e : ents) {
+    e.prog = e.job->op == EC_OP_ENCODE ? e.plan->enc.get() : dec[{e.plan, e.er}];
+    ec_status s = job_pointers(&e);
+    if (s != EC_OK) return s;
+    e.S = static_cast<long long>(e.job->block_bytes / 8);
+    e.tiles = (e.S + kTile - 1) / kTile;
+  }
+
+  // 3. tiers: compile programs without a module (per plan, per input width)
+  bool compiled = executor != EC_EXEC_INTERP && xorec::jit_available();
+  if (executor == EC_EXEC_COMPILED && !compiled)
+    return fail(EC_ENOTSUP, "no run-time compiler available");
+  const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 16));
+  const int minb = env_int("EC_JIT_MINB", 4);
+  std::vector<std::pair<ec_plan*, std::vector<Program*>>> to_compile;
+  if (compiled) {
+    std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
+    std::vector<Program*> seen;
+    for (auto& e : ents) {
+      std::lock_guard<std::mutex> lk(e.plan->mu);
+      if (e.prog->mod || std::find(seen.begin(), seen.end(), e.prog) != seen.end()) continue;
+      seen.push_back(e.prog);
+      pending[{e.plan, e.prog->n_in}].push_back(e.prog);
+    }
+    for (auto& kv : pending)
+      for (size_t i = 0; i < kv.second.size(); i += module_size)
+        to_compile.emplace_back(
+            kv.first.first,
+            std::vector<Program*>(kv.second.begin() + i,
+                                  kv.second.begin() + std::min(kv.second.size(), i + module_size)));
+    std::vector<std::string> errs(to_compile.size());
+    std::vector<void*> mods(to_compile.size(), nullptr);
+    parallel_for(to_compile.size(), [&](size_t i) {
+      std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
+      mods[i] = xorec::jit_compile_module(ps, kThreads, minb, &errs[i]);
+    });
+    for (size_t i = 0; i < to_compile.size(); ++i) {
+      ec_plan* plan = to_compile[i].first;
+      std::lock_guard<std::mutex> lk(plan->mu);
+      if (!mods[i]) {
+        if (executor == EC_EXEC_COMPILED) {
+          for (void* m : mods) xorec::jit_module_release(m);
+          return fail(EC_ECUDA, "module compile failed: " + errs[i]);
+        }
+        continue;   // these programs stay with the interpreter
+      }
+      plan->modules.push_back(mods[i]);
+      for (size_t j = 0; j < to_compile[i].second.size(); ++j) {
+        to_compile[i].second[j]->mod = mods[i];
+        to_compile[i].second[j]->mod_index = static_cast<int>(j);
+      }
+    }
+  }
+
+  // 4. launches: one per module in use, one for the interpreter
+  auto b = new ec_batch();
+  b->device = di.device;
+  b->status = di.status;
+  std::map<void*, int> launch_of;
+  for (auto& e : ents) {
+    void* mod = compiled ? e.prog->mod : nullptr;
+    auto it = launch_of.find(mod);
+    if (it == launch_of.end()) {
+      it = launch_of.emplace(mod, static_cast<int>(b->launches.size())).first;
+      Launch L;
+      L.mod = mod;
+      b->launches.push_back(L);
+    }
+    e.launch = it->second;
+    Launch& L = b->launches[e.launch];
+    L.max_in = std::max(L.max_in, e.prog->n_in);
+    if (!mod) L.max_slots = std::max(L.max_slots, e.prog->n_slots);
+  }
+  // interpreter programs need their streams on the device
+  for (auto& e : ents)
+    if (!(compiled && e.prog->mod) && !xorec::ensure_device_code(e.prog)) {
+      free_batch(b);
+      return EC_ECUDA;
+    }
+
+  // 5. host layout: stripes grouped by launch, largest first
+  std::vector<int> order(ents.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    if (ents[a].launch != ents[c].launch) return ents[a].launch < ents[c].launch;
+    return ents[a].S > ents[c].S;
+  });
+  std::vector<xk::StripeDesc> descs(ents.size());
+  std::vector<unsigned> items;
+  std::vector<xk::u64> blocks;
+  long long bytes_in = 0, bytes_out = 0;
+  int cur = -1;
+  long long launch_begin = 0;
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    Entry& e = ents[order[oi]];
+    if (e.launch != cur) {
+      if (cur >= 0) b->launches[cur].n_items = static_cast<long long>(items.size()) - launch_begin;
+      cur = e.launch;
+      launch_begin = static_cast<long long>(items.size());
+      b->launches[cur].item_begin = launch_begin;
+    }
+    xk::StripeDesc& d = descs[oi];
+    std::memset(&d, 0, sizeof(d));
+    d.blocks = reinterpret_cast<const xk::u64*>(blocks.size() * sizeof(xk::u64));  // offset for now
+    d.S = e.S;
+    d.item_base = static_cast<long long>(items.size()) - launch_begin;
+    d.n_inblk = e.prog->n_in / 8;
+    d.n_outblk = e.prog->n_out / 8;
+    d.prog = e.prog->mod_index;
+    d.code = e.prog->d_code;
+    d.code_len = static_cast<int>(e.prog->code.size());
+    d.n_slots = e.prog->n_slots;
+    for (uint64_t p : e.ptrs) blocks.push_back(p);
+    for (long long t = 0; t < e.tiles; ++t) items.push_back(static_cast<unsigned>(oi));
+    bytes_in += static_cast<long long>(d.n_inblk) * static_cast<long long>(e.job->block_bytes);
+    bytes_out += static_cast<long long>(d.n_outblk) * static_cast<long long>(e.job->block_bytes);
+  }
+  if (cur >= 0) b->launches[cur].n_items = static_cast<long long>(items.size()) - launch_begin;
+
+  // 6. device copies (owned by the batch)
+  if (!ents.empty()) {
+    if (cudaMalloc(&b->d_descs, descs.size() * sizeof(xk::StripeDesc)) != cudaSuccess ||
+        cudaMalloc(&b->d_items, items.size() * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_blocks, std::max<size_t>(1, blocks.size()) * sizeof(xk::u64)) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(EC_ENOMEM, "device allocation of the batch tables failed");
+    }
+    for (auto& d : descs)
+      d.blocks = b->d_blocks + reinterpret_cast<uintptr_t>(d.blocks) / sizeof(xk::u64);
+    if (cudaMemcpy(b->d_descs, descs.data(), descs.size() * sizeof(xk::StripeDesc),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(unsigned),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_blocks, blocks.data(), blocks.size() * sizeof(xk::u64),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(EC_ECUDA, "upload of the batch tables failed");
+    }
+  }
+
+  // 7. launch shapes
+  int n_modules = 0, n_compiled_progs = 0;
+  for (auto& L : b->launches) {
+    int per_sm = 1;
+    if (L.mod) {
+      ++n_modules;
+      L.smem = 128 + static_cast<size_t>(L.max_in) * kTile;
+      per_sm = xorec::jit_module_ctas_per_sm(L.mod, L.smem);
+    } else {
+      L.smem = xorec::interp_batch_smem_bytes(L.max_in, L.max_slots, kTile);
+      if (L.smem > di.smem_optin) {
+        free_batch(b);
+        return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
+      }
+      per_sm = xorec::interp_batch_max_ctas_per_sm(kThreads, L.smem);
+    }
+    long long grid = static_cast<long long>(di.sms) * std::max(1, per_sm);
+    L.grid = static_cast<int>(std::min<long long>(grid, std::max<long long>(1, L.n_items)));
+  }
+  std::vector<Program*> progs;
+  for (auto& e : ents)
+    if (std::find(progs.begin(), progs.end(), e.prog) == progs.end()) {
+      progs.push_back(e.prog);
+      if (compiled && e.prog->mod) ++n_compiled_progs;
+    }
+  b->info.stripes = static_cast<long long>(ents.size());
+  b->info.items = static_cast<long long>(items.size());
+  b->info.bytes_in = bytes_in;
+  b->info.bytes_out = bytes_out;
+  b->info.programs = static_cast<int>(progs.size());
+  b->info.compiled_programs = n_compiled_progs;
+  b->info.launches = static_cast<int>(b->launches.size());
+  b->info.modules_built = static_cast<int>(to_compile.size());
+  b->info.prepare_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = b;
+  return EC_OK;
+}
+
+ec_status ec_batch_run(ec_batch* b, void* stream) {
+  if (!b) return fail(EC_EINVAL, "NULL batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (const auto& L : b->launches) {
+    if (L.n_items == 0) continue;
+    xk::BatchParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.stripes = b->d_descs;
+    bp.items = b->d_items + L.item_begin;
+    bp.n_items = L.n_items;
+    bp.T = kTile;
+    bp.max_in = L.max_in;
+    bp.status = b->status;
+    const bool ok = L.mod ? xorec::jit_module_launch(L.mod, bp, L.grid, L.smem, st)
+                          : xorec::launch_interp_batch(bp, kThreads, L.grid, L.smem, st);
+    if (!ok) return EC_ECUDA;
+  }
+  return EC_OK;
+}
+
+ec_status ec_batch_info_get(const ec_batch* b, ec_batch_info* out) {
+  if (!b || !out) return fail(EC_EINVAL, "NULL argument");
+  *out = b->info;
+  return EC_OK;
+}
+
+void ec_batch_destroy(ec_batch* b) {
+  if (b) free_batch(b);
+}
+
+ec_status ec_run_batch(const ec_job* jobs, int n_jobs, void* stream) {
+  ec_batch* b = nullptr;
+  ec_status s = ec_batch_create(jobs, n_jobs, EC_EXEC_AUTO, &b);
+  if (s != EC_OK) return s;
+  s = ec_batch_run(b, stream);
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && s == EC_OK) {
+    cudaGetLastError();
+    s = fail(EC_ECUDA, "batch execution failed");
+  }
+  ec_batch_destroy(b);
+  return s;
+}
+
+}  // extern "C"

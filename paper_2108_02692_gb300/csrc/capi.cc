@@ -159,10 +159,14 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
 
 namespace {
 
+}  // namespace
+
 ec_status fail(ec_status s, const std::string& msg) {
   xorec::set_error(msg);
   return s;
 }
+
+namespace {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -196,6 +200,8 @@ ec_status run_with_table(Program* p, const std::vector<uint64_t>& tab, int n_inb
   cudaFreeAsync(d, st);
   return ok ? EC_OK : EC_ECUDA;
 }
+
+}  // namespace
 
 // Decode program for a sorted erasure set (built on first use).
 ec_status get_decode_program(ec_plan* plan, const std::vector<int>& er, Program** out) {
@@ -240,6 +246,8 @@ ec_status canon_erasures(const ec_plan* plan, const int* erasures, int n, std::v
   *out = e;
   return EC_OK;
 }
+
+namespace {
 
 void release_program(Program* p) {
   if (!p) return;
@@ -305,6 +313,7 @@ ec_status ec_plan_create(int k, int m, const uint8_t* matrix, ec_plan** out) {
 
 void ec_plan_destroy(ec_plan* plan) {
   if (!plan) return;
+  for (void* mod : plan->modules) xorec::jit_module_release(mod);
   release_program(plan->enc.get());
   xorec::jit_release(plan->enc.get());
   for (auto& kv : plan->dec) {

@@ -20,60 +20,84 @@ namespace {
 
 using namespace xk;
 
+// Runs an instruction stream for one thread's 4-byte column of a tile.
+// in_col: the column in strip 0 of the stage; slots: base of the slot area;
+// out(r): address of output strip r at this column.
+template <class OutAddr>
+__device__ __forceinline__ void interpret(const u16* __restrict__ code, int code_len, int n_in, int T,
+                                          int col, const u8* in_col, u8* slots,
+                                          const OutAddr& out) {
+  // operand id -> address: inputs live in the stage, slots after it
+  u8* slot_col = slots + col - static_cast<i64>(n_in) * T;
+  int pc = 0;
+  while (pc < code_len) {
+    const int na = __ldg(code + pc);
+    const int w1 = __ldg(code + pc + 1);
+    pc += 2;
+    const int no = w1 & 0x7fff;
+    int slot = -1;
+    if (w1 & 0x8000) slot = __ldg(code + pc++);
+    const int ob = pc;
+    pc += no;
+    u32 acc = 0;
+    int a = 0;
+    for (; a + 4 <= na; a += 4) {
+      const int o0 = __ldg(code + pc + a), o1 = __ldg(code + pc + a + 1);
+      const int o2 = __ldg(code + pc + a + 2), o3 = __ldg(code + pc + a + 3);
+      const u32 x0 = *reinterpret_cast<const u32*>((o0 < n_in ? in_col : slot_col) + static_cast<i64>(o0) * T);
+      const u32 x1 = *reinterpret_cast<const u32*>((o1 < n_in ? in_col : slot_col) + static_cast<i64>(o1) * T);
+      const u32 x2 = *reinterpret_cast<const u32*>((o2 < n_in ? in_col : slot_col) + static_cast<i64>(o2) * T);
+      const u32 x3 = *reinterpret_cast<const u32*>((o3 < n_in ? in_col : slot_col) + static_cast<i64>(o3) * T);
+      acc ^= x0 ^ x1 ^ x2 ^ x3;
+    }
+    for (; a < na; ++a) {
+      const int o = __ldg(code + pc + a);
+      acc ^= *reinterpret_cast<const u32*>((o < n_in ? in_col : slot_col) + static_cast<i64>(o) * T);
+    }
+    pc += na;
+    if (slot >= 0) *reinterpret_cast<u32*>(slots + static_cast<i64>(slot) * T + col) = acc;
+    for (int o = 0; o < no; ++o) *reinterpret_cast<u32*>(out(__ldg(code + ob + o))) = acc;
+  }
+}
+
 struct InterpBody {
   static constexpr bool kEarlyRelease = false;
-  struct Regs {};
-  __device__ void load(const LaunchParams&, int, const u8*, Regs&) const {}
-  __device__ void compute(const LaunchParams&, i64, i64, int, Regs&) const {}
   __device__ __forceinline__ void operator()(const LaunchParams& p, i64 s, i64 c0, int len,
                                              const u8* stg, u8* slots) const {
     const int col = threadIdx.x * 4;
     if (col >= len) return;
-    const u16* __restrict__ code = p.code;
-    const int T = p.T;
-    const int n_in = p.n_in;
-    const u8* in_col = stg + col;
-    // operand id -> address: inputs live in the stage, slots after it
-    u8* slot_col = slots + col - static_cast<i64>(n_in) * T;
-    int pc = 0;
-    while (pc < p.code_len) {
-      const int na = __ldg(code + pc);
-      const int w1 = __ldg(code + pc + 1);
-      pc += 2;
-      const int no = w1 & 0x7fff;
-      int slot = -1;
-      if (w1 & 0x8000) slot = __ldg(code + pc++);
-      const int ob = pc;
-      pc += no;
-      u32 acc = 0;
-      int a = 0;
-      for (; a + 4 <= na; a += 4) {
-        const int o0 = __ldg(code + pc + a), o1 = __ldg(code + pc + a + 1);
-        const int o2 = __ldg(code + pc + a + 2), o3 = __ldg(code + pc + a + 3);
-        const u32 x0 = *reinterpret_cast<const u32*>((o0 < n_in ? in_col : slot_col) + static_cast<i64>(o0) * T);
-        const u32 x1 = *reinterpret_cast<const u32*>((o1 < n_in ? in_col : slot_col) + static_cast<i64>(o1) * T);
-        const u32 x2 = *reinterpret_cast<const u32*>((o2 < n_in ? in_col : slot_col) + static_cast<i64>(o2) * T);
-        const u32 x3 = *reinterpret_cast<const u32*>((o3 < n_in ? in_col : slot_col) + static_cast<i64>(o3) * T);
-        acc ^= x0 ^ x1 ^ x2 ^ x3;
-      }
-      for (; a < na; ++a) {
-        const int o = __ldg(code + pc + a);
-        acc ^= *reinterpret_cast<const u32*>((o < n_in ? in_col : slot_col) + static_cast<i64>(o) * T);
-      }
-      pc += na;
-      if (slot >= 0) *reinterpret_cast<u32*>(slots + static_cast<i64>(slot) * T + col) = acc;
-      for (int o = 0; o < no; ++o) {
-        const int r = __ldg(code + ob + o);
-        u8* dst = out_block(p.io, s, r >> 3) + static_cast<i64>(r & 7) * p.io.S + c0 + col;
-        *reinterpret_cast<u32*>(dst) = acc;
-      }
-    }
+    auto out = [&](int r) {
+      return out_block(p.io, s, r >> 3) + static_cast<i64>(r & 7) * p.io.S + c0 + col;
+    };
+    interpret(p.code, p.code_len, p.n_in, p.T, col, stg + col, slots, out);
+  }
+};
+
+struct InterpBatchBody {
+  static constexpr bool kEarlyRelease = false;
+  __device__ __forceinline__ void operator()(const StripeDesc& d, i64 c0, int len, const u8* stg,
+                                             u8* slots, int T) const {
+    const int col = threadIdx.x * 4;
+    if (col >= len) return;
+    const u64* outs = d.blocks + d.n_inblk;
+    auto out = [&](int r) {
+      return reinterpret_cast<u8*>(outs[r >> 3]) + static_cast<i64>(r & 7) * d.S + c0 + col;
+    };
+    interpret(d.code, d.code_len, 8 * d.n_inblk, T, col, stg + col, slots, out);
   }
 };
 
 __global__ void __launch_bounds__(256) interp_kernel(LaunchParams p) {
   extern __shared__ __align__(128) u8 smem[];
   run_pipeline(p, smem, InterpBody());
+}
+
+// Batched interpreter: shared memory = [barrier 128 B][stage: max_in * T]
+// [slots: the largest slot count of the launch * T].
+__global__ void __launch_bounds__(256) interp_batch_kernel(BatchParams p) {
+  extern __shared__ __align__(128) u8 smem[];
+  u8* slots = smem + 128 + static_cast<i64>(p.max_in) * p.T;
+  run_batch_pipeline(p, smem, InterpBatchBody(), slots);
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014) in counter form: byte n of stream
@@ -137,6 +161,37 @@ bool launch_interp(const xk::LaunchParams& lp, int threads, int grid, size_t sme
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("interpreter launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+size_t interp_batch_smem_bytes(int max_in, int max_slots, int T) {
+  return 128 + static_cast<size_t>(max_in) * T + static_cast<size_t>(max_slots) * T;
+}
+
+int interp_batch_max_ctas_per_sm(int threads, size_t smem) {
+  if (cudaFuncSetAttribute(interp_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, interp_batch_kernel, threads, smem) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_t smem,
+                         cudaStream_t stream) {
+  if (cudaFuncSetAttribute(interp_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess) {
+    set_error("cudaFuncSetAttribute(interp batch) failed");
+    return false;
+  }
+  interp_batch_kernel<<<grid, threads, smem, stream>>>(bp);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("batched interpreter launch failed: ") + cudaGetErrorString(e));
     return false;
   }
   return true;

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/xorec.h"
 #include "plan.h"
 #include "tile_pipeline.cuh"
 
@@ -20,9 +21,15 @@ struct ec_plan {
   xorec::PlanOptions opts;
   int executor = 0;                          // EC_EXEC_*
   std::unique_ptr<xorec::Program> enc;
-  std::mutex mu;                             // guards dec
+  std::mutex mu;                             // guards dec and modules
   std::map<std::vector<int>, std::unique_ptr<xorec::Program>> dec;  // key: sorted erasures
+  std::vector<void*> modules;                // compiled multi-program modules (batches)
 };
+
+// Shared by the C ABI translation units.
+ec_status fail(ec_status s, const std::string& msg);
+ec_status canon_erasures(const ec_plan* plan, const int* erasures, int n, std::vector<int>* out);
+ec_status get_decode_program(ec_plan* plan, const std::vector<int>& er, xorec::Program** out);
 
 namespace xorec {
 
@@ -56,6 +63,12 @@ bool launch_interp(const xk::LaunchParams& lp, int threads, int grid, size_t sme
 size_t interp_smem_bytes(int n_in, int n_slots, int T, int nstage);
 int interp_max_ctas_per_sm(int threads, size_t smem);
 
+// Batched interpreter (executor.cu).
+size_t interp_batch_smem_bytes(int max_in, int max_slots, int T);
+int interp_batch_max_ctas_per_sm(int threads, size_t smem);
+bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_t smem,
+                         cudaStream_t stream);
+
 // Compiled tier (jit.cc).
 bool jit_available();
 bool jit_compile(Program* p, int threads, std::string* err);
@@ -65,6 +78,13 @@ int jit_max_ctas_per_sm(Program* p, int threads, size_t smem);
 void jit_release(Program* p);
 int jit_regs(const Program* p);
 std::string jit_source(const Program& p, int threads);
+void* jit_compile_module(const std::vector<const Program*>& progs, int threads, int minb,
+                         std::string* err);
+int jit_module_ctas_per_sm(void* mod, size_t smem);
+bool jit_module_launch(void* mod, const xk::BatchParams& bp, int grid, size_t smem,
+                       cudaStream_t stream);
+void jit_module_release(void* mod);
+int jit_module_regs(void* mod);
 
 // Synthetic input generator (executor.cu).
 bool launch_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset,

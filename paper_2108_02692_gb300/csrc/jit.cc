@@ -32,13 +32,39 @@ struct JitKernel {
   int device = -1;
 };
 
-// The straight-line body.  load(): each thread copies its 4-byte column of
-// every input strip from the stage into registers.  compute(): one SSA
-// register per scheduled statement, stores to the output strips as soon as
-// a returned value is ready.
-std::string gen_body(const xorec::Program& p, int threads) {
+// Straight-line statements of a scheduled program: one SSA register per
+// statement, stores to output strip t of output block b through O(b, t, v)
+// as soon as a returned value is ready.  Inputs come from I(c).
+void emit_statements(std::ostringstream& os, const xorec::Program& p) {
   const xorec::Slp& q = p.fused;
   const int nc = q.n_const;
+  std::vector<std::vector<int>> outs_of(q.n_var);
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
+    if (q.ret[r] >= nc) outs_of[q.ret[r] - nc].push_back(r);
+  for (const auto& st : p.sched.steps) {
+    os << "    const xk::u32 v" << st.node << " = ";
+    if (st.args.empty()) os << "0u";
+    for (size_t i = 0; i < st.args.size(); ++i) {
+      const int a = st.args[i];
+      if (i) os << " ^ ";
+      if (a < nc) os << "I(" << a << ")";
+      else os << "v" << (a - nc);
+    }
+    os << ";\n";
+    for (int r : outs_of[st.node]) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", v" << st.node << ");\n";
+  }
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r) {
+    const int t = q.ret[r];
+    if (t < 0) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", 0u);\n";
+    else if (t < nc) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", I(" << t << "));\n";
+  }
+}
+
+// Single-program body.  load(): each thread copies its 4-byte column of
+// every input strip from the stage into registers.  compute(): the
+// statements, from registers.
+std::string gen_body(const xorec::Program& p, int threads) {
+  const int nc = p.fused.n_const;
   const int T = 4 * threads;
   std::ostringstream os;
   os << "struct SlpBody {\n"
@@ -61,27 +87,58 @@ std::string gen_body(const xorec::Program& p, int threads) {
     os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
   os << "#define I(c) r.x[c]\n";
   os << "#define O(b, t, v) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
-  std::vector<std::vector<int>> outs_of(q.n_var);
-  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
-    if (q.ret[r] >= nc) outs_of[q.ret[r] - nc].push_back(r);
-  for (const auto& st : p.sched.steps) {
-    os << "    const xk::u32 v" << st.node << " = ";
-    if (st.args.empty()) os << "0u";
-    for (size_t i = 0; i < st.args.size(); ++i) {
-      const int a = st.args[i];
-      if (i) os << " ^ ";
-      if (a < nc) os << "I(" << a << ")";
-      else os << "v" << (a - nc);
-    }
-    os << ";\n";
-    for (int r : outs_of[st.node]) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", v" << st.node << ");\n";
-  }
-  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r) {
-    const int t = q.ret[r];
-    if (t < 0) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", 0u);\n";
-    else if (t < nc) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", I(" << t << "));\n";
-  }
+  emit_statements(os, p);
   os << "#undef I\n#undef O\n  }\n};\n";
+  return os.str();
+}
+
+// Multi-program module for batched launches: all programs share n_in; the
+// stripe descriptor names the program (d.prog) and the output blocks.
+std::string gen_module_source(const std::vector<const xorec::Program*>& progs, int threads,
+                              int minb) {
+  const int nc = progs.front()->n_in;
+  const int T = 4 * threads;
+  std::ostringstream os;
+  os << kPipelineSrc << "\n";
+  for (size_t i = 0; i < progs.size(); ++i) {
+    os << "__device__ __forceinline__ void prog_" << i
+       << "(const xk::StripeDesc& d, xk::i64 c0, int col, const xk::u32* x) {\n"
+          "    const xk::i64 S = d.S;\n";
+    for (int b = 0; b < progs[i]->n_out / 8; ++b)
+      os << "    xk::u8* ob" << b << " = reinterpret_cast<xk::u8*>(d.blocks[d.n_inblk + " << b
+         << "]) + c0 + col;\n";
+    os << "#define I(c) x[c]\n";
+    os << "#define O(b, t, v) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
+    emit_statements(os, *progs[i]);
+    os << "#undef I\n#undef O\n}\n";
+  }
+  os << "struct ModBody {\n"
+        "  static constexpr bool kEarlyRelease = true;\n"
+        "  struct Regs { xk::u32 x[" << nc << "]; };\n"
+        "  __device__ __forceinline__ void load(const xk::StripeDesc&, int len, const xk::u8* stg,\n"
+        "                                       Regs& r) const {\n"
+        "    const int col = threadIdx.x * 4;\n"
+        "    if (col >= len) return;\n"
+        "    const xk::u8* in = stg + col;\n";
+  for (int c = 0; c < nc; ++c)
+    os << "    r.x[" << c << "] = *reinterpret_cast<const xk::u32*>(in + " << c * T << ");\n";
+  os << "  }\n"
+        "  __device__ __forceinline__ void compute(const xk::StripeDesc& d, xk::i64 c0, int len,\n"
+        "                                          Regs& r) const {\n"
+        "    const int col = threadIdx.x * 4;\n"
+        "    if (col >= len) return;\n"
+        "    switch (d.prog) {\n";
+  for (size_t i = 0; i < progs.size(); ++i)
+    os << "      case " << i << ": prog_" << i << "(d, c0, col, r.x); break;\n";
+  os << "      default: break;\n"
+        "    }\n"
+        "  }\n"
+        "};\n";
+  os << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", " << minb
+     << ") xorec_mod(xk::BatchParams p) {\n"
+        "  extern __shared__ __align__(128) xk::u8 smem[];\n"
+        "  xk::run_batch_pipeline(p, smem, ModBody(), nullptr);\n"
+        "}\n";
   return os.str();
 }
 
@@ -111,65 +168,6 @@ bool jit_available() {
   return nvrtcVersion(&major, &minor) == NVRTC_SUCCESS;
 }
 
-// Compile `p` for the current device's architecture.  Stores a JitKernel in
-// p->jit on success.
-bool jit_compile(Program* p, int threads, std::string* err) {
-  if (p->jit) return true;
-  DeviceInfo di;
-  if (!device_info(&di)) {
-    *err = "no CUDA device";
-    return false;
-  }
-  cudaDeviceProp prop;
-  if (cudaGetDeviceProperties(&prop, di.device) != cudaSuccess) {
-    *err = "cudaGetDeviceProperties failed";
-    return false;
-  }
-  const std::string src = gen_source(*p, threads);
-  nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "xorec_slp.cu", 0, nullptr, nullptr) !=
-      NVRTC_SUCCESS) {
-    *err = "nvrtcCreateProgram failed";
-    return false;
-  }
-  char arch[64];
-  std::snprintf(arch, sizeof(arch), "-arch=sm_%d%da", prop.major, prop.minor);
-  const char* opts[] = {arch, "-std=c++17", "-default-device", "--extra-device-vectorization"};
-  const nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
-  if (rc != NVRTC_SUCCESS) {
-    size_t n = 0;
-    nvrtcGetProgramLogSize(prog, &n);
-    std::string log(n, '\0');
-    nvrtcGetProgramLog(prog, &log[0]);
-    nvrtcDestroyProgram(&prog);
-    *err = "NVRTC compile failed: " + log.substr(0, 2000);
-    return false;
-  }
-  size_t nbin = 0;
-  nvrtcGetCUBINSize(prog, &nbin);
-  std::vector<char> cubin(nbin);
-  nvrtcGetCUBIN(prog, cubin.data());
-  nvrtcDestroyProgram(&prog);
-  auto* jk = new JitKernel();
-  if (cudaLibraryLoadData(&jk->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
-          cudaSuccess ||
-      cudaLibraryGetKernel(&jk->kern, jk->lib, "xorec_slp") != cudaSuccess) {
-    cudaGetLastError();
-    delete jk;
-    *err = "loading the compiled SLP kernel failed";
-    return false;
-  }
-  jk->threads = threads;
-  jk->device = di.device;
-  cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(jk->kern)) == cudaSuccess)
-    jk->regs = fa.numRegs;
-  else
-    cudaGetLastError();
-  p->jit = jk;
-  return true;
-}
-
 static bool jit_set_smem(JitKernel* jk, size_t smem) {
   if (jk->smem_set >= smem) return true;
   if (cudaKernelSetAttributeForDevice(jk->kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -179,6 +177,125 @@ static bool jit_set_smem(JitKernel* jk, size_t smem) {
   }
   jk->smem_set = smem;
   return true;
+}
+
+// NVRTC: source -> cubin for the current device -> loaded kernel `name`.
+static JitKernel* compile_and_load(const std::string& src, const char* name, int threads,
+                                   std::string* err) {
+  DeviceInfo di;
+  if (!device_info(&di)) {
+    *err = "no CUDA device";
+    return nullptr;
+  }
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, di.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, di.device) != cudaSuccess) {
+    *err = "cudaDeviceGetAttribute failed";
+    return nullptr;
+  }
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "xorec_slp.cu", 0, nullptr, nullptr) !=
+      NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return nullptr;
+  }
+  char arch[64];
+  std::snprintf(arch, sizeof(arch), "-arch=sm_%d%da", major, minor);
+  const char* opts[] = {arch, "-std=c++17", "-default-device", "--extra-device-vectorization"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
+  if (rc != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    nvrtcGetProgramLog(prog, &log[0]);
+    nvrtcDestroyProgram(&prog);
+    *err = "NVRTC compile failed: " + log.substr(0, 2000);
+    return nullptr;
+  }
+  size_t nbin = 0;
+  nvrtcGetCUBINSize(prog, &nbin);
+  std::vector<char> cubin(nbin);
+  nvrtcGetCUBIN(prog, cubin.data());
+  nvrtcDestroyProgram(&prog);
+  auto* jk = new JitKernel();
+  if (cudaLibraryLoadData(&jk->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
+          cudaSuccess ||
+      cudaLibraryGetKernel(&jk->kern, jk->lib, name) != cudaSuccess) {
+    cudaGetLastError();
+    delete jk;
+    *err = "loading the compiled SLP kernel failed";
+    return nullptr;
+  }
+  jk->threads = threads;
+  jk->device = di.device;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(jk->kern)) == cudaSuccess)
+    jk->regs = fa.numRegs;
+  else
+    cudaGetLastError();
+  return jk;
+}
+
+// Compile `p` for the current device's architecture.  Stores a JitKernel in
+// p->jit on success.
+bool jit_compile(Program* p, int threads, std::string* err) {
+  if (p->jit) return true;
+  JitKernel* jk = compile_and_load(gen_source(*p, threads), "xorec_slp", threads, err);
+  if (!jk) return false;
+  p->jit = jk;
+  return true;
+}
+
+// A module of programs sharing n_in (batched launches).
+void* jit_compile_module(const std::vector<const Program*>& progs, int threads, int minb,
+                         std::string* err) {
+  if (progs.empty()) {
+    *err = "empty module";
+    return nullptr;
+  }
+  return compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads, err);
+}
+
+int jit_module_ctas_per_sm(void* mod, size_t smem) {
+  auto* jk = static_cast<JitKernel*>(mod);
+  if (!jk || !jit_set_smem(jk, smem)) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, reinterpret_cast<const void*>(jk->kern),
+                                                    jk->threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n;
+}
+
+bool jit_module_launch(void* mod, const xk::BatchParams& bp, int grid, size_t smem,
+                       cudaStream_t stream) {
+  auto* jk = static_cast<JitKernel*>(mod);
+  if (!jk || !jit_set_smem(jk, smem)) {
+    set_error("compiled module missing or shared memory size refused");
+    return false;
+  }
+  xk::BatchParams copy = bp;
+  void* args[] = {&copy};
+  const cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(jk->kern), dim3(grid),
+                                         dim3(jk->threads), args, smem, stream);
+  if (e != cudaSuccess) {
+    set_error(std::string("compiled module launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+void jit_module_release(void* mod) {
+  auto* jk = static_cast<JitKernel*>(mod);
+  if (!jk) return;
+  cudaLibraryUnload(jk->lib);
+  delete jk;
+}
+
+int jit_module_regs(void* mod) {
+  auto* jk = static_cast<JitKernel*>(mod);
+  return jk ? jk->regs : 0;
 }
 
 int jit_max_ctas_per_sm(Program* p, int threads, size_t smem) {

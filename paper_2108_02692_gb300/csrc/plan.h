@@ -47,6 +47,9 @@ struct Program {
   uint16_t* d_code = nullptr;
   // compiled tier (set once a straight-line kernel exists for this program)
   void* jit = nullptr;
+  // multi-program module holding this program (batched launches)
+  void* mod = nullptr;
+  int mod_index = -1;
 };
 
 struct PlanOptions {

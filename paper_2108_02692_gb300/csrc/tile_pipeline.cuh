@@ -54,6 +54,29 @@ struct LaunchParams {
   int* status;
 };
 
+// Batched launches: every stripe has its own program, strip length and
+// blocks.  Work items are (stripe, tile) pairs listed in `items`.
+struct StripeDesc {
+  const u64* blocks;     // n_inblk input block addresses, then n_outblk outputs
+  i64 S;                 // strip bytes (block bytes / 8)
+  i64 item_base;         // index of the stripe's first item in the launch
+  const u16* code;       // interpreter stream of the stripe's program
+  int code_len;
+  int n_slots;
+  int n_inblk, n_outblk;
+  int prog;              // program index inside a compiled module
+  int pad_;
+};
+
+struct BatchParams {
+  const StripeDesc* stripes;
+  const unsigned* items;   // stripe index of each item (items of a stripe are consecutive)
+  i64 n_items;
+  int T;                   // tile bytes per strip
+  int max_in;              // largest n_in (strips) of the launch: stage size
+  int* status;
+};
+
 #if defined(__CUDACC__) || defined(__CUDACC_RTC__)
 
 __device__ __forceinline__ const u8* in_block(const IoDesc& io, i64 s, int b) {
@@ -206,6 +229,89 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
         if (tid == 0) fence_proxy_async();
         __syncwarp();
         issue_item(p, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
+      }
+    }
+  }
+}
+
+// Batched pipeline: the same single-stage, early-release ring as
+// run_pipeline, but each item names its stripe, whose descriptor gives the
+// program, the strip length and the block addresses.  Body (for batches):
+//   kEarlyRelease == true:
+//     void load(const StripeDesc&, int len, const u8* stage, Regs&) const
+//     void compute(const StripeDesc&, i64 c0, int len, Regs&) const
+//   kEarlyRelease == false:
+//     void operator()(const StripeDesc&, i64 c0, int len, const u8* stage,
+//                     u8* slots, int T) const
+__device__ __forceinline__ void batch_item_geom(const BatchParams& p, i64 item, const StripeDesc*& d,
+                                                i64& c0, int& len) {
+  d = &p.stripes[p.items[item]];
+  c0 = (item - d->item_base) * p.T;
+  const i64 rest = d->S - c0;
+  len = rest < p.T ? static_cast<int>(rest) : p.T;
+}
+
+__device__ __forceinline__ void issue_batch_item(const BatchParams& p, i64 item, u8* dst, u32 bar) {
+  const StripeDesc* d;
+  i64 c0;
+  int len;
+  batch_item_geom(p, item, d, c0, len);
+  const int n_in = 8 * d->n_inblk;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(n_in) * static_cast<u32>(len));
+  __syncwarp();
+  for (int c = lane; c < n_in; c += 32) {
+    const u8* src = reinterpret_cast<const u8*>(d->blocks[c >> 3]) + static_cast<i64>(c & 7) * d->S + c0;
+    tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), src, static_cast<u32>(len), bar);
+  }
+}
+
+template <class Body>
+__device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* smem, const Body& body,
+                                                   u8* slots) {
+  u64* bar = reinterpret_cast<u64*>(smem);
+  u8* stage = smem + 128;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(smem_addr(bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const i64 first = blockIdx.x, step = gridDim.x;
+  if (tid < 32 && first < p.n_items) issue_batch_item(p, first, stage, smem_addr(bar));
+  for (i64 i = 0;; ++i) {
+    const i64 item = first + i * step;
+    if (item >= p.n_items) break;
+    const bool ok = mbar_wait(smem_addr(bar), static_cast<u32>(i & 1));
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(p.status, XK_STATUS_TIMEOUT);
+        mbar_wait(smem_addr(bar), static_cast<u32>(i & 1));
+      }
+      return;
+    }
+    const StripeDesc* d;
+    i64 c0;
+    int len;
+    batch_item_geom(p, item, d, c0, len);
+    const i64 nxt = item + step;
+    if constexpr (Body::kEarlyRelease) {
+      typename Body::Regs r;
+      body.load(*d, len, stage, r);
+      __syncthreads();
+      if (tid < 32 && nxt < p.n_items) {
+        if (tid == 0) fence_proxy_async();
+        __syncwarp();
+        issue_batch_item(p, nxt, stage, smem_addr(bar));
+      }
+      body.compute(*d, c0, len, r);
+    } else {
+      body(*d, c0, len, stage, slots, p.T);
+      __syncthreads();
+      if (tid < 32 && nxt < p.n_items) {
+        if (tid == 0) fence_proxy_async();
+        __syncwarp();
+        issue_batch_item(p, nxt, stage, smem_addr(bar));
       }
     }
   }
