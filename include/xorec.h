@@ -195,6 +195,12 @@ ec_status ec_decode(ec_plan *plan, const int *erasures, int n_erasures,
 ec_status ec_decode_prepare(ec_plan *plan, const int *sets, const int *counts, int n_sets,
                             int n_threads);
 
+/* Compile, in parallel host threads, the straight-line kernels of the
+ * encoder (n_sets == 0) or of the decoders of the given erasure sets (same
+ * layout as ec_decode_prepare), so that later calls do not compile. */
+ec_status ec_plan_compile(ec_plan *plan, const int *sets, const int *counts, int n_sets,
+                          int n_threads);
+
 /* Select the executor tier (EC_EXEC_*).  EC_EXEC_COMPILED fails with
  * EC_ENOTSUP when no run-time compiler is present. */
 ec_status ec_plan_set_executor(ec_plan *plan, int executor);

@@ -226,6 +226,14 @@ def ec_run_batch(jobs, stream: int = 0) -> None:
     _check(lib().ec_run_batch(arr, len(jobs), stream or None))
 
 
+def ec_plan_compile(plan: int, sets=None, n_threads: int = 0) -> None:
+    sets = sets or []
+    flat = [int(x) for s in sets for x in s]
+    counts = [len(s) for s in sets]
+    _check(lib().ec_plan_compile(plan, _int_array(flat), _int_array(counts), len(sets),
+                                 n_threads))
+
+
 def ec_device_status(reset: bool = False) -> int:
     st = ctypes.c_int()
     _check(lib().ec_device_status(ctypes.byref(st), 1 if reset else 0))

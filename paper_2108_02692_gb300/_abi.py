@@ -82,6 +82,7 @@ SIGNATURES = {
                                   c_size, c_vp]),
     "ec_decode": (c_int, [c_vp, intp, c_int, vpp, vpp, c_size, c_vp]),
     "ec_decode_prepare": (c_int, [c_vp, intp, intp, c_int, c_int]),
+    "ec_plan_compile": (c_int, [c_vp, intp, intp, c_int, c_int]),
     "ec_plan_set_executor": (c_int, [c_vp, c_int]),
     "ec_batch_create": (c_int, [ctypes.POINTER(Job), c_int, c_int, ctypes.POINTER(c_vp)]),
     "ec_batch_run": (c_int, [c_vp, c_vp]),

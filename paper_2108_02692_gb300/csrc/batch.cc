@@ -5,8 +5,8 @@
 // parallel host threads, Sec. 1 inversion + Sec. 4-6 optimisation), compiles
 // the ones without a compiled form into multi-program modules (one module
 // per plan and input width, NVRTC, in parallel), and lays out in device
-// memory one descriptor per stripe and one record per work item (a 512-byte
-// tile of every strip of a stripe).  ec_batch_run then only launches: one
+// memory one descriptor per stripe (work items are 512-byte tiles of every
+// strip of a stripe, numbered stripe after stripe).  ec_batch_run then only launches: one
 // persistent launch per module plus one interpreter launch for programs
 // left to the interpreter; it allocates nothing and can be captured in a
 // CUDA graph.  Items are ordered stripe by stripe, largest stripes first
@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -28,17 +29,21 @@ using xorec::Program;
 
 namespace {
 
-constexpr int kThreads = 128;          // threads per CTA; tile = 4 * threads bytes
-constexpr int kTile = 4 * kThreads;
 
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   return v && *v ? std::atoi(v) : dflt;
 }
 
+// Threads per CTA of batched launches (tile = 4 * threads bytes per strip)
+// and the occupancy the compiled modules are built for.
+int batch_threads() { return env_int("EC_BATCH_THREADS", 128); }
+int batch_minb() { return env_int("EC_BATCH_MINB", 512 / batch_threads()); }
+
 struct Launch {
   void* mod = nullptr;                 // compiled module, or nullptr = interpreter
-  long long item_begin = 0, n_items = 0;
+  int stripe_begin = 0, n_stripes = 0; // the launch's stripes in the descriptor array
+  long long n_items = 0;
   int max_in = 0, max_slots = 0;
   size_t smem = 0;
   int grid = 0;
@@ -66,8 +71,15 @@ void parallel_for(size_t n, F f) {
 struct ec_batch {
   int device = -1;
   std::vector<Launch> launches;
+  // launches fan out over these streams (fork/join through events) so that
+  // the tail of one persistent launch overlaps the start of the next
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
+  int chunk = 8;
+  int threads = 128;
+  xk::u64* d_queues = nullptr;         // one work-queue head per launch
   xk::StripeDesc* d_descs = nullptr;
-  unsigned* d_items = nullptr;
   xk::u64* d_blocks = nullptr;
   int* status = nullptr;
   ec_batch_info info{};
@@ -125,8 +137,11 @@ ec_status job_pointers(Entry* e) {
 }
 
 void free_batch(ec_batch* b) {
+  for (cudaStream_t st : b->lanes) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_descs) cudaFree(b->d_descs);
-  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_queues) cudaFree(b->d_queues);
   if (b->d_blocks) cudaFree(b->d_blocks);
   delete b;
 }
@@ -177,22 +192,26 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     ec_status s = job_pointers(&e);
     if (s != EC_OK) return s;
     e.S = static_cast<long long>(e.job->block_bytes / 8);
-    e.tiles = (e.S + kTile - 1) / kTile;
+    e.tiles = (e.S + 4 * batch_threads() - 1) / (4 * batch_threads());
   }
 
   // 3. tiers: compile programs without a module (per plan, per input width)
   bool compiled = executor != EC_EXEC_INTERP && xorec::jit_available();
   if (executor == EC_EXEC_COMPILED && !compiled)
     return fail(EC_ENOTSUP, "no run-time compiler available");
-  const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 16));
-  const int minb = env_int("EC_JIT_MINB", 4);
+  const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 32));
+  const int kThreads = batch_threads();
+  const int kTile = 4 * kThreads;
+  const int minb = batch_minb();
   std::vector<std::pair<ec_plan*, std::vector<Program*>>> to_compile;
   if (compiled) {
     std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
     std::vector<Program*> seen;
     for (auto& e : ents) {
       std::lock_guard<std::mutex> lk(e.plan->mu);
-      if (e.prog->mod || std::find(seen.begin(), seen.end(), e.prog) != seen.end()) continue;
+      if ((e.prog->mod && xorec::jit_module_threads(e.prog->mod) == kThreads) ||
+          std::find(seen.begin(), seen.end(), e.prog) != seen.end())
+        continue;
       seen.push_back(e.prog);
       pending[{e.plan, e.prog->n_in}].push_back(e.prog);
     }
@@ -230,6 +249,8 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   auto b = new ec_batch();
   b->device = di.device;
   b->status = di.status;
+  b->chunk = std::max(1, env_int("EC_BATCH_CHUNK", 2));
+  b->threads = kThreads;
   std::map<void*, int> launch_of;
   for (auto& e : ents) {
     void* mod = compiled ? e.prog->mod : nullptr;
@@ -260,24 +281,23 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     return ents[a].S > ents[c].S;
   });
   std::vector<xk::StripeDesc> descs(ents.size());
-  std::vector<unsigned> items;
   std::vector<xk::u64> blocks;
-  long long bytes_in = 0, bytes_out = 0;
+  long long bytes_in = 0, bytes_out = 0, total_items = 0;
   int cur = -1;
-  long long launch_begin = 0;
+  long long launch_items = 0;
   for (size_t oi = 0; oi < order.size(); ++oi) {
     Entry& e = ents[order[oi]];
     if (e.launch != cur) {
-      if (cur >= 0) b->launches[cur].n_items = static_cast<long long>(items.size()) - launch_begin;
       cur = e.launch;
-      launch_begin = static_cast<long long>(items.size());
-      b->launches[cur].item_begin = launch_begin;
+      launch_items = 0;
+      b->launches[cur].stripe_begin = static_cast<int>(oi);
     }
+    Launch& L = b->launches[cur];
     xk::StripeDesc& d = descs[oi];
     std::memset(&d, 0, sizeof(d));
     d.blocks = reinterpret_cast<const xk::u64*>(blocks.size() * sizeof(xk::u64));  // offset for now
     d.S = e.S;
-    d.item_base = static_cast<long long>(items.size()) - launch_begin;
+    d.item_base = launch_items;
     d.n_inblk = e.prog->n_in / 8;
     d.n_outblk = e.prog->n_out / 8;
     d.prog = e.prog->mod_index;
@@ -285,16 +305,18 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     d.code_len = static_cast<int>(e.prog->code.size());
     d.n_slots = e.prog->n_slots;
     for (uint64_t p : e.ptrs) blocks.push_back(p);
-    for (long long t = 0; t < e.tiles; ++t) items.push_back(static_cast<unsigned>(oi));
+    launch_items += e.tiles;
+    L.n_items = launch_items;
+    L.n_stripes += 1;
+    total_items += e.tiles;
     bytes_in += static_cast<long long>(d.n_inblk) * static_cast<long long>(e.job->block_bytes);
     bytes_out += static_cast<long long>(d.n_outblk) * static_cast<long long>(e.job->block_bytes);
   }
-  if (cur >= 0) b->launches[cur].n_items = static_cast<long long>(items.size()) - launch_begin;
 
   // 6. device copies (owned by the batch)
   if (!ents.empty()) {
     if (cudaMalloc(&b->d_descs, descs.size() * sizeof(xk::StripeDesc)) != cudaSuccess ||
-        cudaMalloc(&b->d_items, items.size() * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_queues, b->launches.size() * sizeof(xk::u64)) != cudaSuccess ||
         cudaMalloc(&b->d_blocks, std::max<size_t>(1, blocks.size()) * sizeof(xk::u64)) != cudaSuccess) {
       cudaGetLastError();
       free_batch(b);
@@ -304,8 +326,6 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       d.blocks = b->d_blocks + reinterpret_cast<uintptr_t>(d.blocks) / sizeof(xk::u64);
     if (cudaMemcpy(b->d_descs, descs.data(), descs.size() * sizeof(xk::StripeDesc),
                    cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(unsigned),
-                   cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_blocks, blocks.data(), blocks.size() * sizeof(xk::u64),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
@@ -314,13 +334,14 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     }
   }
 
-  // 7. launch shapes
+  // 7. launch shapes: persistent grids; launches of different modules are
+  // spread over a few lanes so that their tails overlap
   int n_modules = 0, n_compiled_progs = 0;
   for (auto& L : b->launches) {
     int per_sm = 1;
     if (L.mod) {
       ++n_modules;
-      L.smem = 128 + static_cast<size_t>(L.max_in) * kTile;
+      L.smem = xk::kBatchHeader + static_cast<size_t>(L.max_in) * kTile;
       per_sm = xorec::jit_module_ctas_per_sm(L.mod, L.smem);
     } else {
       L.smem = xorec::interp_batch_smem_bytes(L.max_in, L.max_slots, kTile);
@@ -330,8 +351,36 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       }
       per_sm = xorec::interp_batch_max_ctas_per_sm(kThreads, L.smem);
     }
-    long long grid = static_cast<long long>(di.sms) * std::max(1, per_sm);
+    const long long grid = static_cast<long long>(di.sms) * std::max(1, per_sm);
     L.grid = static_cast<int>(std::min<long long>(grid, std::max<long long>(1, L.n_items)));
+    if (env_int("XOREC_LOG", 0))
+      std::fprintf(stderr, "[xorec] batch launch: %s items=%lld max_in=%d smem=%zu ctas/sm=%d grid=%d regs=%d\n",
+                   L.mod ? "module" : "interp", L.n_items, L.max_in, L.smem, per_sm, L.grid,
+                   L.mod ? xorec::jit_module_regs(L.mod) : 0);
+  }
+  // largest launches first; lanes for concurrent launches
+  std::stable_sort(b->launches.begin(), b->launches.end(),
+                   [](const Launch& x, const Launch& y) { return x.n_items > y.n_items; });
+  const int n_lanes = std::min<int>(static_cast<int>(b->launches.size()),
+                                    std::max(1, env_int("EC_BATCH_LANES", 4)));
+  if (n_lanes > 1) {
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(EC_ECUDA, "cudaEventCreate failed");
+    }
+    for (int i = 0; i < n_lanes; ++i) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return fail(EC_ECUDA, "stream or event creation failed");
+      }
+      b->lanes.push_back(st);
+      b->done.push_back(ev);
+    }
   }
   std::vector<Program*> progs;
   for (auto& e : ents)
@@ -340,7 +389,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       if (compiled && e.prog->mod) ++n_compiled_progs;
     }
   b->info.stripes = static_cast<long long>(ents.size());
-  b->info.items = static_cast<long long>(items.size());
+  b->info.items = total_items;
   b->info.bytes_in = bytes_in;
   b->info.bytes_out = bytes_out;
   b->info.programs = static_cast<int>(progs.size());
@@ -354,21 +403,42 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
 }
 
 ec_status ec_batch_run(ec_batch* b, void* stream) {
+  const int kThreads = b->threads;
   if (!b) return fail(EC_EINVAL, "NULL batch");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  for (const auto& L : b->launches) {
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (b->launches.empty()) return EC_OK;
+  if (cudaMemsetAsync(b->d_queues, 0, b->launches.size() * sizeof(xk::u64), caller) != cudaSuccess)
+    return fail(EC_ECUDA, "resetting the work queues failed");
+  const bool fan = !b->lanes.empty();
+  if (fan) {
+    if (cudaEventRecord(b->fork, caller) != cudaSuccess) return fail(EC_ECUDA, "cudaEventRecord failed");
+    for (cudaStream_t ln : b->lanes)
+      if (cudaStreamWaitEvent(ln, b->fork, 0) != cudaSuccess) return fail(EC_ECUDA, "cudaStreamWaitEvent failed");
+  }
+  for (size_t li = 0; li < b->launches.size(); ++li) {
+    const Launch& L = b->launches[li];
+    cudaStream_t st = fan ? b->lanes[li % b->lanes.size()] : caller;
     if (L.n_items == 0) continue;
     xk::BatchParams bp;
     std::memset(&bp, 0, sizeof(bp));
-    bp.stripes = b->d_descs;
-    bp.items = b->d_items + L.item_begin;
+    bp.stripes = b->d_descs + L.stripe_begin;
+    bp.n_stripes = L.n_stripes;
+    bp.chunk = b->chunk;
+    bp.queue = b->d_queues + li;
     bp.n_items = L.n_items;
-    bp.T = kTile;
+    bp.T = 4 * kThreads;
     bp.max_in = L.max_in;
     bp.status = b->status;
     const bool ok = L.mod ? xorec::jit_module_launch(L.mod, bp, L.grid, L.smem, st)
                           : xorec::launch_interp_batch(bp, kThreads, L.grid, L.smem, st);
     if (!ok) return EC_ECUDA;
+  }
+  if (fan) {
+    for (size_t i = 0; i < b->lanes.size(); ++i) {
+      if (cudaEventRecord(b->done[i], b->lanes[i]) != cudaSuccess ||
+          cudaStreamWaitEvent(caller, b->done[i], 0) != cudaSuccess)
+        return fail(EC_ECUDA, "joining the batch lanes failed");
+    }
   }
   return EC_OK;
 }

@@ -84,6 +84,32 @@ static int env_int(const char* name, int dflt) {
 
 static std::mutex g_jit_mu;
 
+// Compile p's straight-line kernel once.  The compile itself runs without
+// the lock so that several programs can compile at the same time.
+bool jit_ensure(Program* p, int threads, std::string* err) {
+  {
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    if (p->jit) return true;
+  }
+  if (!jit_available()) {
+    *err = "no run-time compiler";
+    return false;
+  }
+  Program tmp;   // compile into a scratch holder, then publish
+  tmp.fused = p->fused;
+  tmp.sched = p->sched;
+  tmp.n_in = p->n_in;
+  tmp.n_out = p->n_out;
+  if (!jit_compile(&tmp, threads, err)) return false;
+  std::lock_guard<std::mutex> lk(g_jit_mu);
+  if (p->jit) {
+    jit_release(&tmp);   // another thread won
+  } else {
+    p->jit = tmp.jit;
+  }
+  return true;
+}
+
 bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t stream) {
   DeviceInfo di;
   if (!device_info(&di)) return false;
@@ -94,10 +120,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     threads = env_int("EC_JIT_THREADS", 128);
     nstage = env_int("EC_JIT_NSTAGE", 1);
     std::string err;
-    {
-      std::lock_guard<std::mutex> lk(g_jit_mu);
-      compiled = p->jit != nullptr || (jit_available() && jit_compile(p, threads, &err));
-    }
+    compiled = jit_ensure(p, threads, &err);
     if (!compiled && executor == EC_EXEC_COMPILED) {
       set_error("compiled tier unavailable: " + err);
       return false;
@@ -493,6 +516,53 @@ ec_status ec_decode_prepare(ec_plan* plan, const int* sets, const int* counts, i
     });
   for (auto& th : pool) th.join();
   return static_cast<ec_status>(rc.load());
+}
+
+ec_status ec_plan_compile(ec_plan* plan, const int* sets, const int* counts, int n_sets,
+                          int n_threads) {
+  if (!plan || (n_sets > 0 && (!sets || !counts))) return fail(EC_EINVAL, "NULL argument");
+  if (!xorec::jit_available()) return fail(EC_ENOTSUP, "no run-time compiler available");
+  std::vector<Program*> progs;
+  if (n_sets == 0) progs.push_back(plan->enc.get());
+  size_t off = 0;
+  for (int i = 0; i < n_sets; ++i) {
+    std::vector<int> er;
+    ec_status s = canon_erasures(plan, sets + off, counts[i], &er);
+    if (s != EC_OK) return s;
+    off += counts[i];
+    Program* p = nullptr;
+    s = get_decode_program(plan, er, &p);
+    if (s != EC_OK) return s;
+    if (std::find(progs.begin(), progs.end(), p) == progs.end()) progs.push_back(p);
+  }
+  xorec::DeviceInfo di;
+  if (!xorec::device_info(&di)) return EC_ECUDA;
+  if (n_threads <= 0) n_threads = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+  const int threads = [] {
+    const char* v = std::getenv("EC_JIT_THREADS");
+    return v && *v ? std::atoi(v) : 128;
+  }();
+  std::atomic<size_t> next{0};
+  std::atomic<int> rc{EC_OK};
+  std::string first_err;
+  std::mutex err_mu;
+  std::vector<std::thread> pool;
+  for (int t = 0; t < n_threads; ++t)
+    pool.emplace_back([&]() {
+      for (;;) {
+        const size_t i = next.fetch_add(1);
+        if (i >= progs.size()) return;
+        std::string err;
+        if (!xorec::jit_ensure(progs[i], threads, &err)) {
+          rc.store(EC_ECUDA);
+          std::lock_guard<std::mutex> lk(err_mu);
+          if (first_err.empty()) first_err = err;
+        }
+      }
+    });
+  for (auto& th : pool) th.join();
+  if (rc.load() != EC_OK) return fail(EC_ECUDA, "compile failed: " + first_err);
+  return EC_OK;
 }
 
 ec_status ec_device_status(int* status, int reset) {

@@ -92,11 +92,11 @@ __global__ void __launch_bounds__(256) interp_kernel(LaunchParams p) {
   run_pipeline(p, smem, InterpBody());
 }
 
-// Batched interpreter: shared memory = [barrier 128 B][stage: max_in * T]
+// Batched interpreter: shared memory = [header][stage: max_in * T]
 // [slots: the largest slot count of the launch * T].
 __global__ void __launch_bounds__(256) interp_batch_kernel(BatchParams p) {
   extern __shared__ __align__(128) u8 smem[];
-  u8* slots = smem + 128 + static_cast<i64>(p.max_in) * p.T;
+  u8* slots = smem + kBatchHeader + static_cast<i64>(p.max_in) * p.T;
   run_batch_pipeline(p, smem, InterpBatchBody(), slots);
 }
 
@@ -167,7 +167,7 @@ bool launch_interp(const xk::LaunchParams& lp, int threads, int grid, size_t sme
 }
 
 size_t interp_batch_smem_bytes(int max_in, int max_slots, int T) {
-  return 128 + static_cast<size_t>(max_in) * T + static_cast<size_t>(max_slots) * T;
+  return xk::kBatchHeader + static_cast<size_t>(max_in) * T + static_cast<size_t>(max_slots) * T;
 }
 
 int interp_batch_max_ctas_per_sm(int threads, size_t smem) {

@@ -71,6 +71,7 @@ bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_
 
 // Compiled tier (jit.cc).
 bool jit_available();
+bool jit_ensure(Program* p, int threads, std::string* err);
 bool jit_compile(Program* p, int threads, std::string* err);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, int threads, int grid, size_t smem,
                 cudaStream_t stream);
@@ -85,6 +86,7 @@ bool jit_module_launch(void* mod, const xk::BatchParams& bp, int grid, size_t sm
                        cudaStream_t stream);
 void jit_module_release(void* mod);
 int jit_module_regs(void* mod);
+int jit_module_threads(void* mod);
 
 // Synthetic input generator (executor.cu).
 bool launch_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset,

@@ -293,6 +293,11 @@ void jit_module_release(void* mod) {
   delete jk;
 }
 
+int jit_module_threads(void* mod) {
+  auto* jk = static_cast<JitKernel*>(mod);
+  return jk ? jk->threads : 0;
+}
+
 int jit_module_regs(void* mod) {
   auto* jk = static_cast<JitKernel*>(mod);
   return jk ? jk->regs : 0;

@@ -69,13 +69,21 @@ struct StripeDesc {
 };
 
 struct BatchParams {
-  const StripeDesc* stripes;
-  const unsigned* items;   // stripe index of each item (items of a stripe are consecutive)
+  const StripeDesc* stripes;   // the launch's stripes; item_base is increasing
+  int n_stripes;
+  int chunk;                   // consecutive items a CTA takes from the queue at a time
+  u64* queue;                  // work queue head (chunks handed out), zero at launch
   i64 n_items;
   int T;                   // tile bytes per strip
   int max_in;              // largest n_in (strips) of the launch: stage size
   int* status;
 };
+
+// Shared-memory header of batched launches: the mbarrier (128 B) and the
+// table of the next item's source addresses (one per strip).
+constexpr int kMaxPrepared = 128;
+constexpr int kBatchHeader = 128 + 8 * kMaxPrepared;
+constexpr int kRing = 4;   // item ring in the header (bytes 64..95)
 
 #if defined(__CUDACC__) || defined(__CUDACC_RTC__)
 
@@ -243,26 +251,71 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
 //   kEarlyRelease == false:
 //     void operator()(const StripeDesc&, i64 c0, int len, const u8* stage,
 //                     u8* slots, int T) const
-__device__ __forceinline__ void batch_item_geom(const BatchParams& p, i64 item, const StripeDesc*& d,
-                                                i64& c0, int& len) {
-  d = &p.stripes[p.items[item]];
+// Item -> stripe.  A CTA visits its items in increasing order, so each
+// caller keeps a cursor into the stripe list and only moves it forward.
+__device__ __forceinline__ void batch_item_geom(const BatchParams& p, i64 item, int& cursor,
+                                                const StripeDesc*& d, i64& c0, int& len) {
+  while (cursor + 1 < p.n_stripes && p.stripes[cursor + 1].item_base <= item) ++cursor;
+  d = &p.stripes[cursor];
   c0 = (item - d->item_base) * p.T;
   const i64 rest = d->S - c0;
   len = rest < p.T ? static_cast<int>(rest) : p.T;
 }
 
-__device__ __forceinline__ void issue_batch_item(const BatchParams& p, i64 item, u8* dst, u32 bar) {
+// Source addresses of one batched item, computed by warp 0 ahead of the
+// copy into a small shared table (strip c -> src[c]), so that the copy can
+// be issued without waiting on descriptor loads.  Codes wider than
+// kMaxPrepared strips are addressed at issue time instead.
+struct NextCopy {
+  u32 bytes;     // n_in * len (expected transaction bytes)
+  u32 len;
+  int n_in;
+};
+
+// First stripe cursor for `item` (binary search over item_base).
+__device__ __forceinline__ int find_stripe(const BatchParams& p, i64 item) {
+  int lo = 0, hi = p.n_stripes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.stripes[mid].item_base <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void prepare_batch_item(const BatchParams& p, i64 item, int& cursor,
+                                                   NextCopy& nc, const u8** src) {
   const StripeDesc* d;
   i64 c0;
   int len;
-  batch_item_geom(p, item, d, c0, len);
+  batch_item_geom(p, item, cursor, d, c0, len);
   const int n_in = 8 * d->n_inblk;
   const int lane = threadIdx.x & 31;
-  if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(n_in) * static_cast<u32>(len));
+  if (n_in <= kMaxPrepared)
+    for (int c = lane; c < n_in; c += 32)
+      src[c] = reinterpret_cast<const u8*>(d->blocks[c >> 3]) + static_cast<i64>(c & 7) * d->S + c0;
+  nc.len = static_cast<u32>(len);
+  nc.n_in = n_in;
+  nc.bytes = static_cast<u32>(n_in) * static_cast<u32>(len);
+}
+
+__device__ __forceinline__ void issue_batch_prepared(const BatchParams& p, i64 item, int cursor,
+                                                     const NextCopy& nc, const u8* const* src,
+                                                     u8* dst, u32 bar) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_arrive_expect_tx(bar, nc.bytes);
   __syncwarp();
-  for (int c = lane; c < n_in; c += 32) {
-    const u8* src = reinterpret_cast<const u8*>(d->blocks[c >> 3]) + static_cast<i64>(c & 7) * d->S + c0;
-    tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), src, static_cast<u32>(len), bar);
+  if (nc.n_in <= kMaxPrepared) {
+    for (int c = lane; c < nc.n_in; c += 32)
+      tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), src[c], nc.len, bar);
+    return;
+  }
+  const StripeDesc* d;
+  i64 c0;
+  int len;
+  batch_item_geom(p, item, cursor, d, c0, len);
+  for (int c = lane; c < nc.n_in; c += 32) {
+    const u8* s = reinterpret_cast<const u8*>(d->blocks[c >> 3]) + static_cast<i64>(c & 7) * d->S + c0;
+    tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), s, nc.len, bar);
   }
 }
 
@@ -270,18 +323,67 @@ template <class Body>
 __device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* smem, const Body& body,
                                                    u8* slots) {
   u64* bar = reinterpret_cast<u64*>(smem);
-  u8* stage = smem + 128;
+  const u8** src = reinterpret_cast<const u8**>(smem + 128);
+  u8* stage = smem + kBatchHeader;
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(smem_addr(bar), 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const i64 first = blockIdx.x, step = gridDim.x;
-  if (tid < 32 && first < p.n_items) issue_batch_item(p, first, stage, smem_addr(bar));
+  // Work queue: warp 0 pops chunks of `chunk` consecutive items from the
+  // launch's queue head (consecutive items mostly share a stripe, whose
+  // descriptor stays in L1, and each CTA streams long runs of every strip;
+  // popping on demand balances stripes of different cost).  Warp 0 works
+  // two items ahead: it publishes item indices in a ring in shared memory
+  // and keeps the source table of the next copy prepared, so that neither
+  // the queue nor the descriptors delay the barrier.
+  volatile i64* ring = reinterpret_cast<volatile i64*>(smem + 64);
+  const i64 n = p.n_items;
+  const i64 C = p.chunk > 0 ? p.chunk : 1;
+  i64 q_pos = 0, q_end = 0;   // warp 0: current chunk
+  auto pop = [&]() -> i64 {   // warp 0 (all lanes): next item of this CTA, -1 at the end
+    if (q_pos >= q_end) {
+      u64 c = 0;
+      if ((threadIdx.x & 31) == 0) c = atomicAdd(p.queue, 1ull);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      q_pos = static_cast<i64>(c) * C;
+      q_end = q_pos + C < n ? q_pos + C : n;
+      if (q_pos >= n) { q_end = q_pos; return -1; }
+    }
+    return q_pos++;
+  };
+  NextCopy nc;
+  int cur = 0, prep_cur = 0;   // stripe cursors of this item and of the prepared one
+  if (tid < 32) {
+    const i64 a = pop();
+    const i64 b2 = a >= 0 ? pop() : -1;
+    if (tid == 0) {
+      ring[0] = a;
+      ring[1] = b2;
+    }
+    if (a >= 0) {
+      prep_cur = find_stripe(p, a);
+      prepare_batch_item(p, a, prep_cur, nc, src);
+      __syncwarp();
+      issue_batch_prepared(p, a, prep_cur, nc, src, stage, smem_addr(bar));
+      __syncwarp();
+      if (b2 >= 0) prepare_batch_item(p, b2, prep_cur, nc, src);
+    }
+  }
+  __syncthreads();
+  {
+    const i64 a = ring[0];
+    cur = a >= 0 ? find_stripe(p, a) : 0;
+  }
   for (i64 i = 0;; ++i) {
-    const i64 item = first + i * step;
-    if (item >= p.n_items) break;
+    const i64 item = ring[i % kRing];
+    if (item < 0) break;
+    const i64 nxt = ring[(i + 1) % kRing];
+    const StripeDesc* d;
+    i64 c0;
+    int len;
+    batch_item_geom(p, item, cur, d, c0, len);
     const bool ok = mbar_wait(smem_addr(bar), static_cast<u32>(i & 1));
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
@@ -290,29 +392,31 @@ __device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* sme
       }
       return;
     }
-    const StripeDesc* d;
-    i64 c0;
-    int len;
-    batch_item_geom(p, item, d, c0, len);
-    const i64 nxt = item + step;
+    // warp 0, after the stage is free: issue the next copy, pop the item
+    // after it and prepare its sources
+    auto refill = [&]() {
+      if (tid < 32) {
+        if (nxt >= 0) {
+          if (tid == 0) fence_proxy_async();
+          __syncwarp();
+          issue_batch_prepared(p, nxt, prep_cur, nc, src, stage, smem_addr(bar));
+          __syncwarp();
+        }
+        const i64 after = nxt >= 0 ? pop() : -1;
+        if (tid == 0) ring[(i + 2) % kRing] = after;
+        if (after >= 0) prepare_batch_item(p, after, prep_cur, nc, src);
+      }
+    };
     if constexpr (Body::kEarlyRelease) {
       typename Body::Regs r;
       body.load(*d, len, stage, r);
       __syncthreads();
-      if (tid < 32 && nxt < p.n_items) {
-        if (tid == 0) fence_proxy_async();
-        __syncwarp();
-        issue_batch_item(p, nxt, stage, smem_addr(bar));
-      }
+      refill();
       body.compute(*d, c0, len, r);
     } else {
       body(*d, c0, len, stage, slots, p.T);
       __syncthreads();
-      if (tid < 32 && nxt < p.n_items) {
-        if (tid == 0) fence_proxy_async();
-        __syncwarp();
-        issue_batch_item(p, nxt, stage, smem_addr(bar));
-      }
+      refill();
     }
   }
 }
