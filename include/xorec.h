@@ -250,6 +250,45 @@ void ec_batch_destroy(ec_batch *batch);
 /* create + run + synchronise + destroy. */
 ec_status ec_run_batch(const ec_job *jobs, int n_jobs, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of encode/decode requests.  Jobs submitted from any
+ * thread are admitted while the block bytes of admitted, unfinished
+ * requests stay within hbm_budget (else EC_EBUSY: retry later).  A
+ * scheduler thread forms a batch from every request that arrived while
+ * earlier batches were on the GPU and launches it on one of `slots`
+ * streams, so that batches overlap on the device; completion events
+ * timestamp each request.  Job pointers are captured at submission; the
+ * buffers must stay valid until the ticket is returned by ec_server_poll. */
+typedef struct ec_server ec_server;
+
+typedef struct {
+  size_t hbm_budget;     /* bytes of request blocks admitted at once (0 = 32 GiB) */
+  int max_batch;         /* requests per batch (0 = 512)                          */
+  int slots;             /* batches in flight on separate streams (0 = 4)         */
+} ec_server_opts;
+
+typedef struct {
+  long long submitted, completed, rejected, failed;
+  long long batches, max_batch_seen;
+  long long bytes_in, bytes_out;   /* block bytes read / written by completed requests */
+  long long admitted_bytes;        /* currently admitted                             */
+  long long pending;               /* admitted, not yet launched                     */
+  int slots_busy;
+} ec_server_stats;
+
+ec_status ec_server_create(const ec_server_opts *opts, ec_server **out);
+/* Build and compile, before serving, the encoder and every decoder of up to
+ * max_erasures erasures of `plan`, so that no request waits for planning. */
+ec_status ec_server_warm(ec_server *server, ec_plan *plan, int max_erasures);
+ec_status ec_server_submit(ec_server *server, const ec_job *job, uint64_t *ticket);
+/* Up to max completed tickets (and their latency from submission, in
+ * microseconds) since the last call; *n_done receives the count. */
+ec_status ec_server_poll(ec_server *server, uint64_t *tickets, double *latency_us, int max,
+                         int *n_done);
+ec_status ec_server_stats_get(ec_server *server, ec_server_stats *out);
+/* Finish every admitted request, then free the server. */
+void ec_server_destroy(ec_server *server);
+
 /* Device status word written by kernels whose bounded waits gave up:
  * *status = 0 (ok) or EC_ETIMEOUT.  reset != 0 clears it.  Synchronises the
  * current device. */

@@ -234,6 +234,56 @@ def ec_plan_compile(plan: int, sets=None, n_threads: int = 0) -> None:
                                  n_threads))
 
 
+def ec_server_create(hbm_budget: int = 0, max_batch: int = 0, slots: int = 0) -> int:
+    h = ctypes.c_void_p()
+    opts = _abi.ServerOpts(hbm_budget, max_batch, slots)
+    _check(lib().ec_server_create(ctypes.byref(opts), ctypes.byref(h)))
+    return h.value
+
+
+def ec_server_warm(server: int, plan: int, max_erasures: int) -> None:
+    _check(lib().ec_server_warm(server, plan, max_erasures))
+
+
+def make_jobs(jobs):
+    """ctypes job array (and the objects it references) for repeated use."""
+    return _jobs(jobs)
+
+
+def ec_server_submit_raw(server: int, job_struct) -> int:
+    """Submit a prepared ctypes job; returns the ticket, 0 when the budget
+    is full (EC_EBUSY)."""
+    t = ctypes.c_uint64()
+    rc = lib().ec_server_submit(server, ctypes.byref(job_struct), ctypes.byref(t))
+    if rc == EC_EBUSY:
+        return 0
+    _check(rc)
+    return t.value
+
+
+def ec_server_submit(server: int, job) -> int:
+    arr, keep = _jobs([job])
+    return ec_server_submit_raw(server, arr[0])
+
+
+def ec_server_poll(server: int, max_n: int = 4096):
+    tickets = (ctypes.c_uint64 * max_n)()
+    lat = (ctypes.c_double * max_n)()
+    n = ctypes.c_int()
+    _check(lib().ec_server_poll(server, tickets, lat, max_n, ctypes.byref(n)))
+    return [(tickets[i], lat[i]) for i in range(n.value)]
+
+
+def ec_server_stats_get(server: int) -> dict:
+    s = _abi.ServerStats()
+    _check(lib().ec_server_stats_get(server, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in _abi.ServerStats._fields_}
+
+
+def ec_server_destroy(server: int) -> None:
+    lib().ec_server_destroy(server)
+
+
 def ec_device_status(reset: bool = False) -> int:
     st = ctypes.c_int()
     _check(lib().ec_device_status(ctypes.byref(st), 1 if reset else 0))

@@ -66,6 +66,16 @@ class BatchInfo(ctypes.Structure):
                 ("modules_built", c_int), ("prepare_ms", ctypes.c_double)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", c_size), ("max_batch", c_int), ("slots", c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in
+                ("submitted", "completed", "rejected", "failed", "batches", "max_batch_seen",
+                 "bytes_in", "bytes_out", "admitted_bytes", "pending")] + [("slots_busy", c_int)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/xorec.h
 SIGNATURES = {
     "ec_plan_create": (c_int, [c_int, c_int, u8p, ctypes.POINTER(c_vp)]),
@@ -89,6 +99,13 @@ SIGNATURES = {
     "ec_batch_info_get": (c_int, [c_vp, ctypes.POINTER(BatchInfo)]),
     "ec_batch_destroy": (None, [c_vp]),
     "ec_run_batch": (c_int, [ctypes.POINTER(Job), c_int, c_vp]),
+    "ec_server_create": (c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(c_vp)]),
+    "ec_server_warm": (c_int, [c_vp, c_vp, c_int]),
+    "ec_server_submit": (c_int, [c_vp, ctypes.POINTER(Job), ctypes.POINTER(c_u64)]),
+    "ec_server_poll": (c_int, [c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(ctypes.c_double),
+                               c_int, intp]),
+    "ec_server_stats_get": (c_int, [c_vp, ctypes.POINTER(ServerStats)]),
+    "ec_server_destroy": (None, [c_vp]),
     "ec_device_status": (c_int, [intp, c_int]),
     "ec_last_error": (c_char_p, []),
     "ec_version": (c_char_p, []),

@@ -148,6 +148,102 @@ void free_batch(ec_batch* b) {
 
 }  // namespace
 
+namespace xorec {
+
+// Program, sorted erasures and block pointers (program order) of one job.
+ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
+                      std::vector<uint64_t>* ptrs) {
+  ec_status s = check_job(j);
+  if (s != EC_OK) return s;
+  Entry e;
+  e.job = &j;
+  e.plan = j.plan;
+  if (j.op == EC_OP_DECODE) {
+    s = canon_erasures(j.plan, j.erasures, j.n_erasures, &e.er);
+    if (s != EC_OK) return s;
+    s = get_decode_program(j.plan, e.er, &e.prog);
+    if (s != EC_OK) return s;
+  } else {
+    e.prog = j.plan->enc.get();
+  }
+  s = job_pointers(&e);
+  if (s != EC_OK) return s;
+  *prog = e.prog;
+  *er = e.er;
+  *ptrs = e.ptrs;
+  return EC_OK;
+}
+
+int batch_threads_default() { return batch_threads(); }
+int batch_minb_default() { return batch_minb(); }
+
+// Compile every program of `want` that has no module for this block size
+// into modules of at most EC_BATCH_MODULE_SIZE programs (per plan and input
+// width, NVRTC, in parallel host threads).  Modules belong to their plan.
+ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, int threads,
+                          int minb, bool must, int* built) {
+  const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 32));
+  std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
+  std::vector<Program*> seen;
+  for (const auto& w : want) {
+    std::lock_guard<std::mutex> lk(w.first->mu);
+    if ((w.second->mod && jit_module_threads(w.second->mod) == threads) ||
+        std::find(seen.begin(), seen.end(), w.second) != seen.end())
+      continue;
+    seen.push_back(w.second);
+    pending[{w.first, w.second->n_in}].push_back(w.second);
+  }
+  std::vector<std::pair<ec_plan*, std::vector<Program*>>> to_compile;
+  for (auto& kv : pending)
+    for (size_t i = 0; i < kv.second.size(); i += module_size)
+      to_compile.emplace_back(
+          kv.first.first,
+          std::vector<Program*>(kv.second.begin() + i,
+                                kv.second.begin() + std::min(kv.second.size(), i + module_size)));
+  std::vector<std::string> errs(to_compile.size());
+  std::vector<void*> mods(to_compile.size(), nullptr);
+  parallel_for(to_compile.size(), [&](size_t i) {
+    std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
+    mods[i] = jit_compile_module(ps, threads, minb, &errs[i]);
+  });
+  if (built) *built = static_cast<int>(to_compile.size());
+  for (size_t i = 0; i < to_compile.size(); ++i) {
+    ec_plan* plan = to_compile[i].first;
+    std::lock_guard<std::mutex> lk(plan->mu);
+    if (!mods[i]) {
+      if (must) {
+        for (size_t j = i; j < mods.size(); ++j) jit_module_release(mods[j]);
+        return fail(EC_ECUDA, "module compile failed: " + errs[i]);
+      }
+      continue;   // these programs stay with the interpreter
+    }
+    plan->modules.push_back(mods[i]);
+    for (size_t j = 0; j < to_compile[i].second.size(); ++j) {
+      to_compile[i].second[j]->mod = mods[i];
+      to_compile[i].second[j]->mod_index = static_cast<int>(j);
+    }
+  }
+  return EC_OK;
+}
+
+// Shared memory and resident CTAs per SM of a batched launch (module or
+// interpreter).
+bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
+                        size_t* smem, int* per_sm) {
+  const int T = 4 * threads;
+  if (mod) {
+    *smem = xk::kBatchHeader + static_cast<size_t>(max_in) * T;
+    *per_sm = std::max(1, jit_module_ctas_per_sm(mod, *smem));
+    return true;
+  }
+  *smem = interp_batch_smem_bytes(max_in, max_slots, T);
+  if (*smem > smem_optin) return false;
+  *per_sm = std::max(1, interp_batch_max_ctas_per_sm(threads, *smem));
+  return true;
+}
+
+}  // namespace xorec
+
 extern "C" {
 
 ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch** out) {
@@ -199,50 +295,15 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   bool compiled = executor != EC_EXEC_INTERP && xorec::jit_available();
   if (executor == EC_EXEC_COMPILED && !compiled)
     return fail(EC_ENOTSUP, "no run-time compiler available");
-  const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 32));
   const int kThreads = batch_threads();
-  const int kTile = 4 * kThreads;
   const int minb = batch_minb();
-  std::vector<std::pair<ec_plan*, std::vector<Program*>>> to_compile;
+  int modules_built = 0;
   if (compiled) {
-    std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
-    std::vector<Program*> seen;
-    for (auto& e : ents) {
-      std::lock_guard<std::mutex> lk(e.plan->mu);
-      if ((e.prog->mod && xorec::jit_module_threads(e.prog->mod) == kThreads) ||
-          std::find(seen.begin(), seen.end(), e.prog) != seen.end())
-        continue;
-      seen.push_back(e.prog);
-      pending[{e.plan, e.prog->n_in}].push_back(e.prog);
-    }
-    for (auto& kv : pending)
-      for (size_t i = 0; i < kv.second.size(); i += module_size)
-        to_compile.emplace_back(
-            kv.first.first,
-            std::vector<Program*>(kv.second.begin() + i,
-                                  kv.second.begin() + std::min(kv.second.size(), i + module_size)));
-    std::vector<std::string> errs(to_compile.size());
-    std::vector<void*> mods(to_compile.size(), nullptr);
-    parallel_for(to_compile.size(), [&](size_t i) {
-      std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
-      mods[i] = xorec::jit_compile_module(ps, kThreads, minb, &errs[i]);
-    });
-    for (size_t i = 0; i < to_compile.size(); ++i) {
-      ec_plan* plan = to_compile[i].first;
-      std::lock_guard<std::mutex> lk(plan->mu);
-      if (!mods[i]) {
-        if (executor == EC_EXEC_COMPILED) {
-          for (void* m : mods) xorec::jit_module_release(m);
-          return fail(EC_ECUDA, "module compile failed: " + errs[i]);
-        }
-        continue;   // these programs stay with the interpreter
-      }
-      plan->modules.push_back(mods[i]);
-      for (size_t j = 0; j < to_compile[i].second.size(); ++j) {
-        to_compile[i].second[j]->mod = mods[i];
-        to_compile[i].second[j]->mod_index = static_cast<int>(j);
-      }
-    }
+    std::vector<std::pair<ec_plan*, Program*>> want;
+    for (auto& e : ents) want.emplace_back(e.plan, e.prog);
+    const ec_status cs = xorec::compile_modules(want, kThreads, minb, executor == EC_EXEC_COMPILED,
+                                                &modules_built);
+    if (cs != EC_OK) return cs;
   }
 
   // 4. launches: one per module in use, one for the interpreter
@@ -339,17 +400,11 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   int n_modules = 0, n_compiled_progs = 0;
   for (auto& L : b->launches) {
     int per_sm = 1;
-    if (L.mod) {
-      ++n_modules;
-      L.smem = xk::kBatchHeader + static_cast<size_t>(L.max_in) * kTile;
-      per_sm = xorec::jit_module_ctas_per_sm(L.mod, L.smem);
-    } else {
-      L.smem = xorec::interp_batch_smem_bytes(L.max_in, L.max_slots, kTile);
-      if (L.smem > di.smem_optin) {
-        free_batch(b);
-        return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
-      }
-      per_sm = xorec::interp_batch_max_ctas_per_sm(kThreads, L.smem);
+    if (L.mod) ++n_modules;
+    if (!xorec::batch_launch_shape(L.mod, L.max_in, L.max_slots, kThreads, di.smem_optin, &L.smem,
+                                   &per_sm)) {
+      free_batch(b);
+      return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
     }
     const long long grid = static_cast<long long>(di.sms) * std::max(1, per_sm);
     L.grid = static_cast<int>(std::min<long long>(grid, std::max<long long>(1, L.n_items)));
@@ -395,7 +450,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   b->info.programs = static_cast<int>(progs.size());
   b->info.compiled_programs = n_compiled_progs;
   b->info.launches = static_cast<int>(b->launches.size());
-  b->info.modules_built = static_cast<int>(to_compile.size());
+  b->info.modules_built = modules_built;
   b->info.prepare_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = b;

@@ -88,6 +88,16 @@ void jit_module_release(void* mod);
 int jit_module_regs(void* mod);
 int jit_module_threads(void* mod);
 
+// Batch helpers (batch.cc), shared with the serving loop.
+ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
+                      std::vector<uint64_t>* ptrs);
+int batch_threads_default();
+int batch_minb_default();
+ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, int threads,
+                          int minb, bool must, int* built);
+bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
+                        size_t* smem, int* per_sm);
+
 // Synthetic input generator (executor.cu).
 bool launch_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset,
                        cudaStream_t stream);

@@ -1,0 +1,404 @@
+// Serving loop: continuous batching of encode/decode requests on one GPU.
+//
+// Callers submit jobs (ec_server_submit) from any thread.  A request is
+// admitted only while the block bytes of all admitted, unfinished requests
+// stay within an HBM budget; otherwise EC_EBUSY tells the caller to retry.
+// One scheduler thread forms a batch from every request that arrived while
+// earlier batches were on the GPU, writes its stripe descriptors and block
+// table into the pinned staging of a free slot, copies them to the slot's
+// device tables and launches the batched pipeline (one persistent launch
+// per compiled module, the interpreter for programs without one) on the
+// slot's stream.  Several slots are in flight at once, so their work
+// overlaps on the device; a slot returns to the pool when its completion
+// event fires, which also timestamps every request in it (latency =
+// submission to observed completion) and frees its admitted bytes.  No
+// device memory is allocated per batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+using xorec::Program;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Req {
+  uint64_t ticket = 0;
+  Program* prog = nullptr;
+  std::vector<uint64_t> ptrs;
+  long long S = 0, tiles = 0;
+  size_t bytes = 0;
+  long long bytes_in = 0, bytes_out = 0;
+  Clock::time_point t0;
+};
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  std::vector<Req> reqs;
+  xk::StripeDesc* d_descs = nullptr;
+  xk::u64* d_blocks = nullptr;
+  xk::u64* d_queues = nullptr;
+  xk::StripeDesc* h_descs = nullptr;   // pinned staging
+  xk::u64* h_blocks = nullptr;
+  size_t cap_blocks = 0;
+};
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+}  // namespace
+
+struct ec_server {
+  int device = -1;
+  size_t budget = 0;
+  int max_batch = 0;
+  int threads = 128, minb = 4, chunk = 2;
+  xorec::DeviceInfo di;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Req> pending;
+  size_t admitted = 0;
+  std::vector<Slot> slots;
+  std::vector<std::pair<uint64_t, double>> done;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  int error = EC_OK;
+  std::thread th;
+  ec_server_stats stats{};
+  std::map<std::tuple<void*, int, int>, std::pair<size_t, int>> shapes;
+};
+
+namespace {
+
+void free_slot(Slot& s) {
+  if (s.st) cudaStreamDestroy(s.st);
+  if (s.done) cudaEventDestroy(s.done);
+  if (s.d_descs) cudaFree(s.d_descs);
+  if (s.d_blocks) cudaFree(s.d_blocks);
+  if (s.d_queues) cudaFree(s.d_queues);
+  if (s.h_descs) cudaFreeHost(s.h_descs);
+  if (s.h_blocks) cudaFreeHost(s.h_blocks);
+  s = Slot();
+}
+
+bool grow_blocks(Slot& s, size_t need) {
+  if (need <= s.cap_blocks) return true;
+  size_t cap = std::max(need, 2 * s.cap_blocks);
+  if (s.d_blocks) cudaFree(s.d_blocks);
+  if (s.h_blocks) cudaFreeHost(s.h_blocks);
+  s.d_blocks = nullptr;
+  s.h_blocks = nullptr;
+  if (cudaMalloc(&s.d_blocks, cap * sizeof(xk::u64)) != cudaSuccess ||
+      cudaMallocHost(&s.h_blocks, cap * sizeof(xk::u64)) != cudaSuccess) {
+    cudaGetLastError();
+    s.cap_blocks = 0;
+    return false;
+  }
+  s.cap_blocks = cap;
+  return true;
+}
+
+// Launch one batch of requests on a free slot.
+bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
+  // group by launch target: compiled module of this block size, or interpreter
+  auto target = [&](const Req& r) -> void* {
+    return r.prog->mod && xorec::jit_module_threads(r.prog->mod) == sv->threads ? r.prog->mod
+                                                                                : nullptr;
+  };
+  std::stable_sort(reqs.begin(), reqs.end(),
+                   [&](const Req& a, const Req& b) { return target(a) < target(b); });
+  size_t n_blocks = 0;
+  for (const auto& r : reqs) n_blocks += r.ptrs.size();
+  if (!grow_blocks(sl, n_blocks)) return false;
+  struct L { void* mod; int begin, n; long long items; int max_in, max_slots; };
+  std::vector<L> launches;
+  size_t off = 0;
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    const Req& r = reqs[i];
+    void* mod = target(r);
+    if (launches.empty() || launches.back().mod != mod)
+      launches.push_back(L{mod, static_cast<int>(i), 0, 0, 0, 0});
+    L& l = launches.back();
+    xk::StripeDesc& d = sl.h_descs[i];
+    std::memset(&d, 0, sizeof(d));
+    d.blocks = sl.d_blocks + off;
+    d.S = r.S;
+    d.item_base = l.items;
+    d.n_inblk = r.prog->n_in / 8;
+    d.n_outblk = r.prog->n_out / 8;
+    d.prog = r.prog->mod_index;
+    d.code = r.prog->d_code;
+    d.code_len = static_cast<int>(r.prog->code.size());
+    d.n_slots = r.prog->n_slots;
+    std::memcpy(sl.h_blocks + off, r.ptrs.data(), r.ptrs.size() * sizeof(xk::u64));
+    off += r.ptrs.size();
+    l.n += 1;
+    l.items += r.tiles;
+    l.max_in = std::max(l.max_in, r.prog->n_in);
+    if (!mod) l.max_slots = std::max(l.max_slots, r.prog->n_slots);
+  }
+  if (cudaMemcpyAsync(sl.d_descs, sl.h_descs, reqs.size() * sizeof(xk::StripeDesc),
+                      cudaMemcpyHostToDevice, sl.st) != cudaSuccess ||
+      cudaMemcpyAsync(sl.d_blocks, sl.h_blocks, n_blocks * sizeof(xk::u64), cudaMemcpyHostToDevice,
+                      sl.st) != cudaSuccess ||
+      cudaMemsetAsync(sl.d_queues, 0, launches.size() * sizeof(xk::u64), sl.st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (size_t li = 0; li < launches.size(); ++li) {
+    const L& l = launches[li];
+    auto key = std::make_tuple(l.mod, l.max_in, l.max_slots);
+    auto it = sv->shapes.find(key);
+    if (it == sv->shapes.end()) {
+      size_t smem = 0;
+      int per_sm = 1;
+      if (!xorec::batch_launch_shape(l.mod, l.max_in, l.max_slots, sv->threads, sv->di.smem_optin,
+                                     &smem, &per_sm))
+        return false;
+      it = sv->shapes.emplace(key, std::make_pair(smem, per_sm)).first;
+    }
+    xk::BatchParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.stripes = sl.d_descs + l.begin;
+    bp.n_stripes = l.n;
+    bp.chunk = sv->chunk;
+    bp.queue = sl.d_queues + li;
+    bp.n_items = l.items;
+    bp.T = 4 * sv->threads;
+    bp.max_in = l.max_in;
+    bp.status = sv->di.status;
+    const long long full = static_cast<long long>(sv->di.sms) * it->second.second;
+    const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(full, l.items)));
+    const bool ok = l.mod ? xorec::jit_module_launch(l.mod, bp, grid, it->second.first, sl.st)
+                          : xorec::launch_interp_batch(bp, sv->threads, grid, it->second.first, sl.st);
+    if (!ok) return false;
+  }
+  if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) return false;
+  sl.reqs = std::move(reqs);
+  sl.busy = true;
+  return true;
+}
+
+void scheduler(ec_server* sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    bool worked = false;
+    for (Slot& sl : sv->slots) {
+      if (!sl.busy) continue;
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      const auto now = Clock::now();
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (q != cudaSuccess) {
+        cudaGetLastError();
+        sv->error = EC_ECUDA;
+      }
+      for (const Req& r : sl.reqs) {
+        sv->done.emplace_back(r.ticket,
+                              std::chrono::duration<double, std::micro>(now - r.t0).count());
+        sv->admitted -= r.bytes;
+        sv->stats.completed += 1;
+        sv->stats.bytes_in += r.bytes_in;
+        sv->stats.bytes_out += r.bytes_out;
+      }
+      sl.reqs.clear();
+      sl.busy = false;
+      worked = true;
+    }
+    Slot* free_slot_p = nullptr;
+    int busy = 0;
+    for (Slot& sl : sv->slots) {
+      if (sl.busy) ++busy;
+      else if (!free_slot_p) free_slot_p = &sl;
+    }
+    std::vector<Req> take;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->stats.slots_busy = busy;
+      if (sv->stop && sv->pending.empty() && busy == 0) return;
+      if (free_slot_p && !sv->pending.empty()) {
+        while (!sv->pending.empty() && static_cast<int>(take.size()) < sv->max_batch) {
+          take.push_back(std::move(sv->pending.front()));
+          sv->pending.pop_front();
+        }
+      } else if (!worked && busy == 0) {
+        sv->cv.wait_for(lk, std::chrono::microseconds(200));
+        continue;
+      }
+    }
+    if (!take.empty()) {
+      const size_t n = take.size();
+      if (!dispatch(sv, *free_slot_p, std::move(take))) {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->error = EC_ECUDA;
+        sv->stats.failed += static_cast<long long>(n);
+      } else {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stats.batches += 1;
+        sv->stats.max_batch_seen = std::max<long long>(sv->stats.max_batch_seen, n);
+      }
+      worked = true;
+    }
+    if (!worked) std::this_thread::yield();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
+  if (!out) return fail(EC_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto sv = new ec_server();
+  if (!xorec::device_info(&sv->di)) {
+    delete sv;
+    return EC_ECUDA;
+  }
+  sv->device = sv->di.device;
+  sv->budget = opts && opts->hbm_budget ? opts->hbm_budget : (static_cast<size_t>(32) << 30);
+  sv->max_batch = opts && opts->max_batch > 0 ? opts->max_batch : 512;
+  const int n_slots = opts && opts->slots > 0 ? opts->slots : 4;
+  sv->threads = xorec::batch_threads_default();
+  sv->minb = xorec::batch_minb_default();
+  sv->chunk = std::max(1, env_int("EC_BATCH_CHUNK", 2));
+  sv->slots.resize(n_slots);
+  for (Slot& sl : sv->slots) {
+    if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&sl.d_descs, sv->max_batch * sizeof(xk::StripeDesc)) != cudaSuccess ||
+        cudaMalloc(&sl.d_queues, sv->max_batch * sizeof(xk::u64)) != cudaSuccess ||
+        cudaMallocHost(&sl.h_descs, sv->max_batch * sizeof(xk::StripeDesc)) != cudaSuccess ||
+        !grow_blocks(sl, static_cast<size_t>(sv->max_batch) * 16)) {
+      cudaGetLastError();
+      for (Slot& s2 : sv->slots) free_slot(s2);
+      delete sv;
+      return fail(EC_ENOMEM, "allocation of the serving slots failed");
+    }
+  }
+  sv->th = std::thread(scheduler, sv);
+  *out = sv;
+  return EC_OK;
+}
+
+ec_status ec_server_warm(ec_server* sv, ec_plan* plan, int max_erasures) {
+  if (!sv || !plan) return fail(EC_EINVAL, "NULL argument");
+  const int n = plan->k + plan->m;
+  max_erasures = std::min(max_erasures, plan->m);
+  std::vector<std::vector<int>> sets;
+  for (int e = 1; e <= max_erasures; ++e) {
+    std::vector<int> idx(e);
+    for (int i = 0; i < e; ++i) idx[i] = i;
+    for (;;) {
+      sets.push_back(idx);
+      int i = e - 1;
+      while (i >= 0 && idx[i] == n - e + i) --i;
+      if (i < 0) break;
+      ++idx[i];
+      for (int j = i + 1; j < e; ++j) idx[j] = idx[j - 1] + 1;
+    }
+  }
+  std::vector<int> flat, counts;
+  for (auto& s : sets) {
+    flat.insert(flat.end(), s.begin(), s.end());
+    counts.push_back(static_cast<int>(s.size()));
+  }
+  ec_status st = ec_decode_prepare(plan, flat.data(), counts.data(), static_cast<int>(sets.size()), 0);
+  if (st != EC_OK) return st;
+  std::vector<std::pair<ec_plan*, Program*>> want;
+  want.emplace_back(plan, plan->enc.get());
+  for (auto& s : sets) {
+    Program* p = nullptr;
+    st = get_decode_program(plan, s, &p);
+    if (st != EC_OK) return st;
+    want.emplace_back(plan, p);
+  }
+  if (!xorec::jit_available()) return EC_OK;   // interpreter serves everything
+  return xorec::compile_modules(want, sv->threads, sv->minb, false, nullptr);
+}
+
+ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
+  if (!sv || !job) return fail(EC_EINVAL, "NULL argument");
+  Req r;
+  std::vector<int> er;
+  ec_status s = xorec::resolve_job(*job, &r.prog, &er, &r.ptrs);
+  if (s != EC_OK) return s;
+  {
+    bool compiled_here = r.prog->mod && xorec::jit_module_threads(r.prog->mod) == sv->threads;
+    if (!compiled_here) {
+      std::lock_guard<std::mutex> lk(job->plan->mu);
+      if (!xorec::ensure_device_code(r.prog)) return EC_ECUDA;
+    }
+  }
+  const size_t B = job->block_bytes;
+  r.S = static_cast<long long>(B / 8);
+  r.tiles = (r.S + 4 * sv->threads - 1) / (4 * sv->threads);
+  r.bytes_in = static_cast<long long>(r.prog->n_in / 8) * static_cast<long long>(B);
+  r.bytes_out = static_cast<long long>(r.prog->n_out / 8) * static_cast<long long>(B);
+  r.bytes = static_cast<size_t>(r.bytes_in + r.bytes_out);
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->stop) return fail(EC_EINVAL, "server is shutting down");
+  if (sv->admitted + r.bytes > sv->budget) {
+    sv->stats.rejected += 1;
+    return EC_EBUSY;
+  }
+  r.ticket = sv->next_ticket++;
+  r.t0 = Clock::now();
+  if (ticket) *ticket = r.ticket;
+  sv->admitted += r.bytes;
+  sv->stats.submitted += 1;
+  sv->pending.push_back(std::move(r));
+  sv->cv.notify_one();
+  return EC_OK;
+}
+
+ec_status ec_server_poll(ec_server* sv, uint64_t* tickets, double* latency_us, int max,
+                         int* n_done) {
+  if (!sv || !n_done || max < 0) return fail(EC_EINVAL, "bad argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const int n = std::min<int>(max, static_cast<int>(sv->done.size()));
+  for (int i = 0; i < n; ++i) {
+    if (tickets) tickets[i] = sv->done[i].first;
+    if (latency_us) latency_us[i] = sv->done[i].second;
+  }
+  sv->done.erase(sv->done.begin(), sv->done.begin() + n);
+  *n_done = n;
+  return sv->error == EC_OK ? EC_OK : fail(static_cast<ec_status>(sv->error), "a batch failed on the GPU");
+}
+
+ec_status ec_server_stats_get(ec_server* sv, ec_server_stats* out) {
+  if (!sv || !out) return fail(EC_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *out = sv->stats;
+  out->admitted_bytes = static_cast<long long>(sv->admitted);
+  out->pending = static_cast<long long>(sv->pending.size());
+  return EC_OK;
+}
+
+void ec_server_destroy(ec_server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    sv->cv.notify_one();
+  }
+  if (sv->th.joinable()) sv->th.join();
+  for (Slot& s : sv->slots) free_slot(s);
+  delete sv;
+}
+
+}  // extern "C"
