@@ -71,6 +71,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """Largest value over all ranks (time of the slowest rank); identity
+    without a process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbps(per_rank_bytes_per_step: int, world: int, steps: int, ms_total: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank processes its own stripes)."""
+    return world * per_rank_bytes_per_step * steps / (ms_total / 1e3) / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -254,10 +271,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms_total = t_start.elapsed_time(t_end)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, "cuda")
 
     # sampled bit-exact check of the timed output against the oracle
     parity_status = "not-checked"
@@ -278,7 +292,7 @@ def run_ours(args):
     info = xo.ec_plan_info(plan)
     in_bytes = n * k * B
     moved = (k + m) * B * n
-    value = ws * in_bytes * K / (ms_total / 1e3) / 1e9
+    value = whole_job_gbps(in_bytes, ws, K, ms_total)
     peak, peak_kind = measured_peaks()
     mean_launch_ms = statistics.mean(launch_ms)
     achieved = moved / (mean_launch_ms / 1e3) / 1e9

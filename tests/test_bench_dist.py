@@ -1,0 +1,51 @@
+"""The multi-rank timing logic of bench.py (max over ranks, whole-job
+throughput) with world_size 2 on the gloo backend, CPU only."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 100.0 + 50.0 * rank                 # rank 1 is the slow one
+    worst = bench.max_over_ranks(ms, dist, "cpu")
+    q.put((rank, worst, bench.whole_job_gbps(10 << 20, world, 4, worst)))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_value():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, worst, gbps in res:
+        assert worst == 150.0
+        assert abs(gbps - 2 * (10 << 20) * 4 / 0.150 / 1e9) < 1e-9
+
+
+def test_single_process_identity():
+    assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
