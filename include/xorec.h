@@ -177,6 +177,20 @@ ec_status ec_encode_strided(ec_plan *plan, const uint8_t *data, size_t data_stri
                             size_t par_stripe_stride, size_t par_block_stride,
                             int n_stripes, size_t block_bytes, void *stream);
 
+/* Encode n_stripes stripes that live in HOST memory (same strided layout as
+ * ec_encode_strided, host addresses).  Chunks of chunk_stripes stripes (0 =
+ * 16) are copied to device staging owned by the plan, encoded and their
+ * parity copied back, on three internal streams so that both copy
+ * directions and the kernels overlap.  Pinned host memory gives full link
+ * speed; pageable memory works but copies synchronously.  Asynchronous with
+ * respect to the host: the work is ordered after `stream`'s prior work and
+ * `stream` waits for all of it; keep the buffers alive until then. */
+ec_status ec_encode_host_strided(ec_plan *plan, const uint8_t *data, size_t data_stripe_stride,
+                                 size_t data_block_stride, uint8_t *parity,
+                                 size_t par_stripe_stride, size_t par_block_stride,
+                                 int n_stripes, size_t block_bytes, int chunk_stripes,
+                                 void *stream);
+
 /* Decode one stripe (Sec. 1): recover the blocks listed in erasures (ids in
  * [0, k+m), unique, any order, 1 <= n_erasures <= m) from the first k
  * surviving blocks in ascending id order.  blocks[k+m] is indexed by block

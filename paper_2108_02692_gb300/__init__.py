@@ -164,6 +164,16 @@ def ec_encode_strided(plan: int, data_ptr: int, data_stripe_stride: int, data_bl
                                    block_bytes, stream or None))
 
 
+def ec_encode_host_strided(plan: int, data_ptr: int, data_stripe_stride: int,
+                           data_block_stride: int, parity_ptr: int, par_stripe_stride: int,
+                           par_block_stride: int, n_stripes: int, block_bytes: int,
+                           chunk_stripes: int = 0, stream: int = 0) -> None:
+    """Encode stripes held in host memory (pinned for full speed)."""
+    _check(lib().ec_encode_host_strided(plan, data_ptr, data_stripe_stride, data_block_stride,
+                                        parity_ptr, par_stripe_stride, par_block_stride,
+                                        n_stripes, block_bytes, chunk_stripes, stream or None))
+
+
 def ec_decode(plan: int, erasures, block_ptrs, out_ptrs, block_bytes: int,
               stream: int = 0) -> None:
     _check(lib().ec_decode(plan, _int_array(erasures), len(erasures), _vp_array(block_ptrs),

@@ -90,6 +90,8 @@ SIGNATURES = {
     "ec_encode_noalloc": (c_int, [c_vp, vpp, vpp, c_size, c_vp]),
     "ec_encode_strided": (c_int, [c_vp, c_vp, c_size, c_size, c_vp, c_size, c_size, c_int,
                                   c_size, c_vp]),
+    "ec_encode_host_strided": (c_int, [c_vp, c_vp, c_size, c_size, c_vp, c_size, c_size, c_int,
+                                       c_size, c_int, c_vp]),
     "ec_decode": (c_int, [c_vp, intp, c_int, vpp, vpp, c_size, c_vp]),
     "ec_decode_prepare": (c_int, [c_vp, intp, intp, c_int, c_int]),
     "ec_plan_compile": (c_int, [c_vp, intp, intp, c_int, c_int]),

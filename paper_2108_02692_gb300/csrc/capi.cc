@@ -336,6 +336,7 @@ ec_status ec_plan_create(int k, int m, const uint8_t* matrix, ec_plan** out) {
 
 void ec_plan_destroy(ec_plan* plan) {
   if (!plan) return;
+  xorec::host_io_release(plan->hostio);
   for (void* mod : plan->modules) xorec::jit_module_release(mod);
   release_program(plan->enc.get());
   xorec::jit_release(plan->enc.get());

@@ -14,6 +14,8 @@
 #include "plan.h"
 #include "tile_pipeline.cuh"
 
+struct xorec_host_io;   // host-memory encode lanes (hostio.cc)
+
 struct ec_plan {
   int k = 0, m = 0;
   int matrix_kind = 0;
@@ -24,6 +26,7 @@ struct ec_plan {
   std::mutex mu;                             // guards dec and modules
   std::map<std::vector<int>, std::unique_ptr<xorec::Program>> dec;  // key: sorted erasures
   std::vector<void*> modules;                // compiled multi-program modules (batches)
+  xorec_host_io* hostio = nullptr;           // lanes and staging of ec_encode_host_strided
 };
 
 // Shared by the C ABI translation units.
@@ -87,6 +90,8 @@ bool jit_module_launch(void* mod, const xk::BatchParams& bp, int grid, size_t sm
 void jit_module_release(void* mod);
 int jit_module_regs(void* mod);
 int jit_module_threads(void* mod);
+
+void host_io_release(xorec_host_io* h);
 
 // Batch helpers (batch.cc), shared with the serving loop.
 ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,

@@ -339,3 +339,35 @@ def test_full_size_decode_rs10_4_sampled():
         p.close()
         del surv, outs
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_encode_from_host_memory(pinned):
+    k, m, B, n = 10, 4, 8 * 1040, 9
+    p = Plan(k, m)
+    try:
+        data = np.stack([np.stack([synth.block_bytes(27, s, j, B) for j in range(k)])
+                         for s in range(n)])
+        h_data = torch.from_numpy(data)
+        h_par = torch.zeros((n, m, B), dtype=torch.uint8)
+        if pinned:
+            h_data = h_data.pin_memory()
+            h_par = h_par.pin_memory()
+        xo.ec_encode_host_strided(p.h, h_data.data_ptr(), k * B, B, h_par.data_ptr(), m * B, B,
+                                  n, B, 4, stream())
+        torch.cuda.synchronize()
+        P = oracle.cauchy(k, m)
+        for s in range(n):
+            ref = oracle.encode(P, list(data[s]))
+            for i in range(m):
+                assert np.array_equal(h_par[s, i].numpy(), ref[i]), (s, i)
+        # non-dense host layout: parity blocks interleaved with a gap
+        h_par2 = torch.zeros((n, m, B + 128), dtype=torch.uint8)
+        xo.ec_encode_host_strided(p.h, h_data.data_ptr(), k * B, B, h_par2.data_ptr(),
+                                  m * (B + 128), B + 128, n, B, 3, stream())
+        torch.cuda.synchronize()
+        for s in range(n):
+            for i in range(m):
+                assert np.array_equal(h_par2[s, i, :B].numpy(), h_par[s, i].numpy())
+    finally:
+        p.close()
