@@ -183,9 +183,12 @@ int batch_minb_default() { return batch_minb(); }
 ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, int threads,
                           int minb, bool must, int* built) {
   const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 32));
+  DeviceInfo di;
+  if (!device_info(&di)) return EC_ECUDA;
   std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
   std::vector<Program*> seen;
   for (const auto& w : want) {
+    if (!compiled_tier_fits(w.second, threads, di.smem_optin)) continue;   // interpreter
     std::lock_guard<std::mutex> lk(w.first->mu);
     if ((w.second->mod && jit_module_threads(w.second->mod) == threads) ||
         std::find(seen.begin(), seen.end(), w.second) != seen.end())

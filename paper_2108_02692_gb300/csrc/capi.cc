@@ -84,6 +84,16 @@ static int env_int(const char* name, int dflt) {
 
 static std::mutex g_jit_mu;
 
+// The compiled tier runs a program only when one tile of all its input
+// strips fits a CTA's shared memory and the straight-line code stays small
+// enough to compile quickly; everything else goes to the interpreter.
+constexpr long kMaxCompiledMemOps = 65536;
+
+bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin) {
+  const size_t smem = 128 + static_cast<size_t>(p->n_in) * 4 * threads + xk::kBatchHeader;
+  return smem <= smem_optin && p->stats.fused.mem <= kMaxCompiledMemOps;
+}
+
 // Compile p's straight-line kernel once.  The compile itself runs without
 // the lock so that several programs can compile at the same time.
 bool jit_ensure(Program* p, int threads, std::string* err) {
@@ -119,8 +129,8 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   if (executor != EC_EXEC_INTERP) {
     threads = env_int("EC_JIT_THREADS", 128);
     nstage = env_int("EC_JIT_NSTAGE", 1);
-    std::string err;
-    compiled = jit_ensure(p, threads, &err);
+    std::string err = "program too large for the compiled tier";
+    compiled = compiled_tier_fits(p, threads, di.smem_optin) && jit_ensure(p, threads, &err);
     if (!compiled && executor == EC_EXEC_COMPILED) {
       set_error("compiled tier unavailable: " + err);
       return false;
@@ -538,6 +548,13 @@ ec_status ec_plan_compile(ec_plan* plan, const int* sets, const int* counts, int
   }
   xorec::DeviceInfo di;
   if (!xorec::device_info(&di)) return EC_ECUDA;
+  {
+    const char* v = std::getenv("EC_JIT_THREADS");
+    const int th = v && *v ? std::atoi(v) : 128;
+    progs.erase(std::remove_if(progs.begin(), progs.end(),
+                               [&](Program* p) { return !xorec::compiled_tier_fits(p, th, di.smem_optin); }),
+                progs.end());
+  }
   if (n_threads <= 0) n_threads = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
   const int threads = [] {
     const char* v = std::getenv("EC_JIT_THREADS");

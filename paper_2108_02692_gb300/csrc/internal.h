@@ -75,6 +75,7 @@ bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_
 // Compiled tier (jit.cc).
 bool jit_available();
 bool jit_ensure(Program* p, int threads, std::string* err);
+bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin);
 bool jit_compile(Program* p, int threads, std::string* err);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, int threads, int grid, size_t smem,
                 cudaStream_t stream);

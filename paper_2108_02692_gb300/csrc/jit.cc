@@ -60,13 +60,36 @@ void emit_statements(std::ostringstream& os, const xorec::Program& p) {
   }
 }
 
-// Single-program body.  load(): each thread copies its 4-byte column of
-// every input strip from the stage into registers.  compute(): the
-// statements, from registers.
+// Programs with more input strips than this read their operands from the
+// shared-memory stage at each use instead of preloading every input word
+// into registers (which would not fit the register file).
+constexpr int kPreloadMaxInputs = 96;
+
+// Single-program body.  Narrow programs (n_in <= kPreloadMaxInputs):
+// load() copies each thread's 4-byte column of every input strip from the
+// stage into registers and compute() runs the statements from registers.
+// Wide programs run from the stage (kEarlyRelease = false).
 std::string gen_body(const xorec::Program& p, int threads) {
   const int nc = p.fused.n_const;
   const int T = 4 * threads;
   std::ostringstream os;
+  if (nc > kPreloadMaxInputs) {
+    os << "struct SlpBody {\n"
+          "  static constexpr bool kEarlyRelease = false;\n"
+          "  __device__ __forceinline__ void operator()(const xk::LaunchParams& p, xk::i64 s,\n"
+          "      xk::i64 c0, int len, const xk::u8* stg, xk::u8*) const {\n"
+          "    const int col = threadIdx.x * 4;\n"
+          "    if (col >= len) return;\n"
+          "    const xk::u8* in = stg + col;\n"
+          "    const xk::i64 S = p.io.S;\n";
+    for (int b = 0; b < p.n_out / 8; ++b)
+      os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
+    os << "#define I(c) (*reinterpret_cast<const xk::u32*>(in + (c) * " << T << "))\n";
+    os << "#define O(b, t, v) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
+    emit_statements(os, p);
+    os << "#undef I\n#undef O\n  }\n};\n";
+    return os.str();
+  }
   os << "struct SlpBody {\n"
         "  static constexpr bool kEarlyRelease = true;\n"
         "  struct Regs { xk::u32 x[" << (nc > 0 ? nc : 1) << "]; };\n"
@@ -111,6 +134,42 @@ std::string gen_module_source(const std::vector<const xorec::Program*>& progs, i
     os << "#define O(b, t, v) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
     emit_statements(os, *progs[i]);
     os << "#undef I\n#undef O\n}\n";
+  }
+  if (nc > kPreloadMaxInputs) {
+    // wide programs: operands from the stage at each use
+    std::ostringstream ws;
+    ws << kPipelineSrc << "\n";
+    for (size_t i = 0; i < progs.size(); ++i) {
+      ws << "__device__ __forceinline__ void prog_" << i
+         << "(const xk::StripeDesc& d, xk::i64 c0, int col, const xk::u8* in) {\n"
+            "    const xk::i64 S = d.S;\n";
+      for (int b = 0; b < progs[i]->n_out / 8; ++b)
+        ws << "    xk::u8* ob" << b << " = reinterpret_cast<xk::u8*>(d.blocks[d.n_inblk + " << b
+           << "]) + c0 + col;\n";
+      ws << "#define I(c) (*reinterpret_cast<const xk::u32*>(in + (c) * " << T << "))\n";
+      ws << "#define O(b, t, v) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
+      emit_statements(ws, *progs[i]);
+      ws << "#undef I\n#undef O\n}\n";
+    }
+    ws << "struct ModBody {\n"
+          "  static constexpr bool kEarlyRelease = false;\n"
+          "  __device__ __forceinline__ void operator()(const xk::StripeDesc& d, xk::i64 c0, int len,\n"
+          "      const xk::u8* stg, xk::u8*, int) const {\n"
+          "    const int col = threadIdx.x * 4;\n"
+          "    if (col >= len) return;\n"
+          "    switch (d.prog) {\n";
+    for (size_t i = 0; i < progs.size(); ++i)
+      ws << "      case " << i << ": prog_" << i << "(d, c0, col, stg + col); break;\n";
+    ws << "      default: break;\n"
+          "    }\n"
+          "  }\n"
+          "};\n";
+    ws << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", " << minb
+       << ") xorec_mod(xk::BatchParams p) {\n"
+          "  extern __shared__ __align__(128) xk::u8 smem[];\n"
+          "  xk::run_batch_pipeline(p, smem, ModBody(), nullptr);\n"
+          "}\n";
+    return ws.str();
   }
   os << "struct ModBody {\n"
         "  static constexpr bool kEarlyRelease = true;\n"

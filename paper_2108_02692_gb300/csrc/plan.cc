@@ -100,6 +100,10 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   if (o.opt_level == kOptRaw) {
     fused = slp_rows_fused(n_in, R, order);
     p.stats.compressed = p.stats.raw;
+  } else if (o.max_temps == -2 && n_in >= o.reg_budget) {
+    // the inputs alone exceed the register budget: no temporaries
+    fused = slp_rows_fused(n_in, R, order);
+    p.stats.compressed = p.stats.raw;
   } else {
     RepairTrace tr(chains, o.opt_level == kOptXorRePair);
     int b = tr.n_temps();

@@ -126,3 +126,39 @@ def test_batch_argument_errors(plans):
         xo.ec_batch_create([{"plan": plans[(4, 2)], "op": xo.EC_OP_DECODE, "erasures": [0, 1, 2],
                              "blocks": [p] * 6, "out": [p] * 3, "block_bytes": 1024}])
     assert e.value.status == xo.EC_ETOOMANY
+
+
+def test_batch_with_wide_codes():
+    torch.cuda.set_device(0)
+    codes = [(40, 8), (10, 4), (20, 4)]
+    plans = {c: xo.ec_plan_create(*c) for c in codes}
+    try:
+        rng = np.random.default_rng(12)
+        jobs, keep, expect = [], [], []
+        for s in range(9):
+            k, m = codes[s % 3]
+            B = int(rng.choice([1024, 4096, 8 * 1040]))
+            P = oracle.cauchy(k, m)
+            data = [synth.block_bytes(33, s, j, B) for j in range(k)]
+            blocks = data + oracle.encode(P, data)
+            d = [torch.from_numpy(x).cuda() for x in blocks]
+            keep += d
+            if s % 2 == 0:
+                o = [torch.full((B,), 0xEE, dtype=torch.uint8, device="cuda") for _ in range(m)]
+                jobs.append({"plan": plans[(k, m)], "op": xo.EC_OP_ENCODE,
+                             "blocks": [t.data_ptr() for t in d[:k]],
+                             "out": [t.data_ptr() for t in o], "block_bytes": B})
+                expect.append((o, blocks[k:]))
+            else:
+                er = [0, k + 1]
+                o = [torch.full((B,), 0xEE, dtype=torch.uint8, device="cuda") for _ in er]
+                jobs.append({"plan": plans[(k, m)], "op": xo.EC_OP_DECODE, "erasures": er,
+                             "blocks": [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                             "out": [t.data_ptr() for t in o], "block_bytes": B})
+                expect.append((o, [blocks[e] for e in er]))
+            keep += o
+        xo.ec_run_batch(jobs, torch.cuda.current_stream().cuda_stream)
+        check(expect)
+    finally:
+        for h in plans.values():
+            xo.ec_plan_destroy(h)

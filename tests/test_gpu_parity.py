@@ -312,6 +312,7 @@ def test_full_size_decode_rs10_4_sampled():
     try:
         pats = synth.decode_patterns(k, m, n)
         xo.ec_decode_prepare(p.h, sorted(set(pats)))
+        xo.ec_plan_compile(p.h, sorted(set(pats)))     # compile in parallel up front
         surv = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
         _fill_stripes(surv, 3, n, k, B)
         outs = torch.zeros((n, m, B), dtype=torch.uint8, device="cuda")
@@ -369,5 +370,38 @@ def test_encode_from_host_memory(pinned):
         for s in range(n):
             for i in range(m):
                 assert np.array_equal(h_par2[s, i, :B].numpy(), h_par[s, i].numpy())
+    finally:
+        p.close()
+
+
+WIDE = [(20, 4, 8 * 1040), (40, 8, 4096), (100, 4, 2048), (1, 255, 1024), (128, 128, 256)]
+
+
+@pytest.mark.parametrize("k,m,B", WIDE)
+def test_wide_and_extreme_codes_encode(k, m, B):
+    """Wide codes (more input strips than registers) run from the shared-
+    memory stage or, when the tile does not fit, in the interpreter;
+    k + m = 256 is the largest code."""
+    p = Plan(k, m)
+    try:
+        data = [synth.block_bytes(28, k, j, B) for j in range(k)]
+        ref = oracle.encode(oracle.cauchy(k, m), data)
+        d = [dev(x) for x in data]
+        par = [torch.full((B,), 0x3C, dtype=torch.uint8, device="cuda") for _ in range(m)]
+        xo.ec_encode(p.h, [t.data_ptr() for t in d], [t.data_ptr() for t in par], B, stream())
+        torch.cuda.synchronize()
+        for i in range(m):
+            assert np.array_equal(host(par[i]), ref[i]), i
+    finally:
+        p.close()
+
+
+def test_wide_code_decode():
+    k, m, B = 20, 4, 8 * 528
+    p = Plan(k, m)
+    try:
+        blocks = _codeword(k, m, B, 29, 0)
+        for er in [(0, 5, 21, 23), (19,), (20, 21, 22, 23), (3, 22)]:
+            _decode_check(p, blocks, er, B)
     finally:
         p.close()
