@@ -61,6 +61,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-decode", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     return ap.parse_args()
 
 
@@ -240,6 +241,9 @@ def run_ours(args):
         for j in range(k):
             xo.ec_synth_fill(data[s, j].data_ptr(), B, synth.block_seed(CONFIG_ID, s, j), 0, sp)
     stream.synchronize()
+    tune = None
+    if not args.no_tune and executor != xo.EC_EXEC_INTERP and args.max_temps == -2 and args.opt == "xorrepair":
+        tune = xo.ec_plan_autotune(plan, B, 32, sp)
 
     def step(st):
         xo.ec_encode_strided(plan, data.data_ptr(), k * B, B, par.data_ptr(), m * B, B, n, B, st)
@@ -324,7 +328,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD if n == N_STRIPES else WORKLOAD.replace("256", str(n)),
                    "k": k, "m": m, "n_stripes": n, "block_bytes": B,
                    "matrix": "cauchy", "executor": kind, "opt": args.opt,
-                   "max_temps": args.max_temps,
+                   "max_temps": args.max_temps, "autotune": tune,
                    "l2": "inputs (2.5 GiB) larger than L2 (129 MB); no flush",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

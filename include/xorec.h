@@ -215,6 +215,26 @@ ec_status ec_decode_prepare(ec_plan *plan, const int *sets, const int *counts, i
 ec_status ec_plan_compile(ec_plan *plan, const int *sets, const int *counts, int n_sets,
                           int n_threads);
 
+/* Autotuner: times the encoder under candidate launch shapes (threads per
+ * CTA, i.e. tile bytes per strip) and register budgets (which bound the
+ * XorRePair temporaries) on n_stripes scratch stripes of block_bytes,
+ * checks that every candidate writes identical parity, and installs the
+ * fastest program in the plan; decoders built afterwards use the same
+ * budget and shape.  Allocates scratch device memory for the duration of
+ * the call and synchronises `stream`.  Must not run concurrently with other
+ * calls on the same plan. */
+typedef struct {
+  int threads;           /* threads per CTA of the compiled tier            */
+  int reg_budget;        /* register budget of the temporaries              */
+  int min_ctas_per_sm;   /* occupancy the kernel was compiled for           */
+  int candidates;        /* candidates timed                                */
+  double ms;             /* best time per launch                            */
+  double gbps_in;        /* best input throughput, GB/s                     */
+} ec_tune_result;
+
+ec_status ec_plan_autotune(ec_plan *plan, size_t block_bytes, int n_stripes, void *stream,
+                           ec_tune_result *out);
+
 /* Select the executor tier (EC_EXEC_*).  EC_EXEC_COMPILED fails with
  * EC_ENOTSUP when no run-time compiler is present. */
 ec_status ec_plan_set_executor(ec_plan *plan, int executor);
@@ -307,6 +327,13 @@ void ec_server_destroy(ec_server *server);
  * *status = 0 (ok) or EC_ETIMEOUT.  reset != 0 clears it.  Synchronises the
  * current device. */
 ec_status ec_device_status(int *status, int reset);
+
+/* Diagnostics: launch a one-thread kernel that waits, with the same bounded
+ * wait the pipelines use (about 2 s), on a barrier nothing completes.  The
+ * wait gives up, the kernel records EC_ETIMEOUT in the status word read by
+ * ec_device_status and returns; the context stays usable.  The paper has
+ * no counterpart; this checks the failure path without faulting the GPU. */
+ec_status ec_selftest_wait_timeout(void *stream);
 
 /* Thread-local message of the last failure ("" if none). */
 const char *ec_last_error(void);

@@ -138,6 +138,12 @@ def ec_plan_program(plan: int, erasures=None) -> np.ndarray:
     return out
 
 
+def ec_plan_autotune(plan: int, block_bytes: int, n_stripes: int = 16, stream: int = 0) -> dict:
+    r = _abi.TuneResult()
+    _check(lib().ec_plan_autotune(plan, block_bytes, n_stripes, stream or None, ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in _abi.TuneResult._fields_}
+
+
 def ec_plan_set_executor(plan: int, executor: int) -> None:
     _check(lib().ec_plan_set_executor(plan, executor))
 
@@ -298,6 +304,10 @@ def ec_device_status(reset: bool = False) -> int:
     st = ctypes.c_int()
     _check(lib().ec_device_status(ctypes.byref(st), 1 if reset else 0))
     return st.value
+
+
+def ec_selftest_wait_timeout(stream: int = 0) -> None:
+    _check(lib().ec_selftest_wait_timeout(stream or None))
 
 
 def ec_synth_fill(ptr: int, n: int, seed: int, offset: int = 0, stream: int = 0) -> None:

@@ -76,6 +76,11 @@ class ServerStats(ctypes.Structure):
                  "bytes_in", "bytes_out", "admitted_bytes", "pending")] + [("slots_busy", c_int)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("threads", c_int), ("reg_budget", c_int), ("min_ctas_per_sm", c_int),
+                ("candidates", c_int), ("ms", ctypes.c_double), ("gbps_in", ctypes.c_double)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/xorec.h
 SIGNATURES = {
     "ec_plan_create": (c_int, [c_int, c_int, u8p, ctypes.POINTER(c_vp)]),
@@ -95,6 +100,7 @@ SIGNATURES = {
     "ec_decode": (c_int, [c_vp, intp, c_int, vpp, vpp, c_size, c_vp]),
     "ec_decode_prepare": (c_int, [c_vp, intp, intp, c_int, c_int]),
     "ec_plan_compile": (c_int, [c_vp, intp, intp, c_int, c_int]),
+    "ec_plan_autotune": (c_int, [c_vp, c_size, c_int, c_vp, ctypes.POINTER(TuneResult)]),
     "ec_plan_set_executor": (c_int, [c_vp, c_int]),
     "ec_batch_create": (c_int, [ctypes.POINTER(Job), c_int, c_int, ctypes.POINTER(c_vp)]),
     "ec_batch_run": (c_int, [c_vp, c_vp]),
@@ -111,6 +117,7 @@ SIGNATURES = {
     "ec_device_status": (c_int, [intp, c_int]),
     "ec_last_error": (c_char_p, []),
     "ec_version": (c_char_p, []),
+    "ec_selftest_wait_timeout": (c_int, [c_vp]),
     "ec_synth_fill": (c_int, [c_vp, c_size, c_u64, c_u64, c_vp]),
     "ec_slp_parse": (c_int, [c_char_p, ctypes.POINTER(c_vp)]),
     "ec_slp_from_matrix": (c_int, [c_int, c_int, u8p, c_int, ctypes.POINTER(c_vp)]),

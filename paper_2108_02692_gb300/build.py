@@ -23,7 +23,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-HOST_SRCS = ["gf.cc", "slp.cc", "plan.cc", "capi.cc", "jit.cc", "batch.cc", "server.cc", "hostio.cc"]
+HOST_SRCS = ["gf.cc", "slp.cc", "plan.cc", "capi.cc", "jit.cc", "batch.cc", "server.cc", "hostio.cc", "tune.cc"]
 CUDA_SRCS = ["executor.cu", "noalloc.cu"]
 HEADERS = ["gf.h", "slp.h", "plan.h", "internal.h", "tile_pipeline.cuh"]
 

@@ -110,6 +110,7 @@ bool jit_ensure(Program* p, int threads, std::string* err) {
   tmp.sched = p->sched;
   tmp.n_in = p->n_in;
   tmp.n_out = p->n_out;
+  tmp.minb = p->minb;
   if (!jit_compile(&tmp, threads, err)) return false;
   std::lock_guard<std::mutex> lk(g_jit_mu);
   if (p->jit) {
@@ -127,7 +128,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   bool compiled = false;
   int threads = 0, nstage = 0;
   if (executor != EC_EXEC_INTERP) {
-    threads = env_int("EC_JIT_THREADS", 128);
+    threads = p->threads > 0 ? p->threads : env_int("EC_JIT_THREADS", 128);
     nstage = env_int("EC_JIT_NSTAGE", 1);
     std::string err = "program too large for the compiled tier";
     compiled = compiled_tier_fits(p, threads, di.smem_optin) && jit_ensure(p, threads, &err);
@@ -259,6 +260,8 @@ ec_status get_decode_program(ec_plan* plan, const std::vector<int>& er, Program*
   std::string err;
   if (!xorec::build_program(static_cast<int>(er.size()), k, R.data(), plan->opts, prog.get(), &err))
     return fail(EC_EINVAL, err);
+  prog->threads = plan->tuned_threads;
+  prog->minb = plan->tuned_minb;
   std::lock_guard<std::mutex> lk(plan->mu);
   auto it = plan->dec.find(er);
   if (it == plan->dec.end()) it = plan->dec.emplace(er, std::move(prog)).first;
@@ -353,6 +356,10 @@ void ec_plan_destroy(ec_plan* plan) {
   for (auto& kv : plan->dec) {
     release_program(kv.second.get());
     xorec::jit_release(kv.second.get());
+  }
+  for (auto& p : plan->retired) {
+    release_program(p.get());
+    xorec::jit_release(p.get());
   }
   delete plan;
 }
@@ -598,6 +605,10 @@ ec_status ec_device_status(int* status, int reset) {
   if (reset && cudaMemset(di.status, 0, sizeof(int)) != cudaSuccess)
     return fail(EC_ECUDA, "resetting the status word failed");
   return EC_OK;
+}
+
+ec_status ec_selftest_wait_timeout(void* stream) {
+  return xorec::launch_selftest_wait(static_cast<cudaStream_t>(stream)) ? EC_OK : EC_ECUDA;
 }
 
 ec_status ec_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset, void* stream) {

@@ -100,6 +100,18 @@ __global__ void __launch_bounds__(256) interp_batch_kernel(BatchParams p) {
   run_batch_pipeline(p, smem, InterpBatchBody(), slots);
 }
 
+// Self-test of the bounded waits: one thread waits, with the pipeline's
+// mbar_wait, on an mbarrier whose phase nothing completes; the wait gives
+// up after its limit, the kernel records the timeout like the pipelines do
+// and returns.
+__global__ void selftest_wait_kernel(int* status) {
+  __shared__ __align__(8) u64 bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(smem_addr(&bar), 1);
+  fence_mbar_init();
+  if (!mbar_wait(smem_addr(&bar), 0)) atomicExch(status, XK_STATUS_TIMEOUT);
+}
+
 // SplitMix64 (Steele, Lea, Flood 2014) in counter form: byte n of stream
 // `seed` is byte n % 8 (little-endian) of mix(seed + (n/8 + 1) * gamma).
 __device__ __forceinline__ u64 mix64(u64 z) {
@@ -192,6 +204,18 @@ bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("batched interpreter launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+bool launch_selftest_wait(cudaStream_t stream) {
+  DeviceInfo di;
+  if (!device_info(&di)) return false;
+  selftest_wait_kernel<<<1, 32, 0, stream>>>(di.status);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("self-test launch failed: ") + cudaGetErrorString(e));
     return false;
   }
   return true;

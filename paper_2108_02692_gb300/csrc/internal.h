@@ -27,6 +27,8 @@ struct ec_plan {
   std::map<std::vector<int>, std::unique_ptr<xorec::Program>> dec;  // key: sorted erasures
   std::vector<void*> modules;                // compiled multi-program modules (batches)
   xorec_host_io* hostio = nullptr;           // lanes and staging of ec_encode_host_strided
+  int tuned_threads = 0, tuned_minb = 0;     // compiled-tier launch shape from the autotuner
+  std::vector<std::unique_ptr<xorec::Program>> retired;  // encoders replaced by the autotuner
 };
 
 // Shared by the C ABI translation units.
@@ -103,6 +105,9 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
                           int minb, bool must, int* built);
 bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
                         size_t* smem, int* per_sm);
+
+// Bounded-wait self-test (executor.cu).
+bool launch_selftest_wait(cudaStream_t stream);
 
 // Synthetic input generator (executor.cu).
 bool launch_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset,

@@ -9,6 +9,7 @@
 #include <nvrtc.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <sstream>
@@ -211,7 +212,8 @@ std::string gen_source(const xorec::Program& p, int threads) {
   os << kPipelineSrc << "\n";
   os << gen_body(p, threads);
   os << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
-     << env_or("EC_JIT_MINB", 4) << ") xorec_slp(xk::LaunchParams p) {\n"
+     << (p.minb > 0 ? p.minb : env_or("EC_JIT_MINB", std::max(1, 512 / threads)))
+     << ") xorec_slp(xk::LaunchParams p) {\n"
         "  extern __shared__ __align__(128) xk::u8 smem[];\n"
         "  xk::run_pipeline(p, smem, SlpBody());\n"
         "}\n";

@@ -50,6 +50,9 @@ struct Program {
   // multi-program module holding this program (batched launches)
   void* mod = nullptr;
   int mod_index = -1;
+  // launch shape of the compiled tier chosen by the autotuner (0 = default)
+  int threads = 0;
+  int minb = 0;
 };
 
 struct PlanOptions {
