@@ -61,6 +61,11 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-decode", action="store_true")
+    ap.add_argument("--decode-stripes", type=int, default=N_STRIPES,
+                    help="stripes of the decode measurement")
+    ap.add_argument("--decode-patterns", type=int, default=0,
+                    help="0: erasure sets uniform over all patterns; N > 0: the stripes cycle "
+                         "through N distinct sets of m erasures (profiling program diversity)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     return ap.parse_args()
 
@@ -306,7 +311,8 @@ def run_ours(args):
     if not args.no_e2e and n == N_STRIPES:
         e2e = run_e2e(args, xo, plan, data, par, stream, torch)
     decode = None
-    if not args.no_decode and n == N_STRIPES:
+    if not args.no_decode and (n == N_STRIPES or args.decode_patterns > 0
+                               or args.decode_stripes != N_STRIPES):
         del data, par
         torch.cuda.empty_cache()
         decode = run_decode(args, xo, torch, stream, peak)
@@ -366,10 +372,18 @@ def run_decode(args, xo, torch, stream, peak):
     import oracle
     from paper_2108_02692_gb300 import synth
 
-    k, m, B, n = K_DATA, M_PAR, BLOCK, N_STRIPES
+    k, m, B, n = K_DATA, M_PAR, BLOCK, args.decode_stripes
     S = B // 8
     sp = stream.cuda_stream
-    pats = synth.decode_patterns(k, m, n)
+    if args.decode_patterns > 0:
+        full = list(dict.fromkeys(p for p in synth.decode_patterns(k, m, 4096) if len(p) == m))
+        pats = [full[s % min(args.decode_patterns, len(full))] for s in range(n)]
+        what = (f"RS(10,4) decode, {n} stripes x 1 MiB, {m} erasures per stripe, cycling "
+                f"through {min(args.decode_patterns, len(full))} erasure sets")
+    else:
+        pats = synth.decode_patterns(k, m, n)
+        what = (f"RS(10,4) decode, {n} stripes x 1 MiB, erasure sets uniform over all "
+                "1470 patterns of 1-4 blocks")
     surv = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
     outs = torch.zeros((n, m, B), dtype=torch.uint8, device="cuda")
     for s in range(n):
@@ -414,7 +428,7 @@ def run_decode(args, xo, torch, stream, peak):
     P = oracle.cauchy(k, m)
     rng = np.random.default_rng(11)
     ok = True
-    for s in rng.choice(n, 6, replace=False):
+    for s in rng.choice(n, min(n, 6), replace=False):
         er = list(pats[int(s)])
         R = oracle.decode_matrix(P, er)
         w0 = int(rng.integers(0, (S - 32) // 16)) * 16
@@ -439,8 +453,7 @@ def run_decode(args, xo, torch, stream, peak):
     del surv, outs
     torch.cuda.empty_cache()
     return {
-        "workload": "RS(10,4) decode, 256 stripes x 1 MiB, erasure sets uniform over all "
-                    "1470 patterns of 1-4 blocks",
+        "workload": what,
         "value": round(in_bytes / (ms_batch / 1e3) / 1e9, 2), "unit": "GB/s",
         "ms_per_step": round(ms_batch, 4),
         "roofline": {"bound": "hbm", "achieved": round(moved / (ms_batch / 1e3) / 1e9, 1),
