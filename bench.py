@@ -47,7 +47,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="encode", choices=["encode", "batched", "served"])
+    ap.add_argument("--workload", default="encode", choices=["encode", "batched", "served", "codes"])
+    ap.add_argument("--matrix", default="cauchy", choices=["cauchy", "cauchy_min", "power"],
+                    help="coding matrix (default: Cauchy)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--batched-stripes", type=int, default=8192)
@@ -238,8 +240,8 @@ def run_ours(args):
     sp = stream.cuda_stream
     opt = {"raw": xo.EC_OPT_RAW, "repair": xo.EC_OPT_REPAIR,
            "xorrepair": xo.EC_OPT_XORREPAIR}[args.opt]
-    plan = xo.ec_plan_create_ex(k, m, executor=executor, opt_level=opt,
-                                max_temps=args.max_temps)
+    plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, args.matrix), executor=executor,
+                                opt_level=opt, max_temps=args.max_temps)
     data = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
     par = torch.empty((n, m, B), dtype=torch.uint8, device="cuda")
     for s in range(n):
@@ -287,7 +289,7 @@ def run_ours(args):
     if rank == 0:
         import numpy as np
         import oracle
-        P = oracle.cauchy(k, m)
+        P = oracle_matrix(oracle, args.matrix, k, m)
         ok = True
         rng = np.random.default_rng(7)
         for s in rng.choice(n, 4, replace=False):
@@ -333,7 +335,7 @@ def run_ours(args):
         "data": "synthetic (SplitMix64 bytes generated on the device)",
         "config": {"workload": WORKLOAD if n == N_STRIPES else WORKLOAD.replace("256", str(n)),
                    "k": k, "m": m, "n_stripes": n, "block_bytes": B,
-                   "matrix": "cauchy", "executor": kind, "opt": args.opt,
+                   "matrix": args.matrix, "executor": kind, "opt": args.opt,
                    "max_temps": args.max_temps, "autotune": tune,
                    "l2": "inputs (2.5 GiB) larger than L2 (129 MB); no flush",
                    "parallelism": f"replicas x{ws}"},
@@ -391,7 +393,7 @@ def run_decode(args, xo, torch, stream, peak):
             xo.ec_synth_fill(surv[s, j].data_ptr(), B, synth.block_seed(DECODE_CONFIG_ID, s, j),
                              0, sp)
     stream.synchronize()
-    plan = xo.ec_plan_create(k, m)
+    plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, args.matrix))
     jobs, calls = [], []
     for s, er in enumerate(pats):
         ids = [i for i in range(k + m) if i not in er][:k]
@@ -425,7 +427,7 @@ def run_decode(args, xo, torch, stream, peak):
             xo.ec_batch_run(batch, sp)
         ms_batch = timed(lambda: xo.ec_batch_run(batch, sp), max(3, args.steps))
     # sampled bit-exact check against the oracle's decode map
-    P = oracle.cauchy(k, m)
+    P = oracle_matrix(oracle, args.matrix, k, m)
     rng = np.random.default_rng(11)
     ok = True
     for s in rng.choice(n, min(n, 6), replace=False):
@@ -468,6 +470,117 @@ def run_decode(args, xo, torch, stream, peak):
         "prepare_s": round(prep_s, 2), "plain_compile_s": round(compile_s, 2),
         "parity": "bit-exact on sampled windows" if ok else "MISMATCH",
     }
+
+
+def matrix_kind(xo, name):
+    return {"cauchy": xo.EC_MATRIX_CAUCHY, "cauchy_min": xo.EC_MATRIX_CAUCHY_MIN,
+            "power": xo.EC_MATRIX_POWER}[name]
+
+
+def oracle_matrix(oracle, name, k, m):
+    return {"cauchy": oracle.cauchy, "cauchy_min": oracle.cauchy_min,
+            "power": oracle.power}[name](k, m)
+
+
+CODES = [(8, 2), (9, 2), (10, 2), (8, 3), (9, 3), (10, 3), (8, 4), (9, 4), (10, 4)]
+
+
+def run_codes(args):
+    """The codes of the paper's throughput comparison (Sec. 7.6): RS(d,p)
+    for d = 8..10 and p = 2..4, each with the Cauchy matrix and the scaled
+    Cauchy matrix.  Per code: encode of 256 stripes x d x 1 MiB in one
+    launch, and decode of the same stripes with data blocks 0..p-1 erased
+    (every parity block is a survivor) in one batched launch; XOR counts of
+    the programs; sampled bit-exact check against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2108_02692_gb300 as xo
+    from paper_2108_02692_gb300 import synth
+
+    torch.cuda.set_device(0)
+    B, n = BLOCK, args.stripes
+    S = B // 8
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    peak, _ = measured_peaks()
+    reps = max(3, args.steps)
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                fn()
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    rows, all_ok = [], True
+    for (k, m) in CODES:
+        data = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
+        par = torch.empty((n, m, B), dtype=torch.uint8, device="cuda")
+        rec = torch.empty((n, m, B), dtype=torch.uint8, device="cuda")
+        for s in range(n):
+            for j in range(k):
+                xo.ec_synth_fill(data[s, j].data_ptr(), B, synth.block_seed(6, s, j), 0, sp)
+        er = list(range(m))
+        for name in ("cauchy", "cauchy_min"):
+            plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, name))
+            ms_enc = timed(lambda: xo.ec_encode_strided(plan, data.data_ptr(), k * B, B, par.data_ptr(),
+                                                        m * B, B, n, B, sp))
+            jobs = []
+            for s in range(n):
+                blocks = [None] * m + [data[s, j].data_ptr() for j in range(m, k)] + \
+                         [par[s, i].data_ptr() for i in range(m)]
+                jobs.append({"plan": plan, "op": xo.EC_OP_DECODE, "erasures": er, "blocks": blocks,
+                             "out": [rec[s, i].data_ptr() for i in range(m)], "block_bytes": B})
+            batch = xo.ec_batch_create(jobs)
+            ms_dec = timed(lambda: xo.ec_batch_run(batch, sp))
+            xo.ec_batch_destroy(batch)
+            # sampled windows: parity against the oracle, recovered blocks
+            # against the original data
+            P = oracle_matrix(oracle, name, k, m)
+            rng = np.random.default_rng(17)
+            ok = True
+            for s in rng.choice(n, 3, replace=False):
+                w0 = int(rng.integers(0, (S - 64) // 16)) * 16
+                mini = [synth.strip_slice(6, int(s), j, B, w0, 64) for j in range(k)]
+                ref = oracle.encode(P, mini)
+                got = par[int(s)].view(m, 8, S)[:, :, w0:w0 + 64].cpu().numpy()
+                ok &= all(np.array_equal(got[i].reshape(-1), ref[i]) for i in range(m))
+                got = rec[int(s)].view(m, 8, S)[:, :, w0:w0 + 64].cpu().numpy()
+                ok &= all(np.array_equal(got[i].reshape(-1), mini[i]) for i in range(m))
+            all_ok &= ok
+            ie, idd = xo.ec_plan_info(plan), xo.ec_plan_info(plan, er)
+            rows.append({
+                "code": f"RS({k},{m})", "matrix": name,
+                "encode_GBps": round(n * k * B / (ms_enc / 1e3) / 1e9, 1),
+                "encode_frac": round(n * (k + m) * B / (ms_enc / 1e3) / 1e9 / peak, 4),
+                "decode_GBps": round(n * k * B / (ms_dec / 1e3) / 1e9, 1),
+                "decode_frac": round(n * (k + m) * B / (ms_dec / 1e3) / 1e9 / peak, 4),
+                "enc_xors_raw": ie["raw"]["xors"], "enc_xors_fused": ie["fused"]["xors"],
+                "dec_xors_raw": idd["raw"]["xors"], "dec_xors_fused": idd["fused"]["xors"],
+                "parity": "bit-exact on sampled windows" if ok else "MISMATCH"})
+            xo.ec_plan_destroy(plan)
+        del data, par, rec
+        torch.cuda.empty_cache()
+    head = next(r for r in rows if r["code"] == "RS(10,4)" and r["matrix"] == "cauchy")
+    print(json.dumps({
+        "metric": METRIC, "value": head["encode_GBps"], "unit": "GB/s", "n_gpus": 1,
+        "steps": reps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (SplitMix64 bytes generated on the device)",
+        "config": {"workload": f"codes RS(8..10, 2..4), {n} stripes x d x 1 MiB, Cauchy and scaled "
+                               "Cauchy; decode erases data blocks 0..p-1",
+                   "l2": "inputs larger than L2 (129 MB); no flush"},
+        "codes": rows,
+        "parity": "bit-exact on sampled windows" if all_ok else "MISMATCH",
+        "device_status": xo.ec_device_status(),
+    }))
 
 
 def percentile(xs, q):
@@ -760,6 +873,8 @@ def main():
         run_served(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "codes":
+        run_codes(args)
     else:
         run_ours(args)
 

@@ -56,7 +56,15 @@ enum {
   EC_MATRIX_POWER = 1,  /* P[r][j] = 2^(r*j): the matrix whose XOR counts the
                            paper prints for RS(10,4) (Sec. 7.1, Sec. 7.5);
                            not MDS in general                                 */
-  EC_MATRIX_USER = 2    /* caller-supplied m x k parity rows, used as given   */
+  EC_MATRIX_USER = 2,   /* caller-supplied m x k parity rows, used as given   */
+  EC_MATRIX_CAUCHY_MIN = 3 /* the Cauchy rows and columns scaled by nonzero
+                           constants to few bitmatrix ones (the XOR count
+                           depends on the matrix, Sec. 7.6): each column
+                           divided by its row-0 entry (row 0 = all ones),
+                           then each later row divided by the entry of that
+                           row leaving the fewest ones (ties: smallest
+                           entry).  MDS like the Cauchy matrix; its parity
+                           bytes differ from EC_MATRIX_CAUCHY's          */
 };
 
 /* Optimiser level (which passes run before fusion and scheduling). */

@@ -56,6 +56,7 @@ def lib():
             L.orc_gf_tables.argtypes = [_u8p, _u8p]
             L.orc_cauchy.argtypes = [ctypes.c_int, ctypes.c_int, _u8p]
             L.orc_power.argtypes = [ctypes.c_int, ctypes.c_int, _u8p]
+            L.orc_cauchy_min.argtypes = [ctypes.c_int, ctypes.c_int, _u8p]
             L.orc_get_elem.restype = ctypes.c_uint8
             L.orc_get_elem.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_size_t]
             L.orc_set_elem.argtypes = [_u8p, ctypes.c_size_t, ctypes.c_size_t,
@@ -109,6 +110,14 @@ def gf_tables():
 def cauchy(k: int, m: int) -> np.ndarray:
     P = np.zeros((m, k), np.uint8)
     if lib().orc_cauchy(k, m, _p(P)) != 0:
+        raise ValueError("bad (k, m)")
+    return P
+
+
+def cauchy_min(k: int, m: int) -> np.ndarray:
+    """Cauchy rows and columns scaled to few bitmatrix ones (Sec. 7.6)."""
+    P = np.zeros((m, k), np.uint8)
+    if lib().orc_cauchy_min(k, m, _p(P)) != 0:
         raise ValueError("bad (k, m)")
     return P
 

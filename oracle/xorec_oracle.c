@@ -28,7 +28,11 @@
  * Parity status: every function here is pinned by tests that do not re-run
  * its own formula (field axioms checked exhaustively, spot values, a
  * hand-worked RS(2,1) example, unit vectors, linearity, brute-force MDS
- * recovery, the paper's printed XOR counts 755 and 1368).
+ * recovery, the paper's printed XOR counts 755 and 1368).  The scaled
+ * Cauchy matrix is pinned by structure (a row and column scaling of the
+ * Cauchy matrix, all-ones single parity row), by full rank of every survivor
+ * submatrix of RS(10,4) computed with carry-less arithmetic, by brute-force
+ * recovery, and by its bitmatrix ones counted from carry-less products.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -93,6 +97,49 @@ int orc_cauchy(int k, int m, uint8_t *P) {
   for (int i = 0; i < m; i++)
     for (int j = 0; j < k; j++)
       P[i * k + j] = orc_gf_inv((uint8_t)((k + i) ^ j));
+  return 0;
+}
+
+/* Number of ones in the 8x8 GF(2) matrix of multiplication by a: column t
+ * holds the bits of a * 2^t [Sec. 1, property (ii)]. */
+static int orc_ones(uint8_t a) {
+  int n = 0;
+  for (int t = 0; t < 8; t++) {
+    uint8_t col = orc_gf_mul(a, (uint8_t)(1u << t));
+    for (int b = 0; b < 8; b++) n += (col >> b) & 1;
+  }
+  return n;
+}
+
+/* Cauchy parity rows scaled to few bitmatrix ones.  The XOR count of a
+ * bitmatrix program is its number of ones minus one per row, and two
+ * matrices of one size can differ a lot in it [Sec. 7.6].  Multiplying a
+ * row or a column of P by a nonzero constant multiplies every square
+ * submatrix's determinant by a nonzero constant, so the code stays MDS.
+ * Steps: start from orc_cauchy; divide each column by its row-0 entry;
+ * then, for each row r >= 1 in turn, among the entries of row r choose the
+ * divisor that leaves the row with the fewest ones (on a tie the smallest
+ * entry) and divide the row by it. */
+int orc_cauchy_min(int k, int m, uint8_t *P) {
+  if (orc_cauchy(k, m, P) != 0) return -1;
+  for (int j = 0; j < k; j++) {
+    uint8_t top = P[j];
+    for (int i = 0; i < m; i++) P[i * k + j] = orc_gf_mul(P[i * k + j], orc_gf_inv(top));
+  }
+  for (int r = 1; r < m; r++) {
+    int best_ones = 1 << 30;
+    uint8_t best_div = 0;
+    for (int c = 0; c < k; c++) {
+      uint8_t div = P[r * k + c];
+      int ones = 0;
+      for (int j = 0; j < k; j++) ones += orc_ones(orc_gf_mul(P[r * k + j], orc_gf_inv(div)));
+      if (ones < best_ones || (ones == best_ones && div < best_div)) {
+        best_ones = ones;
+        best_div = div;
+      }
+    }
+    for (int j = 0; j < k; j++) P[r * k + j] = orc_gf_mul(P[r * k + j], orc_gf_inv(best_div));
+  }
   return 0;
 }
 

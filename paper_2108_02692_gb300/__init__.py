@@ -27,6 +27,7 @@ EC_ENOTSUP = _abi.EC_ENOTSUP
 EC_MATRIX_CAUCHY = _abi.EC_MATRIX_CAUCHY
 EC_MATRIX_POWER = _abi.EC_MATRIX_POWER
 EC_MATRIX_USER = _abi.EC_MATRIX_USER
+EC_MATRIX_CAUCHY_MIN = _abi.EC_MATRIX_CAUCHY_MIN
 EC_OPT_RAW = _abi.EC_OPT_RAW
 EC_OPT_REPAIR = _abi.EC_OPT_REPAIR
 EC_OPT_XORREPAIR = _abi.EC_OPT_XORREPAIR

@@ -314,6 +314,7 @@ ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix
   switch (matrix_kind) {
     case EC_MATRIX_CAUCHY: plan->P = xorec::cauchy_parity(k, m); break;
     case EC_MATRIX_POWER: plan->P = xorec::power_parity(k, m); break;
+    case EC_MATRIX_CAUCHY_MIN: plan->P = xorec::cauchy_min_parity(k, m); break;
     case EC_MATRIX_USER:
       if (!matrix) return fail(EC_EINVAL, "EC_MATRIX_USER needs a matrix");
       plan->P.assign(matrix, matrix + static_cast<size_t>(k) * m);

@@ -51,6 +51,38 @@ std::vector<uint8_t> cauchy_parity(int k, int m) {
   return P;
 }
 
+int bitmatrix_ones(uint8_t a) {
+  int n = 0;
+  for (int t = 0; t < 8; ++t) n += __builtin_popcount(gf_mul(a, static_cast<uint8_t>(1u << t)));
+  return n;
+}
+
+std::vector<uint8_t> cauchy_min_parity(int k, int m) {
+  std::vector<uint8_t> P = cauchy_parity(k, m);
+  auto at = [&](int i, int j) -> uint8_t& { return P[static_cast<size_t>(i) * k + j]; };
+  for (int j = 0; j < k; ++j) {
+    const uint8_t s = gf_inv(at(0, j));
+    for (int i = 0; i < m; ++i) at(i, j) = gf_mul(at(i, j), s);
+  }
+  for (int i = 1; i < m; ++i) {
+    int best_ones = -1;
+    uint8_t best = 1;
+    for (int c = 0; c < k; ++c) {
+      const uint8_t d = at(i, c);
+      const uint8_t s = gf_inv(d);
+      int ones = 0;
+      for (int j = 0; j < k; ++j) ones += bitmatrix_ones(gf_mul(at(i, j), s));
+      if (best_ones < 0 || ones < best_ones || (ones == best_ones && d < best)) {
+        best_ones = ones;
+        best = d;
+      }
+    }
+    const uint8_t s = gf_inv(best);
+    for (int j = 0; j < k; ++j) at(i, j) = gf_mul(at(i, j), s);
+  }
+  return P;
+}
+
 std::vector<uint8_t> power_parity(int k, int m) {
   std::vector<uint8_t> P(static_cast<size_t>(k) * m);
   for (int r = 0; r < m; ++r)

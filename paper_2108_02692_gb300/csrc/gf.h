@@ -15,6 +15,16 @@ uint8_t gf_exp2(unsigned e);        // 2^e
 // Parity rows of the systematic generator [I ; P] (m x k, row-major).
 // Cauchy: P[i][j] = 1 / ((k + i) XOR j); MDS for k + m <= 256.
 std::vector<uint8_t> cauchy_parity(int k, int m);
+// Cauchy rows and columns scaled by nonzero constants so that the bitmatrix
+// has few ones (the XOR count of an unoptimised program depends on the
+// matrix, Sec. 7.6): every column is divided by its entry in row 0 (row 0
+// becomes all ones), then every other row is divided by the entry of that
+// row that leaves the row with the fewest bitmatrix ones (ties: the smallest
+// entry).  Scaling rows and columns keeps every square submatrix
+// nonsingular, so the code stays MDS.
+std::vector<uint8_t> cauchy_min_parity(int k, int m);
+// Ones in the 8 x 8 GF(2) matrix of multiplication by a (Sec. 1, (ii)).
+int bitmatrix_ones(uint8_t a);
 // Power rows P[r][j] = 2^(r*j): the matrix that reproduces the XOR counts the
 // paper prints for RS(10,4) (Sec. 7.1, Sec. 7.5).  Not MDS in general.
 std::vector<uint8_t> power_parity(int k, int m);

@@ -91,10 +91,11 @@ def test_encode_matches_oracle(k, m, B, executor):
 
 @pytest.mark.parametrize("executor", EXECS, ids=EXEC_IDS)
 @pytest.mark.parametrize("opt", [xo.EC_OPT_RAW, xo.EC_OPT_REPAIR, xo.EC_OPT_XORREPAIR])
-def test_encode_opt_levels_and_power_matrix(opt, executor):
+def test_encode_opt_levels_and_matrices(opt, executor):
     k, m, B = 10, 4, 8 * 2064
     for kind, P in [(xo.EC_MATRIX_CAUCHY, oracle.cauchy(k, m)),
-                    (xo.EC_MATRIX_POWER, oracle.power(k, m))]:
+                    (xo.EC_MATRIX_POWER, oracle.power(k, m)),
+                    (xo.EC_MATRIX_CAUCHY_MIN, oracle.cauchy_min(k, m))]:
         h = xo.ec_plan_create_ex(k, m, matrix_kind=kind, opt_level=opt, executor=executor)
         try:
             data = [synth.block_bytes(22, kind, j, B) for j in range(k)]
@@ -405,3 +406,32 @@ def test_wide_code_decode():
             _decode_check(p, blocks, er, B)
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("executor", EXECS, ids=EXEC_IDS)
+def test_cauchy_min_every_decode_pattern_rs6_3(executor):
+    # scaled Cauchy: all 129 erasure sets of RS(6,3) recover the original
+    # blocks bit for bit (strips of 528 bytes: one 512-byte tile and a
+    # ragged 16-byte tail)
+    k, m, B = 6, 3, 8 * 528
+    P = oracle.cauchy_min(k, m)
+    h = xo.ec_plan_create_ex(k, m, matrix_kind=xo.EC_MATRIX_CAUCHY_MIN, executor=executor)
+    try:
+        data = [synth.block_bytes(23, 0, j, B) for j in range(k)]
+        blocks = data + oracle.encode(P, data)
+        d = [dev(x) for x in blocks]
+        par = [torch.empty(B, dtype=torch.uint8, device="cuda") for _ in range(m)]
+        xo.ec_encode(h, [t.data_ptr() for t in d[:k]], [t.data_ptr() for t in par], B, stream())
+        torch.cuda.synchronize()
+        for i in range(m):
+            assert np.array_equal(host(par[i]), blocks[k + i])
+        for ne in range(1, m + 1):
+            for er in itertools.combinations(range(k + m), ne):
+                out = [torch.empty(B, dtype=torch.uint8, device="cuda") for _ in er]
+                ptrs = [None if i in er else d[i].data_ptr() for i in range(k + m)]
+                xo.ec_decode(h, list(er), ptrs, [t.data_ptr() for t in out], B, stream())
+                torch.cuda.synchronize()
+                for i, e in enumerate(er):
+                    assert np.array_equal(host(out[i]), blocks[e]), (er, e)
+    finally:
+        xo.ec_plan_destroy(h)

@@ -227,3 +227,99 @@ def test_splitmix64_published_vector():
     assert np.array_equal(synth.stream_words(12345, 17, 5), w[17:22])
     b = synth.stream_bytes(99, 0, 100)
     assert np.array_equal(synth.stream_bytes(99, 13, 50), b[13:63])
+
+
+# ---- scaled Cauchy matrix (few bitmatrix ones, Sec. 7.6) ------------------
+
+def _ones_clmul(a: int) -> int:
+    """Ones of the 8x8 bitmatrix of a, from the carry-less product."""
+    return sum(bin(clmul_mod(a, 1 << t)).count("1") for t in range(8))
+
+
+def _inv_clmul(a: int) -> int:
+    return next(b for b in range(1, 256) if clmul_mod(a, b) == 1)
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 255])
+def test_cauchy_min_single_parity_is_all_ones(k):
+    # m = 1: every column is divided by its only entry -> plain XOR parity
+    assert np.array_equal(oracle.cauchy_min(k, 1), np.ones((1, k), np.uint8))
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (6, 3), (10, 4), (12, 4), (20, 8)])
+def test_cauchy_min_is_a_row_and_column_scaling(k, m):
+    C = oracle.cauchy(k, m)
+    Q = oracle.cauchy_min(k, m)
+    assert (Q[0] == 1).all()
+    # Q[i][j] = r_i * c_j * C[i][j]: the ratios form a rank-one table
+    ratio = [[clmul_mod(int(Q[i, j]), _inv_clmul(int(C[i, j]))) for j in range(k)]
+             for i in range(m)]
+    assert all(ratio[i][j] != 0 for i in range(m) for j in range(k))
+    for i in range(m):
+        for j in range(k):
+            assert clmul_mod(ratio[i][j], ratio[0][0]) == clmul_mod(ratio[i][0], ratio[0][j])
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (6, 3), (10, 4), (8, 4), (12, 4)])
+def test_cauchy_min_has_fewer_ones_and_locally_best_rows(k, m):
+    C = oracle.cauchy(k, m)
+    Q = oracle.cauchy_min(k, m)
+    ones_c = sum(_ones_clmul(int(x)) for x in C.flat)
+    ones_q = sum(_ones_clmul(int(x)) for x in Q.flat)
+    assert ones_q < ones_c
+    assert int(oracle.bitmatrix(Q).sum()) == ones_q
+    # no other divisor taken from a row leaves that row with fewer ones
+    for i in range(1, m):
+        row = [int(x) for x in Q[i]]
+        here = sum(_ones_clmul(x) for x in row)
+        for d in row:
+            di = _inv_clmul(d)
+            assert sum(_ones_clmul(clmul_mod(x, di)) for x in row) >= here
+
+
+def _rank_gf(M, T, inv):
+    M = [list(map(int, r)) for r in M]
+    n, c = len(M), len(M[0])
+    r = 0
+    for col in range(c):
+        piv = next((i for i in range(r, n) if M[i][col]), None)
+        if piv is None:
+            continue
+        M[r], M[piv] = M[piv], M[r]
+        s = inv[M[r][col]]
+        M[r] = [int(T[s, x]) for x in M[r]]
+        for i in range(n):
+            if i != r and M[i][col]:
+                f = M[i][col]
+                M[i] = [x ^ int(T[f, y]) for x, y in zip(M[i], M[r])]
+        r += 1
+    return r
+
+
+def test_cauchy_min_rs10_4_every_survivor_set_invertible(mul_table):
+    # MDS: the k x k submatrix of [I ; P] of every set of k survivors has full
+    # rank, checked with elimination over the carry-less table
+    k, m = 10, 4
+    T = np.array([[clmul_mod(a, b) for b in range(256)] for a in range(256)], np.uint8)
+    assert np.array_equal(T, mul_table)
+    inv = [0] + [_inv_clmul(a) for a in range(1, 256)]
+    G = np.vstack([np.eye(k, dtype=np.uint8), oracle.cauchy_min(k, m)])
+    n = 0
+    for rows in itertools.combinations(range(k + m), k):
+        assert _rank_gf(G[list(rows)], T, inv) == k, rows
+        n += 1
+    assert n == 1001
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (6, 3)])
+def test_cauchy_min_bruteforce_recovery(k, m):
+    P = oracle.cauchy_min(k, m)
+    B = 64
+    data = [synth.block_bytes(9, k, j, B) for j in range(k)]
+    blocks = data + oracle.encode(P, data)
+    for ne in range(1, m + 1):
+        for er in itertools.combinations(range(k + m), ne):
+            avail = [None if i in er else blocks[i] for i in range(k + m)]
+            rec = oracle.decode(P, list(er), avail)
+            for i, e in enumerate(er):
+                assert np.array_equal(rec[i], blocks[e]), (er, e)

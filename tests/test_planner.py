@@ -317,6 +317,34 @@ def test_plan_info_rs10_4():
         xo.ec_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("k,m", [(1, 1), (4, 2), (6, 3), (10, 4), (12, 4), (100, 4)])
+def test_plan_cauchy_min_matrix_and_counts(k, m):
+    # the planner's scaled Cauchy matrix equals the oracle's, and its
+    # unoptimised program has one XOR per bitmatrix one beyond the first of
+    # each row (Sec. 2, Sec. 7.6)
+    plan = xo.ec_plan_create_ex(k, m, matrix_kind=xo.EC_MATRIX_CAUCHY_MIN)
+    try:
+        Q = oracle.cauchy_min(k, m)
+        assert np.array_equal(xo.ec_plan_matrix(plan, k, m), Q)
+        info = xo.ec_plan_info(plan)
+        bits = oracle.bitmatrix(Q)
+        assert info["raw"]["xors"] == int(bits.sum()) - 8 * m
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+def test_plan_cauchy_min_rs10_4_fewer_xors():
+    plain = xo.ec_plan_create_ex(10, 4, matrix_kind=xo.EC_MATRIX_CAUCHY)
+    scaled = xo.ec_plan_create_ex(10, 4, matrix_kind=xo.EC_MATRIX_CAUCHY_MIN)
+    try:
+        a, b = xo.ec_plan_info(plain), xo.ec_plan_info(scaled)
+        assert a["raw"]["xors"] == 1234 and b["raw"]["xors"] == 832
+        assert b["fused"]["xors"] < a["fused"]["xors"]
+    finally:
+        xo.ec_plan_destroy(plain)
+        xo.ec_plan_destroy(scaled)
+
+
 def test_plan_argument_errors():
     with pytest.raises(xo.XorecError) as e:
         xo.ec_plan_create(0, 2)
