@@ -671,6 +671,11 @@ def run_served(args):
     warm_s = 1.0
     reqs = synth.served_requests(args.serve_seconds + warm_s, args.serve_rate)
     plans = {c: xo.ec_plan_create(*c) for c in ((10, 4), (6, 3))}
+    tuned = {}
+    if not args.no_tune:
+        for c, h in plans.items():
+            r = xo.ec_plan_autotune(h, 1 << 20, 16, torch.cuda.current_stream().cuda_stream)
+            tuned[f"RS{c}"] = {"threads": r["threads"], "reg_budget": r["reg_budget"]}
     t0 = time.perf_counter()
     probe = xo.ec_server_create()
     for c, p in plans.items():
@@ -693,7 +698,7 @@ def run_served(args):
         "config": {"workload": f"served: Poisson {args.serve_rate:.0f} req/s for "
                                f"{args.serve_seconds:.0f} s (+{warm_s:.0f} s warm-up), RS(10,4)/RS(6,3), "
                                "objects log-uniform 4 KiB-16 MiB, 50% decodes with 1..m erasures, "
-                               "32 GiB admission budget"},
+                               "32 GiB admission budget", "autotune": tuned or None},
         "served": served,
         "plain": plain,
         "p99_plain_over_served": round(plain["p99_us"] / served["p99_us"], 2),
@@ -724,6 +729,14 @@ def run_batched(args):
     mix = mix[:n]
     arena = torch.empty(int(need), dtype=torch.uint8, device="cuda")
     plans = {c: xo.ec_plan_create(*c) for c in synth.BATCH_CODES}
+    sp0 = torch.cuda.current_stream().cuda_stream
+    tuned = {}
+    if not args.no_tune:
+        # per-code launch shape (strip tile = 4 x threads bytes) and register
+        # budget; the batch compiles each code's modules with its own shape
+        for c, h in plans.items():
+            r = xo.ec_plan_autotune(h, 1 << 20, 16, sp0)
+            tuned[f"RS{c}"] = {"threads": r["threads"], "reg_budget": r["reg_budget"]}
     jobs, pos, bytes_in, moved, where = [], 0, 0, 0, []
     base = arena.data_ptr()
     sp = torch.cuda.current_stream().cuda_stream
@@ -761,7 +774,24 @@ def run_batched(args):
         xo.ec_batch_run(batch, sp)
     ev1.record()
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / reps
+    ms_eager = ev0.elapsed_time(ev1) / reps
+    # the same run captured once in a CUDA graph and replayed
+    gs = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        xo.ec_batch_run(batch, gs.cuda_stream)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(gs):
+        for _ in range(max(1, args.warmup)):
+            graph.replay()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(gs)
+        for _ in range(reps):
+            graph.replay()
+        g1.record(gs)
+    torch.cuda.synchronize()
+    ms = g0.elapsed_time(g1) / reps
+    del graph
     # plain: one launch per stripe with the same compiled programs
     singles = [xo.ec_batch_create([j]) for j in jobs]
     for b in singles[:64]:
@@ -784,8 +814,11 @@ def run_batched(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (SplitMix64 bytes generated on the device)",
         "config": {"workload": f"batched: {n} stripes, RS(6,3)/(8,4)/(10,4)/(12,4), blocks "
-                               "log-uniform 4 KiB-8 MiB, ~50% decodes with 1..m erasures",
-                   "input_bytes": bytes_in, "moved_bytes": moved},
+                               "log-uniform 4 KiB-8 MiB, ~50% decodes with 1..m erasures; one "
+                               "ec_batch_run replayed as a CUDA graph",
+                   "input_bytes": bytes_in, "moved_bytes": moved, "autotune": tuned or None},
+        "eager": {"value": round(bytes_in / (ms_eager / 1e3) / 1e9, 2),
+                  "ms_per_step": round(ms_eager, 3)},
         "roofline": {"bound": "hbm", "achieved": round(moved / (ms / 1e3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(moved / (ms / 1e3) / 1e9 / peak, 4)},
         "plain": {"value": round(bytes_in / (ms_plain / 1e3) / 1e9, 2), "ms_per_step": round(ms_plain, 2),

@@ -134,6 +134,8 @@ typedef struct {
   int regs;             /* registers per thread of the compiled kernel        */
   int temps;            /* temporaries kept by (Xor)RePair                    */
   int max_live;         /* values live at once with inputs preloaded          */
+  int threads;          /* threads per CTA of the compiled tier (strip tile =
+                           4 x threads bytes): the plan's launch shape        */
 } ec_program_info;
 
 /* Program of the encoder (erasures == NULL) or of the decoder for the given
@@ -242,6 +244,16 @@ typedef struct {
 
 ec_status ec_plan_autotune(ec_plan *plan, size_t block_bytes, int n_stripes, void *stream,
                            ec_tune_result *out);
+
+/* Set the launch shape without timing: `threads` per CTA of the compiled
+ * tier (a multiple of 32 in [32, 1024]; the strip tile is 4 x threads bytes)
+ * and the register budget of the XorRePair temporaries ([32, 255]).  The
+ * encoder is rebuilt with that budget; decoders and batch modules built
+ * afterwards use the same budget and shape (the paper's cache-capacity
+ * parameter, Sec. 6.2, retargeted to registers).  Host-only; EC_EINVAL for
+ * values out of range.  Must not run concurrently with other calls on the
+ * same plan. */
+ec_status ec_plan_set_launch(ec_plan *plan, int threads, int reg_budget);
 
 /* Select the executor tier (EC_EXEC_*).  EC_EXEC_COMPILED fails with
  * EC_ENOTSUP when no run-time compiler is present. */

@@ -124,7 +124,7 @@ def ec_plan_info(plan: int, erasures=None) -> dict:
             "code_words": info.code_words, "sched_nvar": info.sched_nvar,
             "raw": _stats(info.raw), "compressed": _stats(info.compressed),
             "fused": _stats(info.fused), "compiled": bool(info.compiled), "regs": info.regs,
-            "temps": info.temps, "max_live": info.max_live}
+            "temps": info.temps, "max_live": info.max_live, "threads": info.threads}
 
 
 def ec_plan_program(plan: int, erasures=None) -> np.ndarray:
@@ -143,6 +143,10 @@ def ec_plan_autotune(plan: int, block_bytes: int, n_stripes: int = 16, stream: i
     r = _abi.TuneResult()
     _check(lib().ec_plan_autotune(plan, block_bytes, n_stripes, stream or None, ctypes.byref(r)))
     return {f: getattr(r, f) for f, _ in _abi.TuneResult._fields_}
+
+
+def ec_plan_set_launch(plan: int, threads: int, reg_budget: int) -> None:
+    _check(lib().ec_plan_set_launch(plan, threads, reg_budget))
 
 
 def ec_plan_set_executor(plan: int, executor: int) -> None:

@@ -48,7 +48,7 @@ class ProgramInfo(ctypes.Structure):
     _fields_ = [("n_in", c_int), ("n_out", c_int), ("slots", c_int), ("stmts", c_int),
                 ("code_words", c_int), ("sched_nvar", c_int), ("raw", SlpStats),
                 ("compressed", SlpStats), ("fused", SlpStats), ("compiled", c_int),
-                ("regs", c_int), ("temps", c_int), ("max_live", c_int)]
+                ("regs", c_int), ("temps", c_int), ("max_live", c_int), ("threads", c_int)]
 
 
 EC_OP_ENCODE, EC_OP_DECODE = 0, 1
@@ -101,6 +101,7 @@ SIGNATURES = {
     "ec_decode_prepare": (c_int, [c_vp, intp, intp, c_int, c_int]),
     "ec_plan_compile": (c_int, [c_vp, intp, intp, c_int, c_int]),
     "ec_plan_autotune": (c_int, [c_vp, c_size, c_int, c_vp, ctypes.POINTER(TuneResult)]),
+    "ec_plan_set_launch": (c_int, [c_vp, c_int, c_int]),
     "ec_plan_set_executor": (c_int, [c_vp, c_int]),
     "ec_batch_create": (c_int, [ctypes.POINTER(Job), c_int, c_int, ctypes.POINTER(c_vp)]),
     "ec_batch_run": (c_int, [c_vp, c_vp]),

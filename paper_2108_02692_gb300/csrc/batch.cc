@@ -42,6 +42,7 @@ int batch_minb() { return env_int("EC_BATCH_MINB", 512 / batch_threads()); }
 
 struct Launch {
   void* mod = nullptr;                 // compiled module, or nullptr = interpreter
+  int threads = 128;                   // threads per CTA; tiles of 4 x threads bytes
   int stripe_begin = 0, n_stripes = 0; // the launch's stripes in the descriptor array
   long long n_items = 0;
   int max_in = 0, max_slots = 0;
@@ -77,7 +78,6 @@ struct ec_batch {
   std::vector<cudaEvent_t> done;
   cudaEvent_t fork = nullptr;
   int chunk = 8;
-  int threads = 128;
   xk::u64* d_queues = nullptr;         // one work-queue head per launch
   xk::StripeDesc* d_descs = nullptr;
   xk::u64* d_blocks = nullptr;
@@ -174,20 +174,35 @@ ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
   return EC_OK;
 }
 
-int batch_threads_default() { return batch_threads(); }
-int batch_minb_default() { return batch_minb(); }
 
-// Compile every program of `want` that has no module for this block size
-// into modules of at most EC_BATCH_MODULE_SIZE programs (per plan and input
-// width, NVRTC, in parallel host threads).  Modules belong to their plan.
-ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, int threads,
-                          int minb, bool must, int* built) {
+// Launch shape of a plan's compiled modules: the autotuner's choice for the
+// plan (threads per CTA, hence the strip tile of 4 x threads bytes, and
+// resident CTAs per SM, hence the register cap), else the defaults.
+int plan_module_threads(const ec_plan* p) {
+  return p->tuned_threads > 0 ? p->tuned_threads : batch_threads();
+}
+
+int plan_module_minb(const ec_plan* p) {
+  return p->tuned_threads > 0 && p->tuned_minb > 0 ? p->tuned_minb : batch_minb();
+}
+
+// Threads per CTA of the launch that runs `prog`: its module's, or the
+// interpreter's default.
+int launch_threads(void* mod) { return mod ? jit_module_threads(mod) : batch_threads(); }
+
+// Compile every program of `want` that has no module of its plan's launch
+// shape into modules of at most EC_BATCH_MODULE_SIZE programs (per plan and
+// input width, NVRTC, in parallel host threads).  Modules belong to their
+// plan.
+ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, bool must,
+                          int* built) {
   const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 32));
   DeviceInfo di;
   if (!device_info(&di)) return EC_ECUDA;
   std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
   std::vector<Program*> seen;
   for (const auto& w : want) {
+    const int threads = plan_module_threads(w.first);
     if (!compiled_tier_fits(w.second, threads, di.smem_optin)) continue;   // interpreter
     std::lock_guard<std::mutex> lk(w.first->mu);
     if ((w.second->mod && jit_module_threads(w.second->mod) == threads) ||
@@ -207,7 +222,8 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
   std::vector<void*> mods(to_compile.size(), nullptr);
   parallel_for(to_compile.size(), [&](size_t i) {
     std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
-    mods[i] = jit_compile_module(ps, threads, minb, &errs[i]);
+    ec_plan* plan = to_compile[i].first;
+    mods[i] = jit_compile_module(ps, plan_module_threads(plan), plan_module_minb(plan), &errs[i]);
   });
   if (built) *built = static_cast<int>(to_compile.size());
   for (size_t i = 0; i < to_compile.size(); ++i) {
@@ -291,21 +307,17 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     ec_status s = job_pointers(&e);
     if (s != EC_OK) return s;
     e.S = static_cast<long long>(e.job->block_bytes / 8);
-    e.tiles = (e.S + 4 * batch_threads() - 1) / (4 * batch_threads());
   }
 
   // 3. tiers: compile programs without a module (per plan, per input width)
   bool compiled = executor != EC_EXEC_INTERP && xorec::jit_available();
   if (executor == EC_EXEC_COMPILED && !compiled)
     return fail(EC_ENOTSUP, "no run-time compiler available");
-  const int kThreads = batch_threads();
-  const int minb = batch_minb();
   int modules_built = 0;
   if (compiled) {
     std::vector<std::pair<ec_plan*, Program*>> want;
     for (auto& e : ents) want.emplace_back(e.plan, e.prog);
-    const ec_status cs = xorec::compile_modules(want, kThreads, minb, executor == EC_EXEC_COMPILED,
-                                                &modules_built);
+    const ec_status cs = xorec::compile_modules(want, executor == EC_EXEC_COMPILED, &modules_built);
     if (cs != EC_OK) return cs;
   }
 
@@ -314,7 +326,6 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   b->device = di.device;
   b->status = di.status;
   b->chunk = std::max(1, env_int("EC_BATCH_CHUNK", 2));
-  b->threads = kThreads;
   std::map<void*, int> launch_of;
   for (auto& e : ents) {
     void* mod = compiled ? e.prog->mod : nullptr;
@@ -323,10 +334,12 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       it = launch_of.emplace(mod, static_cast<int>(b->launches.size())).first;
       Launch L;
       L.mod = mod;
+      L.threads = xorec::launch_threads(mod);
       b->launches.push_back(L);
     }
     e.launch = it->second;
     Launch& L = b->launches[e.launch];
+    e.tiles = (e.S + 4 * L.threads - 1) / (4 * L.threads);
     L.max_in = std::max(L.max_in, e.prog->n_in);
     if (!mod) L.max_slots = std::max(L.max_slots, e.prog->n_slots);
   }
@@ -404,7 +417,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   for (auto& L : b->launches) {
     int per_sm = 1;
     if (L.mod) ++n_modules;
-    if (!xorec::batch_launch_shape(L.mod, L.max_in, L.max_slots, kThreads, di.smem_optin, &L.smem,
+    if (!xorec::batch_launch_shape(L.mod, L.max_in, L.max_slots, L.threads, di.smem_optin, &L.smem,
                                    &per_sm)) {
       free_batch(b);
       return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
@@ -461,7 +474,6 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
 }
 
 ec_status ec_batch_run(ec_batch* b, void* stream) {
-  const int kThreads = b->threads;
   if (!b) return fail(EC_EINVAL, "NULL batch");
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   if (b->launches.empty()) return EC_OK;
@@ -484,11 +496,11 @@ ec_status ec_batch_run(ec_batch* b, void* stream) {
     bp.chunk = b->chunk;
     bp.queue = b->d_queues + li;
     bp.n_items = L.n_items;
-    bp.T = 4 * kThreads;
+    bp.T = 4 * L.threads;
     bp.max_in = L.max_in;
     bp.status = b->status;
     const bool ok = L.mod ? xorec::jit_module_launch(L.mod, bp, L.grid, L.smem, st)
-                          : xorec::launch_interp_batch(bp, kThreads, L.grid, L.smem, st);
+                          : xorec::launch_interp_batch(bp, L.threads, L.grid, L.smem, st);
     if (!ok) return EC_ECUDA;
   }
   if (fan) {

@@ -411,6 +411,7 @@ ec_status ec_plan_info(ec_plan* plan, const int* erasures, int n_erasures, ec_pr
   out->regs = xorec::jit_regs(p);
   out->temps = p->stats.temps;
   out->max_live = p->stats.max_live;
+  out->threads = p->threads > 0 ? p->threads : xorec::env_int("EC_JIT_THREADS", 128);
   return EC_OK;
 }
 

@@ -99,10 +99,9 @@ void host_io_release(xorec_host_io* h);
 // Batch helpers (batch.cc), shared with the serving loop.
 ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
                       std::vector<uint64_t>* ptrs);
-int batch_threads_default();
-int batch_minb_default();
-ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, int threads,
-                          int minb, bool must, int* built);
+int launch_threads(void* mod);
+ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, bool must,
+                          int* built);
 bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
                         size_t* smem, int* per_sm);
 

@@ -35,6 +35,7 @@ namespace {
 struct Req {
   uint64_t ticket = 0;
   Program* prog = nullptr;
+  void* mod = nullptr;          // compiled module that runs it, or nullptr = interpreter
   std::vector<uint64_t> ptrs;
   long long S = 0, tiles = 0;
   size_t bytes = 0;
@@ -66,7 +67,7 @@ struct ec_server {
   int device = -1;
   size_t budget = 0;
   int max_batch = 0;
-  int threads = 128, minb = 4, chunk = 2;
+  int chunk = 2;
   xorec::DeviceInfo di;
   std::mutex mu;
   std::condition_variable cv;
@@ -115,23 +116,20 @@ bool grow_blocks(Slot& s, size_t need) {
 // Launch one batch of requests on a free slot.
 bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
   // group by launch target: compiled module of this block size, or interpreter
-  auto target = [&](const Req& r) -> void* {
-    return r.prog->mod && xorec::jit_module_threads(r.prog->mod) == sv->threads ? r.prog->mod
-                                                                                : nullptr;
-  };
+  auto target = [&](const Req& r) -> void* { return r.mod; };
   std::stable_sort(reqs.begin(), reqs.end(),
                    [&](const Req& a, const Req& b) { return target(a) < target(b); });
   size_t n_blocks = 0;
   for (const auto& r : reqs) n_blocks += r.ptrs.size();
   if (!grow_blocks(sl, n_blocks)) return false;
-  struct L { void* mod; int begin, n; long long items; int max_in, max_slots; };
+  struct L { void* mod; int threads, begin, n; long long items; int max_in, max_slots; };
   std::vector<L> launches;
   size_t off = 0;
   for (size_t i = 0; i < reqs.size(); ++i) {
     const Req& r = reqs[i];
     void* mod = target(r);
     if (launches.empty() || launches.back().mod != mod)
-      launches.push_back(L{mod, static_cast<int>(i), 0, 0, 0, 0});
+      launches.push_back(L{mod, xorec::launch_threads(mod), static_cast<int>(i), 0, 0, 0, 0});
     L& l = launches.back();
     xk::StripeDesc& d = sl.h_descs[i];
     std::memset(&d, 0, sizeof(d));
@@ -166,7 +164,7 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
     if (it == sv->shapes.end()) {
       size_t smem = 0;
       int per_sm = 1;
-      if (!xorec::batch_launch_shape(l.mod, l.max_in, l.max_slots, sv->threads, sv->di.smem_optin,
+      if (!xorec::batch_launch_shape(l.mod, l.max_in, l.max_slots, l.threads, sv->di.smem_optin,
                                      &smem, &per_sm))
         return false;
       it = sv->shapes.emplace(key, std::make_pair(smem, per_sm)).first;
@@ -178,13 +176,13 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
     bp.chunk = sv->chunk;
     bp.queue = sl.d_queues + li;
     bp.n_items = l.items;
-    bp.T = 4 * sv->threads;
+    bp.T = 4 * l.threads;
     bp.max_in = l.max_in;
     bp.status = sv->di.status;
     const long long full = static_cast<long long>(sv->di.sms) * it->second.second;
     const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(full, l.items)));
     const bool ok = l.mod ? xorec::jit_module_launch(l.mod, bp, grid, it->second.first, sl.st)
-                          : xorec::launch_interp_batch(bp, sv->threads, grid, it->second.first, sl.st);
+                          : xorec::launch_interp_batch(bp, l.threads, grid, it->second.first, sl.st);
     if (!ok) return false;
   }
   if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) return false;
@@ -273,8 +271,6 @@ ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
   sv->budget = opts && opts->hbm_budget ? opts->hbm_budget : (static_cast<size_t>(32) << 30);
   sv->max_batch = opts && opts->max_batch > 0 ? opts->max_batch : 512;
   const int n_slots = opts && opts->slots > 0 ? opts->slots : 4;
-  sv->threads = xorec::batch_threads_default();
-  sv->minb = xorec::batch_minb_default();
   sv->chunk = std::max(1, env_int("EC_BATCH_CHUNK", 2));
   sv->slots.resize(n_slots);
   for (Slot& sl : sv->slots) {
@@ -328,7 +324,7 @@ ec_status ec_server_warm(ec_server* sv, ec_plan* plan, int max_erasures) {
     want.emplace_back(plan, p);
   }
   if (!xorec::jit_available()) return EC_OK;   // interpreter serves everything
-  return xorec::compile_modules(want, sv->threads, sv->minb, false, nullptr);
+  return xorec::compile_modules(want, false, nullptr);
 }
 
 ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
@@ -338,15 +334,17 @@ ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
   ec_status s = xorec::resolve_job(*job, &r.prog, &er, &r.ptrs);
   if (s != EC_OK) return s;
   {
-    bool compiled_here = r.prog->mod && xorec::jit_module_threads(r.prog->mod) == sv->threads;
-    if (!compiled_here) {
-      std::lock_guard<std::mutex> lk(job->plan->mu);
-      if (!xorec::ensure_device_code(r.prog)) return EC_ECUDA;
-    }
+    // launch target fixed at submission: the program's compiled module
+    // (modules live as long as their plan; a launch takes its module's
+    // block size), else the interpreter
+    std::lock_guard<std::mutex> lk(job->plan->mu);
+    r.mod = r.prog->mod;
+    if (!r.mod && !xorec::ensure_device_code(r.prog)) return EC_ECUDA;
   }
   const size_t B = job->block_bytes;
+  const int th = xorec::launch_threads(r.mod);
   r.S = static_cast<long long>(B / 8);
-  r.tiles = (r.S + 4 * sv->threads - 1) / (4 * sv->threads);
+  r.tiles = (r.S + 4 * th - 1) / (4 * th);
   r.bytes_in = static_cast<long long>(r.prog->n_in / 8) * static_cast<long long>(B);
   r.bytes_out = static_cast<long long>(r.prog->n_out / 8) * static_cast<long long>(B);
   r.bytes = static_cast<size_t>(r.bytes_in + r.bytes_out);

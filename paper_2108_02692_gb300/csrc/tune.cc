@@ -29,7 +29,38 @@ int minb_for(int threads, int reg_budget) {
   return minb;
 }
 
+// Make `prog` the plan's encoder and (threads, reg_budget) the launch shape
+// of the plan's compiled programs and batch modules built from now on.
+void install(ec_plan* plan, std::unique_ptr<Program> prog, int threads, int reg_budget) {
+  std::lock_guard<std::mutex> lk(plan->mu);
+  // the old encoder may still be referenced by existing batches: retire it
+  plan->retired.push_back(std::move(plan->enc));
+  plan->enc = std::move(prog);
+  plan->opts.reg_budget = reg_budget;
+  plan->opts.max_temps = -2;
+  plan->tuned_threads = threads;
+  plan->tuned_minb = minb_for(threads, reg_budget);
+}
+
 }  // namespace
+
+extern "C" ec_status ec_plan_set_launch(ec_plan* plan, int threads, int reg_budget) {
+  if (!plan) return fail(EC_EINVAL, "NULL plan");
+  if (threads < 32 || threads > 1024 || threads % 32 != 0)
+    return fail(EC_EINVAL, "threads must be a multiple of 32 in [32, 1024]");
+  if (reg_budget < 32 || reg_budget > 255) return fail(EC_EINVAL, "reg_budget must be in [32, 255]");
+  xorec::PlanOptions o = plan->opts;
+  o.reg_budget = reg_budget;
+  o.max_temps = -2;
+  auto prog = std::make_unique<Program>();
+  std::string err;
+  if (!xorec::build_program(plan->m, plan->k, plan->P.data(), o, prog.get(), &err))
+    return fail(EC_EINVAL, err);
+  prog->threads = threads;
+  prog->minb = minb_for(threads, reg_budget);
+  install(plan, std::move(prog), threads, reg_budget);
+  return EC_OK;
+}
 
 extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_stripes,
                                       void* stream, ec_tune_result* out) {
@@ -135,16 +166,7 @@ extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_s
   }
   if (best < 0) return fail(EC_ENOTSUP, "no candidate fits the compiled tier");
   // install: encoder program, budget and launch shape for later decoders
-  {
-    std::lock_guard<std::mutex> lk(plan->mu);
-    // the old encoder may still be referenced by existing batches: retire it
-    plan->retired.push_back(std::move(plan->enc));
-    plan->enc = std::move(best_prog);
-    plan->opts.reg_budget = cands[best].reg_budget;
-    plan->opts.max_temps = -2;
-    plan->tuned_threads = cands[best].threads;
-    plan->tuned_minb = minb_for(cands[best].threads, cands[best].reg_budget);
-  }
+  install(plan, std::move(best_prog), cands[best].threads, cands[best].reg_budget);
   if (out) {
     out->threads = cands[best].threads;
     out->reg_budget = cands[best].reg_budget;

@@ -345,6 +345,24 @@ def test_plan_cauchy_min_rs10_4_fewer_xors():
         xo.ec_plan_destroy(scaled)
 
 
+def test_set_launch_shape_host_side():
+    # (threads, register budget) pinned without timing: the encoder is
+    # rebuilt under the new budget and reports the launch shape
+    plan = xo.ec_plan_create(10, 4)
+    try:
+        assert xo.ec_plan_info(plan)["threads"] == 128
+        xo.ec_plan_set_launch(plan, 256, 96)
+        info = xo.ec_plan_info(plan)
+        assert info["threads"] == 256 and info["max_live"] <= 96
+        assert xo.ec_plan_info(plan, [3, 12])["threads"] == 256
+        for bad in [(0, 128), (100, 128), (2048, 128), (128, 16), (128, 300)]:
+            with pytest.raises(xo.XorecError) as e:
+                xo.ec_plan_set_launch(plan, *bad)
+            assert e.value.status == xo.EC_EINVAL
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
 def test_plan_argument_errors():
     with pytest.raises(xo.XorecError) as e:
         xo.ec_plan_create(0, 2)
