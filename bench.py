@@ -52,6 +52,9 @@ def parse_args():
                     help="coding matrix (default: Cauchy)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-idle-spin-us", type=int, default=0,
+                    help="scheduler polling window before it sleeps (0 = library default "
+                         "1000 us, -1 = sleep at once)")
     ap.add_argument("--batched-stripes", type=int, default=8192)
     ap.add_argument("--executor", default="auto", choices=["auto", "interp", "compiled"])
     ap.add_argument("--opt", default="xorrepair", choices=["raw", "repair", "xorrepair"],
@@ -589,7 +592,7 @@ def percentile(xs, q):
 
 
 def serve_stream(xo, torch, reqs, plans, data_arena, out_arena, max_batch, slots, warm_s,
-                 budget=32 << 30):
+                 budget=32 << 30, idle_spin_us=0):
     """Replay a request trace against a server; returns latencies (µs) of the
     requests that arrived after warm_s, and server stats."""
     import numpy as np
@@ -618,7 +621,8 @@ def serve_stream(xo, torch, reqs, plans, data_arena, out_arena, max_batch, slots
                          "out": outs, "block_bytes": B})
         in_bytes.append(k * B)
     arr, keep = xo.make_jobs(jobs)
-    server = xo.ec_server_create(hbm_budget=budget, max_batch=max_batch, slots=slots)
+    server = xo.ec_server_create(hbm_budget=budget, max_batch=max_batch, slots=slots,
+                                 idle_spin_us=idle_spin_us)
     t_ticket = {}
     lat = {}
     n = len(reqs)
@@ -686,8 +690,11 @@ def run_served(args):
     xo.ec_synth_fill(data_arena.data_ptr(), data_arena.numel(), synth.block_seed(5, 0, 0), 0, 0)
     out_arena = torch.empty(48 << 30, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
-    served = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 512, 4, warm_s)
-    plain = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 1, 1, warm_s)
+    spin = args.serve_idle_spin_us
+    served = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 512, 4, warm_s,
+                          idle_spin_us=spin)
+    plain = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 1, 1, warm_s,
+                         idle_spin_us=spin)
     for p in plans.values():
         xo.ec_plan_destroy(p)
     out = {

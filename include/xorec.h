@@ -319,6 +319,10 @@ typedef struct {
   size_t hbm_budget;     /* bytes of request blocks admitted at once (0 = 32 GiB) */
   int max_batch;         /* requests per batch (0 = 512)                          */
   int slots;             /* batches in flight on separate streams (0 = 4)         */
+  int idle_spin_us;      /* after its last work the scheduler keeps polling for
+                            this long before it sleeps on a condition variable
+                            (0 = 1000 us; < 0 = sleep at once).  Polling costs
+                            one host core and spares each request the wake-up */
 } ec_server_opts;
 
 typedef struct {

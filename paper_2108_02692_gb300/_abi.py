@@ -67,7 +67,8 @@ class BatchInfo(ctypes.Structure):
 
 
 class ServerOpts(ctypes.Structure):
-    _fields_ = [("hbm_budget", c_size), ("max_batch", c_int), ("slots", c_int)]
+    _fields_ = [("hbm_budget", c_size), ("max_batch", c_int), ("slots", c_int),
+                ("idle_spin_us", c_int)]
 
 
 class ServerStats(ctypes.Structure):

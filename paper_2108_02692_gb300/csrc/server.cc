@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -68,15 +69,17 @@ struct ec_server {
   size_t budget = 0;
   int max_batch = 0;
   int chunk = 2;
+  std::chrono::microseconds idle_spin{1000};
   xorec::DeviceInfo di;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Req> pending;
+  std::atomic<size_t> n_pending{0};   // pending.size(), readable without the lock
   size_t admitted = 0;
   std::vector<Slot> slots;
   std::vector<std::pair<uint64_t, double>> done;
   uint64_t next_ticket = 1;
-  bool stop = false;
+  std::atomic<bool> stop{false};
   int error = EC_OK;
   std::thread th;
   ec_server_stats stats{};
@@ -193,6 +196,7 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
 
 void scheduler(ec_server* sv) {
   cudaSetDevice(sv->device);
+  auto last_active = Clock::now();
   for (;;) {
     bool worked = false;
     for (Slot& sl : sv->slots) {
@@ -224,6 +228,18 @@ void scheduler(ec_server* sv) {
       else if (!free_slot_p) free_slot_p = &sl;
     }
     std::vector<Req> take;
+    const bool has_pending = sv->n_pending.load(std::memory_order_acquire) > 0;
+    const bool stopping = sv->stop.load(std::memory_order_acquire);
+    const bool can_launch = free_slot_p && has_pending;
+    const bool may_sleep = !worked && busy == 0 && Clock::now() - last_active >= sv->idle_spin;
+    if (!can_launch && !stopping && !may_sleep) {
+      // nothing to launch: poll the slots and the queue again without
+      // taking the lock, so that submitters never wait for the scheduler
+      // and a request that arrives while idle starts without a wake-up
+      if (worked || busy > 0) last_active = Clock::now();
+      if (!worked) std::this_thread::yield();
+      continue;
+    }
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       sv->stats.slots_busy = busy;
@@ -232,8 +248,11 @@ void scheduler(ec_server* sv) {
         while (!sv->pending.empty() && static_cast<int>(take.size()) < sv->max_batch) {
           take.push_back(std::move(sv->pending.front()));
           sv->pending.pop_front();
+          sv->n_pending.fetch_sub(1, std::memory_order_relaxed);
         }
       } else if (!worked && busy == 0) {
+        // idle for longer than the polling window: sleep until a
+        // submission notifies
         sv->cv.wait_for(lk, std::chrono::microseconds(200));
         continue;
       }
@@ -251,6 +270,7 @@ void scheduler(ec_server* sv) {
       }
       worked = true;
     }
+    if (worked || busy > 0) last_active = Clock::now();
     if (!worked) std::this_thread::yield();
   }
 }
@@ -271,6 +291,8 @@ ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
   sv->budget = opts && opts->hbm_budget ? opts->hbm_budget : (static_cast<size_t>(32) << 30);
   sv->max_batch = opts && opts->max_batch > 0 ? opts->max_batch : 512;
   const int n_slots = opts && opts->slots > 0 ? opts->slots : 4;
+  if (opts && opts->idle_spin_us != 0)
+    sv->idle_spin = std::chrono::microseconds(std::max(0, opts->idle_spin_us));
   sv->chunk = std::max(1, env_int("EC_BATCH_CHUNK", 2));
   sv->slots.resize(n_slots);
   for (Slot& sl : sv->slots) {
@@ -360,6 +382,7 @@ ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
   sv->admitted += r.bytes;
   sv->stats.submitted += 1;
   sv->pending.push_back(std::move(r));
+  sv->n_pending.fetch_add(1, std::memory_order_release);
   sv->cv.notify_one();
   return EC_OK;
 }
