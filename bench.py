@@ -164,31 +164,65 @@ class ClockSampler:
 
 # ------------------------------------------------------------ cpu baseline
 
-def oracle_sample_gbs(n_threads: int, stripes_per_thread: int = 1):
-    """Time the oracle encode of whole C2 stripes on host threads."""
+def oracle_sample_gbs(n_threads: int, stripes_per_thread: int = 1, decode: bool = False):
+    """Time the oracle on whole stripes of the headline workloads on host
+    threads: encode of C2 stripes (10 x 1 MiB), or decode of C3-shaped
+    stripes (10 x 1 MiB survivors, 4 erasures, one pattern per stripe)."""
     import oracle
     from paper_2108_02692_gb300 import synth
 
     P = oracle.cauchy(K_DATA, M_PAR)
     n = n_threads * stripes_per_thread
-    inputs = [[synth.block_bytes(CONFIG_ID, s, j, BLOCK) for j in range(K_DATA)]
-              for s in range(n)]
+    if decode:
+        pats = [p for p in synth.decode_patterns(K_DATA, M_PAR, 4 * n) if len(p) == M_PAR][:n]
+        work = []
+        for s, er in enumerate(pats):
+            avail = [None if i in er else synth.block_bytes(DECODE_CONFIG_ID, s, i, BLOCK)
+                     for i in range(K_DATA + M_PAR)]
+            work.append((list(er), avail))
+        fn = lambda w: oracle.decode(P, w[0], w[1])
+    else:
+        work = [[synth.block_bytes(CONFIG_ID, s, j, BLOCK) for j in range(K_DATA)]
+                for s in range(n)]
+        fn = lambda d: oracle.encode(P, d)
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=n_threads) as ex:
-        list(ex.map(lambda d: oracle.encode(P, d), inputs))
+        list(ex.map(fn, work))
     dt = time.perf_counter() - t0
     return n * K_DATA * BLOCK / dt / 1e9, dt, n
 
 
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline_obj():
+    """The oracle on this host: encode over all cores (the reported value),
+    encode on one core, and decode over all cores."""
     cores = os.cpu_count() or 1
     gbs, dt, n = oracle_sample_gbs(cores, 1)
+    g1, dt1, _ = oracle_sample_gbs(1, 1)
+    gd, dtd, nd = oracle_sample_gbs(cores, 1, decode=True)
     return {"value": round(gbs, 5), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} of the 256 stripes (10 x 1 MiB each), one per host thread, "
-                      f"{dt:.2f} s wall"}
+            "sample": f"encode of {n} of the 256 stripes (10 x 1 MiB each), one per host thread, "
+                      f"{dt:.2f} s wall",
+            "cpu_model": cpu_model(),
+            "single_thread": {"value": round(g1, 5), "unit": "GB/s",
+                              "sample": f"encode of 1 stripe on 1 thread, {dt1:.2f} s"},
+            "decode": {"value": round(gd, 5), "unit": "GB/s",
+                       "sample": f"decode of {nd} stripes (10 x 1 MiB survivors, 4 erasures), one "
+                                 f"per host thread, {dtd:.2f} s wall"}}
 
-
-# --------------------------------------------------------- traffic (ncu)
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
