@@ -323,6 +323,13 @@ typedef struct {
                             this long before it sleeps on a condition variable
                             (0 = 1000 us; < 0 = sleep at once).  Polling costs
                             one host core and spares each request the wake-up */
+  int no_background_compile; /* nonzero: a request whose program has no compiled
+                            kernel always runs on the interpreter.  Default:
+                            it runs on the interpreter while a background
+                            thread compiles the program, and later requests
+                            use the compiled kernel.  Plans used with a server
+                            must then stay alive until ec_server_destroy
+                            returns                                            */
 } ec_server_opts;
 
 typedef struct {
@@ -332,6 +339,7 @@ typedef struct {
   long long admitted_bytes;        /* currently admitted                             */
   long long pending;               /* admitted, not yet launched                     */
   int slots_busy;
+  long long compiled_in_background; /* programs compiled by the background thread   */
 } ec_server_stats;
 
 ec_status ec_server_create(const ec_server_opts *opts, ec_server **out);

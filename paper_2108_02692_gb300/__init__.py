@@ -256,9 +256,9 @@ def ec_plan_compile(plan: int, sets=None, n_threads: int = 0) -> None:
 
 
 def ec_server_create(hbm_budget: int = 0, max_batch: int = 0, slots: int = 0,
-                     idle_spin_us: int = 0) -> int:
+                     idle_spin_us: int = 0, background_compile: bool = True) -> int:
     h = ctypes.c_void_p()
-    opts = _abi.ServerOpts(hbm_budget, max_batch, slots, idle_spin_us)
+    opts = _abi.ServerOpts(hbm_budget, max_batch, slots, idle_spin_us, 0 if background_compile else 1)
     _check(lib().ec_server_create(ctypes.byref(opts), ctypes.byref(h)))
     return h.value
 

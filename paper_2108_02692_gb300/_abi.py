@@ -68,13 +68,14 @@ class BatchInfo(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", c_size), ("max_batch", c_int), ("slots", c_int),
-                ("idle_spin_us", c_int)]
+                ("idle_spin_us", c_int), ("no_background_compile", c_int)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_longlong) for n in
                 ("submitted", "completed", "rejected", "failed", "batches", "max_batch_seen",
-                 "bytes_in", "bytes_out", "admitted_bytes", "pending")] + [("slots_busy", c_int)]
+                 "bytes_in", "bytes_out", "admitted_bytes", "pending")] + [
+        ("slots_busy", c_int), ("compiled_in_background", ctypes.c_longlong)]
 
 
 class TuneResult(ctypes.Structure):

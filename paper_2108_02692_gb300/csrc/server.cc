@@ -23,6 +23,7 @@
 #include <deque>
 #include <map>
 #include <thread>
+#include <unordered_set>
 #include <tuple>
 #include <vector>
 
@@ -84,6 +85,14 @@ struct ec_server {
   std::thread th;
   ec_server_stats stats{};
   std::map<std::tuple<void*, int, int>, std::pair<size_t, int>> shapes;
+  // background compilation of programs that arrive without a compiled module
+  bool background_compile = true;
+  std::thread compiler;
+  std::mutex cmu;
+  std::condition_variable ccv;
+  std::vector<std::pair<ec_plan*, Program*>> to_compile;
+  std::unordered_set<Program*> queued;
+  bool cstop = false;
 };
 
 namespace {
@@ -275,6 +284,34 @@ void scheduler(ec_server* sv) {
   }
 }
 
+// Compiles, in the background, the programs that requests found without a
+// compiled module; the interpreter runs them meanwhile.  New programs that
+// arrive together are compiled into shared modules.
+void compiler_loop(ec_server* sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    std::vector<std::pair<ec_plan*, Program*>> want;
+    {
+      std::unique_lock<std::mutex> lk(sv->cmu);
+      sv->ccv.wait(lk, [&] { return sv->cstop || !sv->to_compile.empty(); });
+      if (sv->cstop) return;
+      // a short gathering window, so that a burst of new patterns shares
+      // one module compile
+      sv->ccv.wait_for(lk, std::chrono::milliseconds(5), [&] { return sv->cstop; });
+      if (sv->cstop) return;
+      want.swap(sv->to_compile);
+    }
+    xorec::compile_modules(want, false, nullptr);
+    long long n = 0;
+    for (auto& w : want) {
+      std::lock_guard<std::mutex> lk(w.first->mu);
+      if (w.second->mod) ++n;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stats.compiled_in_background += n;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -294,6 +331,7 @@ ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
   if (opts && opts->idle_spin_us != 0)
     sv->idle_spin = std::chrono::microseconds(std::max(0, opts->idle_spin_us));
   sv->chunk = std::max(1, env_int("EC_BATCH_CHUNK", 2));
+  sv->background_compile = !(opts && opts->no_background_compile) && xorec::jit_available();
   sv->slots.resize(n_slots);
   for (Slot& sl : sv->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -309,6 +347,7 @@ ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
     }
   }
   sv->th = std::thread(scheduler, sv);
+  if (sv->background_compile) sv->compiler = std::thread(compiler_loop, sv);
   *out = sv;
   return EC_OK;
 }
@@ -362,6 +401,13 @@ ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
     std::lock_guard<std::mutex> lk(job->plan->mu);
     r.mod = r.prog->mod;
     if (!r.mod && !xorec::ensure_device_code(r.prog)) return EC_ECUDA;
+  }
+  if (!r.mod && sv->background_compile) {
+    std::lock_guard<std::mutex> lk(sv->cmu);
+    if (sv->queued.insert(r.prog).second) {
+      sv->to_compile.emplace_back(job->plan, r.prog);
+      sv->ccv.notify_one();
+    }
   }
   const size_t B = job->block_bytes;
   const int th = xorec::launch_threads(r.mod);
@@ -418,6 +464,12 @@ void ec_server_destroy(ec_server* sv) {
     sv->cv.notify_one();
   }
   if (sv->th.joinable()) sv->th.join();
+  {
+    std::lock_guard<std::mutex> lk(sv->cmu);
+    sv->cstop = true;
+    sv->ccv.notify_one();
+  }
+  if (sv->compiler.joinable()) sv->compiler.join();
   for (Slot& s : sv->slots) free_slot(s);
   delete sv;
 }

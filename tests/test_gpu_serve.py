@@ -131,3 +131,48 @@ def test_warm_compiles_every_pattern(plans):
                 assert np.array_equal(t.cpu().numpy(), e)
     finally:
         xo.ec_server_destroy(server)
+
+
+@pytest.mark.parametrize("background", [True, False], ids=["background", "interp-only"])
+def test_new_patterns_run_then_get_compiled(background):
+    """Requests whose decode programs were never compiled run on the
+    interpreter at once; with background compilation the programs then get
+    compiled kernels and later requests use them.  Bit-exact throughout."""
+    import itertools
+    k, m, B = 6, 3, 8 * 1552
+    plan = xo.ec_plan_create(k, m)      # fresh: no compiled module yet
+    server = xo.ec_server_create(background_compile=background)
+    try:
+        P = oracle.cauchy(k, m)
+        data = [synth.block_bytes(53, 0, j, B) for j in range(k)]
+        blocks = data + oracle.encode(P, data)
+        d = [torch.from_numpy(x).cuda() for x in blocks]
+        pats = [list(e) for e in itertools.combinations(range(k + m), 2)][:12]
+        outs = [[torch.full((B,), 0xAB, dtype=torch.uint8, device="cuda") for _ in er]
+                for er in pats]
+        jobs = [{"plan": plan, "op": xo.EC_OP_DECODE, "erasures": er,
+                 "blocks": [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                 "out": [t.data_ptr() for t in o], "block_bytes": B}
+                for er, o in zip(pats, outs)]
+        arr, keep = xo.make_jobs(jobs)
+
+        def run_and_check():
+            tickets = [xo.ec_server_submit_raw(server, arr[i]) for i in range(len(jobs))]
+            wait_all(server, tickets)
+            for er, o in zip(pats, outs):
+                for t, e in zip(o, er):
+                    assert np.array_equal(t.cpu().numpy(), blocks[e])
+                    t.fill_(0xAB)
+            torch.cuda.synchronize()
+
+        run_and_check()
+        t0 = time.time()
+        while background and xo.ec_server_stats_get(server)["compiled_in_background"] < len(pats):
+            assert time.time() - t0 < 120, "background compilation did not finish"
+            time.sleep(0.05)
+        run_and_check()
+        n = xo.ec_server_stats_get(server)["compiled_in_background"]
+        assert n == (len(pats) if background else 0)
+    finally:
+        xo.ec_server_destroy(server)
+        xo.ec_plan_destroy(plan)
