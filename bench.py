@@ -57,7 +57,7 @@ def parse_args():
                          "1000 us, -1 = sleep at once)")
     ap.add_argument("--batched-stripes", type=int, default=8192)
     ap.add_argument("--executor", default="auto", choices=["auto", "interp", "compiled"])
-    ap.add_argument("--opt", default="xorrepair", choices=["raw", "repair", "xorrepair"],
+    ap.add_argument("--opt", default="xorrepair", choices=["raw", "repair", "xorrepair", "triple"],
                     help="optimiser level of the encoding program")
     ap.add_argument("--max-temps", type=int, default=-2,
                     help="RePair temporaries budget (-1 = unlimited, -2 = automatic)")
@@ -276,7 +276,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     opt = {"raw": xo.EC_OPT_RAW, "repair": xo.EC_OPT_REPAIR,
-           "xorrepair": xo.EC_OPT_XORREPAIR}[args.opt]
+           "xorrepair": xo.EC_OPT_XORREPAIR, "triple": xo.EC_OPT_TRIPLE}[args.opt]
     plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, args.matrix), executor=executor,
                                 opt_level=opt, max_temps=args.max_temps)
     data = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")

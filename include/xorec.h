@@ -71,7 +71,11 @@ enum {
 enum {
   EC_OPT_RAW = 0,       /* one fused statement per bitmatrix row              */
   EC_OPT_REPAIR = 1,    /* RePair (Sec. 4.3)                                  */
-  EC_OPT_XORREPAIR = 2  /* XorRePair (Sec. 4.4), the default                  */
+  EC_OPT_XORREPAIR = 2, /* XorRePair (Sec. 4.4), the default                  */
+  EC_OPT_TRIPLE = 3     /* RePair's greedy compression with triples of terms
+                           (one three-input XOR instruction each) in place of
+                           pairs; codes too wide to enumerate triples use
+                           XorRePair                                          */
 };
 
 /* Pebble-game scheduler (Sec. 6.6). */
@@ -136,6 +140,8 @@ typedef struct {
   int max_live;         /* values live at once with inputs preloaded          */
   int threads;          /* threads per CTA of the compiled tier (strip tile =
                            4 x threads bytes): the plan's launch shape        */
+  int lop3;             /* three-input XOR instructions of the fused program:
+                           sum over statements of ceil((arity - 1) / 2)       */
 } ec_program_info;
 
 /* Program of the encoder (erasures == NULL) or of the decoder for the given

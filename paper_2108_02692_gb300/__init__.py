@@ -31,6 +31,7 @@ EC_MATRIX_CAUCHY_MIN = _abi.EC_MATRIX_CAUCHY_MIN
 EC_OPT_RAW = _abi.EC_OPT_RAW
 EC_OPT_REPAIR = _abi.EC_OPT_REPAIR
 EC_OPT_XORREPAIR = _abi.EC_OPT_XORREPAIR
+EC_OPT_TRIPLE = _abi.EC_OPT_TRIPLE
 EC_SCHED_DFS = _abi.EC_SCHED_DFS
 EC_SCHED_GREEDY = _abi.EC_SCHED_GREEDY
 EC_EXEC_AUTO = _abi.EC_EXEC_AUTO
@@ -124,7 +125,8 @@ def ec_plan_info(plan: int, erasures=None) -> dict:
             "code_words": info.code_words, "sched_nvar": info.sched_nvar,
             "raw": _stats(info.raw), "compressed": _stats(info.compressed),
             "fused": _stats(info.fused), "compiled": bool(info.compiled), "regs": info.regs,
-            "temps": info.temps, "max_live": info.max_live, "threads": info.threads}
+            "temps": info.temps, "max_live": info.max_live, "threads": info.threads,
+            "lop3": info.lop3}
 
 
 def ec_plan_program(plan: int, erasures=None) -> np.ndarray:

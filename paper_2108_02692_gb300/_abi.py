@@ -30,7 +30,7 @@ EC_EBUSY = -7
 EC_ENOTSUP = -8
 
 EC_MATRIX_CAUCHY, EC_MATRIX_POWER, EC_MATRIX_USER, EC_MATRIX_CAUCHY_MIN = 0, 1, 2, 3
-EC_OPT_RAW, EC_OPT_REPAIR, EC_OPT_XORREPAIR = 0, 1, 2
+EC_OPT_RAW, EC_OPT_REPAIR, EC_OPT_XORREPAIR, EC_OPT_TRIPLE = 0, 1, 2, 3
 EC_SCHED_DFS, EC_SCHED_GREEDY = 0, 1
 EC_EXEC_AUTO, EC_EXEC_INTERP, EC_EXEC_COMPILED = 0, 1, 2
 
@@ -48,7 +48,7 @@ class ProgramInfo(ctypes.Structure):
     _fields_ = [("n_in", c_int), ("n_out", c_int), ("slots", c_int), ("stmts", c_int),
                 ("code_words", c_int), ("sched_nvar", c_int), ("raw", SlpStats),
                 ("compressed", SlpStats), ("fused", SlpStats), ("compiled", c_int),
-                ("regs", c_int), ("temps", c_int), ("max_live", c_int), ("threads", c_int)]
+                ("regs", c_int), ("temps", c_int), ("max_live", c_int), ("threads", c_int), ("lop3", c_int)]
 
 
 EC_OP_ENCODE, EC_OP_DECODE = 0, 1

@@ -322,7 +322,7 @@ ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix
     default: return fail(EC_EINVAL, "unknown matrix kind");
   }
   if (opts) {
-    if (opts->opt_level < EC_OPT_RAW || opts->opt_level > EC_OPT_XORREPAIR)
+    if (opts->opt_level < EC_OPT_RAW || opts->opt_level > EC_OPT_TRIPLE)
       return fail(EC_EINVAL, "bad opt_level");
     if (opts->sched != EC_SCHED_DFS && opts->sched != EC_SCHED_GREEDY)
       return fail(EC_EINVAL, "bad sched");
@@ -412,6 +412,7 @@ ec_status ec_plan_info(ec_plan* plan, const int* erasures, int n_erasures, ec_pr
   out->temps = p->stats.temps;
   out->max_live = p->stats.max_live;
   out->threads = p->threads > 0 ? p->threads : xorec::env_int("EC_JIT_THREADS", 128);
+  out->lop3 = static_cast<int>(p->stats.lop3);
   return EC_OK;
 }
 

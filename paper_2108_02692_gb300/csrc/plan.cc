@@ -1,6 +1,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <memory>
 
 #include "gf.h"
 
@@ -105,14 +106,27 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
     fused = slp_rows_fused(n_in, R, order);
     p.stats.compressed = p.stats.raw;
   } else {
-    RepairTrace tr(chains, o.opt_level == kOptXorRePair);
-    int b = tr.n_temps();
+    // compression trace: (Xor)RePair pairs, or triples when enumerating the
+    // rows' triples stays small
+    long triples = 0;
+    for (const auto& r : R) {
+      const long n = r.count();
+      triples += n * (n - 1) * (n - 2) / 6;
+    }
+    const bool use_triples = o.opt_level == kOptTriple && triples <= 8000000;
+    std::unique_ptr<RepairTrace> rt;
+    std::unique_ptr<TripleTrace> tt;
+    if (use_triples) tt = std::make_unique<TripleTrace>(chains);
+    else rt = std::make_unique<RepairTrace>(chains, o.opt_level != kOptRePair);
+    auto at = [&](int x) { return use_triples ? tt->at(x) : rt->at(x); };
+    int b = use_triples ? tt->n_temps() : rt->n_temps();
+    const int all = b;
     if (o.max_temps >= 0) {
-      b = std::min(o.max_temps, tr.n_temps());
+      b = std::min(o.max_temps, all);
     } else if (o.max_temps == -2) {
       // largest budget whose DFS schedule fits the register budget
       auto live_at = [&](int x) {
-        Slp f = fuse(tr.at(x), o.cancel_pairs);
+        Slp f = fuse(at(x), o.cancel_pairs);
         return max_live_preloaded(f, schedule_dfs(f, false));
       };
       if (live_at(b) > o.reg_budget) {
@@ -124,12 +138,13 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
         b = lo;
       }
     }
-    Slp co = tr.at(b);
+    Slp co = at(b);
     p.stats.temps = b;
     p.stats.compressed = metrics(co);
     fused = fuse(co, o.cancel_pairs);
   }
   p.stats.fused = metrics(fused);
+  p.stats.lop3 = lop3_count(fused);
   if (!equivalent(chains, fused)) {
     *err = "internal: optimised program is not equivalent to the bitmatrix";
     return false;

@@ -16,7 +16,7 @@ namespace xorec {
 // bit s of A[i][j] * 2^t (Sec. 1, property (ii)).
 std::vector<Bits> bitmatrix_rows(int rows, int cols, const uint8_t* A);
 
-enum OptLevel { kOptRaw = 0, kOptRePair = 1, kOptXorRePair = 2 };
+enum OptLevel { kOptRaw = 0, kOptRePair = 1, kOptXorRePair = 2, kOptTriple = 3 };
 enum SchedKind { kSchedDfs = 0, kSchedGreedy = 1 };
 
 struct PipelineStats {
@@ -26,6 +26,7 @@ struct PipelineStats {
   int slots = 0;           // pebbles when outputs stream out (GPU setting)
   int temps = 0;           // temporaries kept by (Xor)RePair
   int max_live = 0;        // registers with all inputs preloaded
+  long lop3 = 0;           // three-input XOR instructions of the fused program
 };
 
 // An executable program for one linear map from n_in input strips to n_out

@@ -4,6 +4,7 @@
 #include <functional>
 #include <list>
 #include <map>
+#include <queue>
 #include <sstream>
 #include <unordered_map>
 
@@ -489,6 +490,152 @@ Slp RepairTrace::at(int b) const {
     out.ret[o] = v;
   }
   return out;
+}
+
+// ------------------------------------------------------ triple compression
+
+namespace {
+
+// Triple key of terms x < y < z (each below 2^21).
+uint64_t triple_key(int x, int y, int z) {
+  return (static_cast<uint64_t>(x) << 42) | (static_cast<uint64_t>(y) << 21) |
+         static_cast<uint64_t>(z);
+}
+
+}  // namespace
+
+TripleTrace::TripleTrace(const Slp& in) : nc_(in.n_const), const_names_(in.const_names) {
+  const int nc = nc_;
+  const std::vector<Bits> goal = semantics(in);
+  n_orig_ = static_cast<int>(goal.size());
+  std::vector<std::vector<int>> def(n_orig_);
+  for (int o = 0; o < n_orig_; ++o)
+    for (int c = 0; c < nc; ++c)
+      if (goal[o].test(c)) def[o].push_back(c);
+  init_ = def;
+
+  // count[key] = originals containing the triple; a lazy max-heap of
+  // (count, -key) finds the most frequent (stale entries are skipped)
+  std::unordered_map<uint64_t, int> count;
+  std::priority_queue<std::pair<int, int64_t>> heap;
+  auto bump = [&](int x, int y, int z, int d) {
+    const uint64_t k = triple_key(x, y, z);
+    int& c = count[k];
+    c += d;
+    if (d > 0 && c >= 2) heap.emplace(c, -static_cast<int64_t>(k));
+  };
+  // the triples of sorted row r that contain its term t
+  auto touch = [&](const std::vector<int>& r, int t, int d) {
+    const int n = static_cast<int>(r.size());
+    for (int i = 0; i < n; ++i) {
+      if (r[i] == t) continue;
+      for (int j = i + 1; j < n; ++j) {
+        if (r[j] == t) continue;
+        int v[3] = {r[i], r[j], t};
+        std::sort(v, v + 3);
+        bump(v[0], v[1], v[2], d);
+      }
+    }
+  };
+  for (const auto& r : def) {
+    const int n = static_cast<int>(r.size());
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j)
+        for (int k = j + 1; k < n; ++k) bump(r[i], r[j], r[k], 1);
+  }
+  for (;;) {
+    int best = 0;
+    uint64_t key = 0;
+    while (!heap.empty()) {
+      const auto top = heap.top();
+      const uint64_t k = static_cast<uint64_t>(-top.second);
+      auto it = count.find(k);
+      if (it == count.end() || it->second != top.first) {
+        heap.pop();
+        continue;
+      }
+      best = top.first;
+      key = k;
+      break;
+    }
+    if (best < 2) break;
+    const int x = static_cast<int>(key >> 42), y = static_cast<int>((key >> 21) & 0x1fffff),
+              z = static_cast<int>(key & 0x1fffff);
+    const int t = nc + static_cast<int>(tdef_.size());
+    if (t >= (1 << 21)) break;   // term ids must fit the key
+    tdef_.push_back({x, y, z});
+    for (auto& r : def) {
+      if (!std::binary_search(r.begin(), r.end(), x) || !std::binary_search(r.begin(), r.end(), y) ||
+          !std::binary_search(r.begin(), r.end(), z))
+        continue;
+      // drop the triples through x, y or z (each once), then the three terms
+      std::vector<int> rest;
+      for (int v : r)
+        if (v != x && v != y && v != z) rest.push_back(v);
+      touch(r, x, -1);
+      {
+        std::vector<int> r2;
+        for (int v : r)
+          if (v != x) r2.push_back(v);
+        touch(r2, y, -1);
+        std::vector<int> r3;
+        for (int v : r2)
+          if (v != y) r3.push_back(v);
+        touch(r3, z, -1);
+      }
+      // add the temporal (it is larger than every term so far)
+      rest.push_back(t);
+      touch(rest, t, 1);
+      r.swap(rest);
+    }
+  }
+}
+
+Slp TripleTrace::at(int b) const {
+  const int nc = nc_;
+  const int T = std::max(0, std::min(b, n_temps()));
+  std::vector<std::vector<int>> def = init_;
+  for (int i = 0; i < T; ++i) {
+    const auto& td = tdef_[i];
+    for (auto& r : def) {
+      if (!std::binary_search(r.begin(), r.end(), td[0]) ||
+          !std::binary_search(r.begin(), r.end(), td[1]) ||
+          !std::binary_search(r.begin(), r.end(), td[2]))
+        continue;
+      std::vector<int> rest;
+      for (int v : r)
+        if (v != td[0] && v != td[1] && v != td[2]) rest.push_back(v);
+      rest.push_back(nc + i);
+      r.swap(rest);
+    }
+  }
+  Slp out;
+  out.n_const = nc;
+  out.const_names = const_names_;
+  out.n_var = T;
+  for (int i = 0; i < T; ++i) {
+    out.body.push_back(Stmt{nc + i, tdef_[i]});
+    out.var_names.push_back("t" + std::to_string(i + 1));
+  }
+  out.ret.resize(n_orig_);
+  for (int o = 0; o < n_orig_; ++o) {
+    if (def[o].size() <= 1) {
+      out.ret[o] = def[o].empty() ? -1 : def[o][0];
+      continue;
+    }
+    const int v = nc + out.n_var++;
+    out.var_names.push_back("o" + std::to_string(o));
+    out.body.push_back(Stmt{v, def[o]});
+    out.ret[o] = v;
+  }
+  return out;
+}
+
+long lop3_count(const Slp& p) {
+  long n = 0;
+  for (const auto& s : p.body)
+    if (s.args.size() >= 2) n += static_cast<long>(s.args.size()) / 2;
+  return n;
 }
 
 Slp repair(const Slp& in, bool xor_cancel, int max_temps) {

@@ -111,6 +111,33 @@ class RepairTrace {
   std::vector<std::vector<std::pair<int, std::vector<int>>>> changes_;  // per iteration
 };
 
+// Triple compression: the RePair idea (Sec. 4.3) with triples of terms in
+// place of pairs, for an executor whose XOR instruction takes three inputs
+// (LOP3): a statement of n arguments costs ceil((n-1)/2) instructions, so a
+// temporal t = a + b + c costs one instruction and removes one from every
+// definition it replaces, where a pair temporal removes one argument
+// (half an instruction on average).  Each iteration replaces the most
+// frequent triple (ties: the smallest triple of term ids; terms are
+// constants, then temporals in creation order) in every original that
+// contains it, while some triple occurs at least twice.  Like RepairTrace,
+// budget b is the first b iterations of one run.
+class TripleTrace {
+ public:
+  explicit TripleTrace(const Slp& p);
+  int n_temps() const { return static_cast<int>(tdef_.size()); }
+  Slp at(int b) const;
+
+ private:
+  int nc_ = 0, n_orig_ = 0;
+  std::vector<std::string> const_names_;
+  std::vector<std::vector<int>> init_;        // initial definitions (sorted constants)
+  std::vector<std::vector<int>> tdef_;        // temporal i = XOR of three terms
+};
+
+// Instructions of a fused program on a three-input XOR unit:
+// sum over statements of ceil((arity - 1) / 2).
+long lop3_count(const Slp& p);
+
 // XOR fusion: repeatedly unfold variables used exactly once into their
 // user; dead variables are dropped.  cancel_pairs removes arguments that
 // occur twice in one fused statement (x + x = 0).  Requires single

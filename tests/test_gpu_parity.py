@@ -90,7 +90,8 @@ def test_encode_matches_oracle(k, m, B, executor):
 
 
 @pytest.mark.parametrize("executor", EXECS, ids=EXEC_IDS)
-@pytest.mark.parametrize("opt", [xo.EC_OPT_RAW, xo.EC_OPT_REPAIR, xo.EC_OPT_XORREPAIR])
+@pytest.mark.parametrize("opt", [xo.EC_OPT_RAW, xo.EC_OPT_REPAIR, xo.EC_OPT_XORREPAIR,
+                                 xo.EC_OPT_TRIPLE])
 def test_encode_opt_levels_and_matrices(opt, executor):
     k, m, B = 10, 4, 8 * 2064
     for kind, P in [(xo.EC_MATRIX_CAUCHY, oracle.cauchy(k, m)),

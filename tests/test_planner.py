@@ -8,6 +8,7 @@ import pytest
 
 import paper_2108_02692_gb300 as xo
 import oracle
+from paper_2108_02692_gb300 import synth
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 EX = json.load(open(os.path.join(GOLD, "slp_examples.json")))
@@ -343,6 +344,54 @@ def test_plan_cauchy_min_rs10_4_fewer_xors():
     finally:
         xo.ec_plan_destroy(plain)
         xo.ec_plan_destroy(scaled)
+
+
+@pytest.mark.parametrize("k,m", [(4, 2), (10, 4), (12, 4)])
+def test_triple_compression_budgets(k, m):
+    # every budget is a prefix of one greedy run; each plan is checked for
+    # equivalence with the bitmatrix when it is built, and decoders too
+    full = xo.ec_plan_create_ex(k, m, opt_level=xo.EC_OPT_TRIPLE, max_temps=-1)
+    raw = xo.ec_plan_create_ex(k, m, opt_level=xo.EC_OPT_RAW)
+    try:
+        n = xo.ec_plan_info(full)["temps"]
+        assert n > 0
+        assert xo.ec_plan_info(full)["lop3"] < xo.ec_plan_info(raw)["lop3"]
+        for b in sorted({0, 1, n // 3, n // 2, n - 1, n, n + 5}):
+            h = xo.ec_plan_create_ex(k, m, opt_level=xo.EC_OPT_TRIPLE, max_temps=b)
+            try:
+                assert xo.ec_plan_info(h)["temps"] == min(b, n)
+                xo.ec_plan_info(h, [0, k])          # a decoder builds and checks too
+            finally:
+                xo.ec_plan_destroy(h)
+        # programs run on a stream emulator match the oracle
+        P = oracle.cauchy(k, m)
+        B = 8 * 64
+        data = [synth.block_bytes(91, 0, j, B) for j in range(k)]
+        ref = oracle.encode(P, data)
+        code = xo.ec_plan_program(full)
+        got = _unstrip(emulate_stream(code, 8 * k, 8 * m, _strips(data)), m)
+        for i in range(m):
+            assert np.array_equal(got[i], ref[i])
+    finally:
+        xo.ec_plan_destroy(full)
+        xo.ec_plan_destroy(raw)
+
+
+def test_lop3_count_of_known_programs():
+    # RS(10,4) Cauchy under the default register budget: 81 statements of
+    # which 49 binary temporaries; 419 three-input instructions
+    plan = xo.ec_plan_create(10, 4)
+    try:
+        info = xo.ec_plan_info(plan)
+        code = xo.ec_plan_program(plan)
+        pc, lop3 = 0, 0
+        while pc < len(code):
+            na, w1 = int(code[pc]), int(code[pc + 1])
+            pc += 2 + (1 if w1 & 0x8000 else 0) + (w1 & 0x7fff) + na
+            lop3 += na // 2 if na >= 2 else 0
+        assert info["lop3"] == lop3 == 419
+    finally:
+        xo.ec_plan_destroy(plan)
 
 
 def test_set_launch_shape_host_side():
