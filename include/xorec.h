@@ -373,6 +373,21 @@ ec_status ec_device_status(int *status, int reset);
  * no counterpart; this checks the failure path without faulting the GPU. */
 ec_status ec_selftest_wait_timeout(void *stream);
 
+/* Host check of an interpreter instruction stream (the format of
+ * ec_plan_program): every statement well formed, operand ids below
+ * n_in + n_slots, slots written before they are read, output strip ids
+ * below n_out.  EC_OK, or EC_EINVAL with the first problem and its word
+ * offset in ec_last_error.  The planner runs the same check on every
+ * program it builds. */
+ec_status ec_program_check(const uint16_t *code, size_t len, int n_in, int n_out, int n_slots);
+
+/* Fault injection for tests: the n-th device or pinned-host allocation
+ * made by the library from now on fails as if memory ran out (the call
+ * that makes it returns EC_ENOMEM after freeing what it had allocated);
+ * n = 0 clears it.  No GPU fault is involved.  The paper has no
+ * counterpart. */
+ec_status ec_debug_fail_alloc(int n);
+
 /* Thread-local message of the last failure ("" if none). */
 const char *ec_last_error(void);
 

@@ -147,6 +147,17 @@ def ec_plan_autotune(plan: int, block_bytes: int, n_stripes: int = 16, stream: i
     return {f: getattr(r, f) for f, _ in _abi.TuneResult._fields_}
 
 
+def ec_program_check(code, n_in: int, n_out: int, n_slots: int) -> None:
+    """Raise XorecError (EC_EINVAL) unless the instruction stream is well formed."""
+    arr = np.ascontiguousarray(code, dtype=np.uint16)
+    _check(lib().ec_program_check(arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), arr.size,
+                                  n_in, n_out, n_slots))
+
+
+def ec_debug_fail_alloc(n: int) -> None:
+    _check(lib().ec_debug_fail_alloc(n))
+
+
 def ec_plan_set_launch(plan: int, threads: int, reg_budget: int) -> None:
     _check(lib().ec_plan_set_launch(plan, threads, reg_budget))
 

@@ -104,6 +104,8 @@ SIGNATURES = {
     "ec_plan_compile": (c_int, [c_vp, intp, intp, c_int, c_int]),
     "ec_plan_autotune": (c_int, [c_vp, c_size, c_int, c_vp, ctypes.POINTER(TuneResult)]),
     "ec_plan_set_launch": (c_int, [c_vp, c_int, c_int]),
+    "ec_program_check": (c_int, [ctypes.POINTER(ctypes.c_uint16), c_size, c_int, c_int, c_int]),
+    "ec_debug_fail_alloc": (c_int, [c_int]),
     "ec_plan_set_executor": (c_int, [c_vp, c_int]),
     "ec_batch_create": (c_int, [ctypes.POINTER(Job), c_int, c_int, ctypes.POINTER(c_vp)]),
     "ec_batch_run": (c_int, [c_vp, c_vp]),

@@ -266,6 +266,7 @@ bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_
 extern "C" {
 
 ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch** out) {
+  xorec::TraceRange trace_("xorec batch create");
   if (!out) return fail(EC_EINVAL, "out is NULL");
   *out = nullptr;
   if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(EC_EINVAL, "bad job list");
@@ -392,9 +393,10 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
 
   // 6. device copies (owned by the batch)
   if (!ents.empty()) {
-    if (cudaMalloc(&b->d_descs, descs.size() * sizeof(xk::StripeDesc)) != cudaSuccess ||
-        cudaMalloc(&b->d_queues, b->launches.size() * sizeof(xk::u64)) != cudaSuccess ||
-        cudaMalloc(&b->d_blocks, std::max<size_t>(1, blocks.size()) * sizeof(xk::u64)) != cudaSuccess) {
+    if (xorec::dev_malloc(&b->d_descs, descs.size() * sizeof(xk::StripeDesc)) != cudaSuccess ||
+        xorec::dev_malloc(&b->d_queues, b->launches.size() * sizeof(xk::u64)) != cudaSuccess ||
+        xorec::dev_malloc(&b->d_blocks, std::max<size_t>(1, blocks.size()) * sizeof(xk::u64)) !=
+            cudaSuccess) {
       cudaGetLastError();
       free_batch(b);
       return fail(EC_ENOMEM, "device allocation of the batch tables failed");
@@ -474,6 +476,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
 }
 
 ec_status ec_batch_run(ec_batch* b, void* stream) {
+  xorec::TraceRange trace_("xorec batch run");
   if (!b) return fail(EC_EINVAL, "NULL batch");
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   if (b->launches.empty()) return EC_OK;

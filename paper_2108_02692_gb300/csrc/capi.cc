@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -19,6 +20,15 @@ namespace xorec {
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+std::atomic<int> g_fail_allocs{0};
+
+bool take_injected_alloc_failure() {
+  int v = g_fail_allocs.load(std::memory_order_relaxed);
+  while (v > 0)
+    if (g_fail_allocs.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 1;
+  return false;
+}
 
 static std::mutex g_dev_mu;
 static DeviceInfo g_dev[64];
@@ -60,7 +70,7 @@ bool ensure_device_code(Program* p) {
   if (p->d_code) return true;
   const size_t bytes = std::max<size_t>(1, p->code.size()) * sizeof(uint16_t);
   uint16_t* d = nullptr;
-  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+  if (dev_malloc(&d, bytes) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc of the program failed");
     return false;
@@ -214,7 +224,7 @@ ec_status run_with_table(Program* p, const std::vector<uint64_t>& tab, int n_inb
                          long long n_stripes, size_t B, int executor, cudaStream_t st) {
   const size_t bytes = tab.size() * sizeof(uint64_t);
   void* d = nullptr;
-  if (cudaMallocAsync(&d, bytes, st) != cudaSuccess) {
+  if (xorec::dev_malloc_async(&d, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return fail(EC_ENOMEM, "cudaMallocAsync of the block table failed");
   }
@@ -239,6 +249,7 @@ ec_status run_with_table(Program* p, const std::vector<uint64_t>& tab, int n_inb
 
 // Decode program for a sorted erasure set (built on first use).
 ec_status get_decode_program(ec_plan* plan, const std::vector<int>& er, Program** out) {
+  xorec::TraceRange trace_("xorec plan decoder");
   {
     std::lock_guard<std::mutex> lk(plan->mu);
     auto it = plan->dec.find(er);
@@ -300,10 +311,24 @@ extern "C" {
 
 const char* ec_last_error(void) { return xorec::g_last_error.c_str(); }
 
+ec_status ec_program_check(const uint16_t* code, size_t len, int n_in, int n_out, int n_slots) {
+  if ((!code && len) || n_in < 0 || n_out < 0 || n_slots < 0)
+    return fail(EC_EINVAL, "bad argument");
+  std::string err;
+  if (!xorec::check_program_stream(code, len, n_in, n_out, n_slots, &err)) return fail(EC_EINVAL, err);
+  return EC_OK;
+}
+
+ec_status ec_debug_fail_alloc(int n) {
+  xorec::g_fail_allocs.store(std::max(0, n));
+  return EC_OK;
+}
+
 const char* ec_version(void) { return "xorec 0.1 (sm_103a)"; }
 
 ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix,
                             const ec_plan_opts* opts, ec_plan** out) {
+  xorec::TraceRange trace_("xorec plan create");
   if (!out) return fail(EC_EINVAL, "out is NULL");
   *out = nullptr;
   if (k < 1 || m < 1 || k + m > 256) return fail(EC_EINVAL, "need 1 <= k, 1 <= m, k + m <= 256");
@@ -434,6 +459,7 @@ ec_status ec_plan_program(ec_plan* plan, const int* erasures, int n_erasures, ui
 
 ec_status ec_encode(ec_plan* plan, const uint8_t* const* data, uint8_t* const* parity,
                     size_t block_bytes, void* stream) {
+  xorec::TraceRange trace_("xorec encode");
   if (!plan || !data || !parity) return fail(EC_EINVAL, "NULL argument");
   ec_status s = check_block_bytes(block_bytes);
   if (s != EC_OK) return s;
@@ -454,6 +480,7 @@ ec_status ec_encode_strided(ec_plan* plan, const uint8_t* data, size_t data_stri
                             size_t data_block_stride, uint8_t* parity, size_t par_stripe_stride,
                             size_t par_block_stride, int n_stripes, size_t block_bytes,
                             void* stream) {
+  xorec::TraceRange trace_("xorec encode strided");
   if (!plan || !data || !parity) return fail(EC_EINVAL, "NULL argument");
   if (n_stripes < 0) return fail(EC_EINVAL, "negative stripe count");
   ec_status s = check_block_bytes(block_bytes);
@@ -483,6 +510,7 @@ ec_status ec_encode_strided(ec_plan* plan, const uint8_t* data, size_t data_stri
 ec_status ec_decode(ec_plan* plan, const int* erasures, int n_erasures,
                     const uint8_t* const* blocks, uint8_t* const* out, size_t block_bytes,
                     void* stream) {
+  xorec::TraceRange trace_("xorec decode");
   if (!plan || !blocks || !out) return fail(EC_EINVAL, "NULL argument");
   std::vector<int> er;
   ec_status s = canon_erasures(plan, erasures, n_erasures, &er);

@@ -67,7 +67,7 @@ ec_status ensure_io(ec_plan* plan, size_t bytes, xorec_host_io** out) {
         cudaFree(h->dbuf[i]);
         h->dbuf[i] = nullptr;
       }
-      if (cudaMalloc(&h->dbuf[i], bytes) != cudaSuccess) {
+      if (xorec::dev_malloc(&h->dbuf[i], bytes) != cudaSuccess) {
         cudaGetLastError();
         h->cap = 0;
         return fail(EC_ENOMEM, "device staging allocation failed");
@@ -86,6 +86,7 @@ extern "C" ec_status ec_encode_host_strided(ec_plan* plan, const uint8_t* data,
                                             uint8_t* parity, size_t par_stripe_stride,
                                             size_t par_block_stride, int n_stripes,
                                             size_t block_bytes, int chunk_stripes, void* stream) {
+  xorec::TraceRange trace_("xorec encode from host");
   if (!plan || !data || !parity) return fail(EC_EINVAL, "NULL argument");
   if (n_stripes < 0) return fail(EC_EINVAL, "negative stripe count");
   if (block_bytes == 0 || block_bytes % 128 != 0)

@@ -2,6 +2,7 @@
 // tier.  Not part of the public interface.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <map>
@@ -39,6 +40,42 @@ ec_status get_decode_program(ec_plan* plan, const std::vector<int>& er, xorec::P
 namespace xorec {
 
 void set_error(const std::string& msg);
+
+// Device and pinned-host allocations of the library.  ec_debug_fail_alloc
+// makes the n-th one from now fail as if memory ran out (host-side fault
+// injection for the tests; no GPU fault is involved).
+bool take_injected_alloc_failure();
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  if (take_injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t st) {
+  if (take_injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st);
+}
+template <class T>
+cudaError_t host_malloc_pinned(T** p, size_t bytes) {
+  if (take_injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+}
+
+// NVTX range for the duration of a scope (plan, compile, encode, decode,
+// batch and serving steps show up on an nsys or ncu timeline).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
+// Host check of an interpreter stream before it is uploaded or compiled:
+// every statement well formed, operands below n_in + n_slots, slots written
+// before they are read, output strips below n_out.  The format is the one
+// Program documents.
+bool check_program_stream(const uint16_t* code, size_t len, int n_in, int n_out, int n_slots,
+                          std::string* err);
 
 // Per-device state: SM count, status word.
 struct DeviceInfo {

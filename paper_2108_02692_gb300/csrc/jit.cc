@@ -243,6 +243,7 @@ static bool jit_set_smem(JitKernel* jk, size_t smem) {
 // NVRTC: source -> cubin for the current device -> loaded kernel `name`.
 static JitKernel* compile_and_load(const std::string& src, const char* name, int threads,
                                    std::string* err) {
+  xorec::TraceRange trace_("xorec nvrtc compile");
   DeviceInfo di;
   if (!device_info(&di)) {
     *err = "no CUDA device";

@@ -87,6 +87,42 @@ bool lower(const Slp& q, const Schedule& s, int n_in, int n_out, Program* p,
 
 }  // namespace
 
+bool check_program_stream(const uint16_t* code, size_t len, int n_in, int n_out, int n_slots,
+                          std::string* err) {
+  std::vector<char> written(static_cast<size_t>(std::max(0, n_slots)), 0);
+  size_t pc = 0;
+  auto bad = [&](const char* what) {
+    *err = std::string("instruction stream: ") + what + " at word " + std::to_string(pc);
+    return false;
+  };
+  while (pc < len) {
+    if (pc + 2 > len) return bad("truncated statement header");
+    const int na = code[pc];
+    const int w1 = code[pc + 1];
+    const int no = w1 & 0x7fff;
+    const bool has_slot = (w1 & 0x8000) != 0;
+    size_t q = pc + 2;
+    int slot = -1;
+    if (has_slot) {
+      if (q >= len) return bad("truncated slot");
+      slot = code[q++];
+      if (slot >= n_slots) return bad("slot out of range");
+    }
+    if (q + static_cast<size_t>(no) + static_cast<size_t>(na) > len) return bad("truncated statement");
+    for (int o = 0; o < no; ++o)
+      if (code[q + o] >= n_out) return bad("output strip out of range");
+    q += no;
+    for (int a = 0; a < na; ++a) {
+      const int id = code[q + a];
+      if (id >= n_in + n_slots) return bad("operand out of range");
+      if (id >= n_in && !written[id - n_in]) return bad("slot read before it is written");
+    }
+    if (slot >= 0) written[slot] = 1;
+    pc = q + na;
+  }
+  return true;
+}
+
 bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
                    Program* out, std::string* err) {
   const int n_in = 8 * cols, n_out = 8 * rows;
@@ -157,6 +193,8 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   p.stats.slots = gpu.n_pebbles;
   p.stats.max_live = max_live_preloaded(fused, gpu);
   if (!lower(fused, gpu, n_in, n_out, &p, err)) return false;
+  if (!check_program_stream(p.code.data(), p.code.size(), n_in, n_out, p.n_slots, err))
+    return false;
   p.fused = fused;
   p.sched = gpu;
   *out = std::move(p);

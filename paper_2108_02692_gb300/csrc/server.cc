@@ -115,8 +115,8 @@ bool grow_blocks(Slot& s, size_t need) {
   if (s.h_blocks) cudaFreeHost(s.h_blocks);
   s.d_blocks = nullptr;
   s.h_blocks = nullptr;
-  if (cudaMalloc(&s.d_blocks, cap * sizeof(xk::u64)) != cudaSuccess ||
-      cudaMallocHost(&s.h_blocks, cap * sizeof(xk::u64)) != cudaSuccess) {
+  if (xorec::dev_malloc(&s.d_blocks, cap * sizeof(xk::u64)) != cudaSuccess ||
+      xorec::host_malloc_pinned(&s.h_blocks, cap * sizeof(xk::u64)) != cudaSuccess) {
     cudaGetLastError();
     s.cap_blocks = 0;
     return false;
@@ -127,6 +127,7 @@ bool grow_blocks(Slot& s, size_t need) {
 
 // Launch one batch of requests on a free slot.
 bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
+  xorec::TraceRange trace_("xorec serve dispatch");
   // group by launch target: compiled module of this block size, or interpreter
   auto target = [&](const Req& r) -> void* { return r.mod; };
   std::stable_sort(reqs.begin(), reqs.end(),
@@ -336,9 +337,10 @@ ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
   for (Slot& sl : sv->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc(&sl.d_descs, sv->max_batch * sizeof(xk::StripeDesc)) != cudaSuccess ||
-        cudaMalloc(&sl.d_queues, sv->max_batch * sizeof(xk::u64)) != cudaSuccess ||
-        cudaMallocHost(&sl.h_descs, sv->max_batch * sizeof(xk::StripeDesc)) != cudaSuccess ||
+        xorec::dev_malloc(&sl.d_descs, sv->max_batch * sizeof(xk::StripeDesc)) != cudaSuccess ||
+        xorec::dev_malloc(&sl.d_queues, sv->max_batch * sizeof(xk::u64)) != cudaSuccess ||
+        xorec::host_malloc_pinned(&sl.h_descs, sv->max_batch * sizeof(xk::StripeDesc)) !=
+            cudaSuccess ||
         !grow_blocks(sl, static_cast<size_t>(sv->max_batch) * 16)) {
       cudaGetLastError();
       for (Slot& s2 : sv->slots) free_slot(s2);

@@ -64,6 +64,7 @@ extern "C" ec_status ec_plan_set_launch(ec_plan* plan, int threads, int reg_budg
 
 extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_stripes,
                                       void* stream, ec_tune_result* out) {
+  xorec::TraceRange trace_("xorec autotune");
   if (!plan) return fail(EC_EINVAL, "NULL plan");
   if (block_bytes == 0 || block_bytes % 128 != 0)
     return fail(EC_EINVAL, "block_bytes must be a positive multiple of 128");
@@ -75,8 +76,8 @@ extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_s
   const int k = plan->k, m = plan->m;
   const size_t din = static_cast<size_t>(k) * block_bytes, dout = static_cast<size_t>(m) * block_bytes;
   uint8_t *d_in = nullptr, *d_out = nullptr;
-  if (cudaMalloc(&d_in, n_stripes * din) != cudaSuccess ||
-      cudaMalloc(&d_out, n_stripes * dout) != cudaSuccess) {
+  if (xorec::dev_malloc(&d_in, n_stripes * din) != cudaSuccess ||
+      xorec::dev_malloc(&d_out, n_stripes * dout) != cudaSuccess) {
     cudaGetLastError();
     if (d_in) cudaFree(d_in);
     return fail(EC_ENOMEM, "scratch allocation for tuning failed");

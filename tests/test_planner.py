@@ -443,3 +443,32 @@ def test_singular_user_matrix_detected():
         assert e.value.status == xo.EC_ESINGULAR
     finally:
         xo.ec_plan_destroy(plan)
+
+
+def test_program_stream_check():
+    # hand-built stream, n_in = 2 inputs, n_out = 1 output strip, 1 slot:
+    #   slot0 <- in0 + in1          (2 args, 0 outputs, has slot)
+    #   out0  <- slot0 + in0        (2 args, 1 output)
+    good = [2, 0x8000, 0, 0, 1,
+            2, 1, 0, 2, 0]
+    xo.ec_program_check(good, 2, 1, 1)
+    bad = {
+        "operand out of range": [2, 0x8000, 0, 0, 3, 2, 1, 0, 2, 0],
+        "slot read before written": [2, 1, 0, 2, 0, 2, 0x8000, 0, 0, 1],
+        "output out of range": [2, 0x8000, 0, 0, 1, 2, 1, 1, 2, 0],
+        "slot out of range": [2, 0x8000, 1, 0, 1, 2, 1, 0, 2, 0],
+        "truncated": good[:-1],
+    }
+    for why, code in bad.items():
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_program_check(code, 2, 1, 1)
+        assert e.value.status == xo.EC_EINVAL, why
+    # every program the planner builds passes
+    plan = xo.ec_plan_create(10, 4)
+    try:
+        for er in (None, [0, 3, 7, 11], [12]):
+            info = xo.ec_plan_info(plan, er)
+            xo.ec_program_check(xo.ec_plan_program(plan, er), info["n_in"], info["n_out"],
+                                info["slots"])
+    finally:
+        xo.ec_plan_destroy(plan)
