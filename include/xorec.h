@@ -346,6 +346,7 @@ typedef struct {
   long long pending;               /* admitted, not yet launched                     */
   int slots_busy;
   long long compiled_in_background; /* programs compiled by the background thread   */
+  long long cancelled;             /* requests dropped by ec_server_cancel           */
 } ec_server_stats;
 
 ec_status ec_server_create(const ec_server_opts *opts, ec_server **out);
@@ -353,6 +354,11 @@ ec_status ec_server_create(const ec_server_opts *opts, ec_server **out);
  * max_erasures erasures of `plan`, so that no request waits for planning. */
 ec_status ec_server_warm(ec_server *server, ec_plan *plan, int max_erasures);
 ec_status ec_server_submit(ec_server *server, const ec_job *job, uint64_t *ticket);
+/* Cancel a request that is still waiting for a batch: it is dropped, its
+ * admitted bytes are returned and its ticket never completes (EC_OK).
+ * EC_EBUSY when it is already on the GPU or done, EC_EINVAL for a ticket
+ * the server never issued. */
+ec_status ec_server_cancel(ec_server *server, uint64_t ticket);
 /* Up to max completed tickets (and their latency from submission, in
  * microseconds) since the last call; *n_done receives the count. */
 ec_status ec_server_poll(ec_server *server, uint64_t *tickets, double *latency_us, int max,

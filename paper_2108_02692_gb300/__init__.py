@@ -301,6 +301,16 @@ def ec_server_submit(server: int, job) -> int:
     return ec_server_submit_raw(server, arr[0])
 
 
+def ec_server_cancel(server: int, ticket: int) -> bool:
+    """True when the request was still queued and is now dropped; False when
+    it is already on the GPU or done."""
+    rc = lib().ec_server_cancel(server, ticket)
+    if rc == EC_EBUSY:
+        return False
+    _check(rc)
+    return True
+
+
 def ec_server_poll(server: int, max_n: int = 4096):
     tickets = (ctypes.c_uint64 * max_n)()
     lat = (ctypes.c_double * max_n)()

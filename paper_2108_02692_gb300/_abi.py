@@ -75,7 +75,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_longlong) for n in
                 ("submitted", "completed", "rejected", "failed", "batches", "max_batch_seen",
                  "bytes_in", "bytes_out", "admitted_bytes", "pending")] + [
-        ("slots_busy", c_int), ("compiled_in_background", ctypes.c_longlong)]
+        ("slots_busy", c_int), ("compiled_in_background", ctypes.c_longlong),
+        ("cancelled", ctypes.c_longlong)]
 
 
 class TuneResult(ctypes.Structure):
@@ -115,6 +116,7 @@ SIGNATURES = {
     "ec_server_create": (c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(c_vp)]),
     "ec_server_warm": (c_int, [c_vp, c_vp, c_int]),
     "ec_server_submit": (c_int, [c_vp, ctypes.POINTER(Job), ctypes.POINTER(c_u64)]),
+    "ec_server_cancel": (c_int, [c_vp, c_u64]),
     "ec_server_poll": (c_int, [c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(ctypes.c_double),
                                c_int, intp]),
     "ec_server_stats_get": (c_int, [c_vp, ctypes.POINTER(ServerStats)]),

@@ -435,6 +435,21 @@ ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
   return EC_OK;
 }
 
+ec_status ec_server_cancel(ec_server* sv, uint64_t ticket) {
+  if (!sv) return fail(EC_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (ticket == 0 || ticket >= sv->next_ticket) return fail(EC_EINVAL, "unknown ticket");
+  for (auto it = sv->pending.begin(); it != sv->pending.end(); ++it) {
+    if (it->ticket != ticket) continue;
+    sv->admitted -= it->bytes;
+    sv->stats.cancelled += 1;
+    sv->pending.erase(it);
+    sv->n_pending.fetch_sub(1, std::memory_order_relaxed);
+    return EC_OK;
+  }
+  return EC_EBUSY;   // launched or finished
+}
+
 ec_status ec_server_poll(ec_server* sv, uint64_t* tickets, double* latency_us, int max,
                          int* n_done) {
   if (!sv || !n_done || max < 0) return fail(EC_EINVAL, "bad argument");

@@ -176,3 +176,37 @@ def test_new_patterns_run_then_get_compiled(background):
     finally:
         xo.ec_server_destroy(server)
         xo.ec_plan_destroy(plan)
+
+
+def test_cancel_queued_requests(plans):
+    """One slot and one request per batch, so requests queue behind each
+    other; cancelling from the back of the queue drops requests that were
+    still waiting (their outputs stay untouched and their tickets never
+    complete) while everything else completes bit-exact."""
+    server = xo.ec_server_create(max_batch=1, slots=1)
+    try:
+        reqs = requests(plans, 40, seed=11)
+        arr, keep = xo.make_jobs([r["job"] for r in reqs])
+        tickets = [xo.ec_server_submit_raw(server, arr[i]) for i in range(len(reqs))]
+        assert all(tickets)
+        cancelled = {t for t in reversed(tickets[-10:]) if xo.ec_server_cancel(server, t)}
+        assert cancelled, "no request was still queued"
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_server_cancel(server, max(tickets) + 100)
+        assert e.value.status == xo.EC_EINVAL
+        left = [t for t in tickets if t not in cancelled]
+        wait_all(server, left)
+        time.sleep(0.05)
+        assert not [t for t, _ in xo.ec_server_poll(server) if t in cancelled]
+        for t, r in zip(tickets, reqs):
+            for o, ex in zip(r["out"], r["expect"]):
+                got = o.cpu().numpy()
+                if t in cancelled:
+                    assert (got == 0xAB).all()
+                else:
+                    assert np.array_equal(got, ex)
+        st = xo.ec_server_stats_get(server)
+        assert st["cancelled"] == len(cancelled) and st["admitted_bytes"] == 0
+        assert not xo.ec_server_cancel(server, left[0])      # already done
+    finally:
+        xo.ec_server_destroy(server)
