@@ -1,4 +1,5 @@
 // C ABI of the library (declared in include/xorec.h).
+#include <cuda.h>   // tensor-map types; the encoder is taken from the driver at run time
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -131,6 +132,59 @@ bool jit_ensure(Program* p, int threads, std::string* err) {
   return true;
 }
 
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return static_cast<EncodeTiledFn>(nullptr);
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+}  // namespace
+
+bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out) {
+  static_assert(sizeof(xk::TensorMap) == sizeof(CUtensorMap), "tensor map size");
+  if (env_int("EC_TMA_TENSOR", 1) == 0) return false;
+  if (io.tab || !io.in_base || io.n_stripes < 1) return false;
+  const long long S = io.S;
+  const uint64_t base = reinterpret_cast<uint64_t>(io.in_base);
+  // strips equally spaced by S across the stripe's blocks; 16-byte rules
+  if (n_in < 1 || n_in > 256 || n_in != 8 * io.n_inblk) return false;
+  if (T % 16 != 0 || T / 4 < 4 || T / 4 > 256) return false;
+  if (S <= 0 || S % 16 != 0 || base % 16 != 0 || io.in_bstride != 8 * S) return false;
+  const long long plane = static_cast<long long>(n_in) * S;
+  const long long sstride = io.n_stripes > 1 ? io.in_sstride : plane;
+  if (sstride % 16 != 0 || sstride < plane || sstride >= (1ll << 40)) return false;
+  if (S / 4 > 0xffffffffll || io.n_stripes > 0xffffffffll) return false;
+  const EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dim[3] = {static_cast<cuuint64_t>(S / 4), static_cast<cuuint64_t>(n_in),
+                             static_cast<cuuint64_t>(io.n_stripes)};
+  const cuuint64_t stride[2] = {static_cast<cuuint64_t>(S), static_cast<cuuint64_t>(sstride)};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(T / 4), static_cast<cuuint32_t>(n_in), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r =
+      enc(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+          const_cast<uint8_t*>(io.in_base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t stream) {
   DeviceInfo di;
   if (!device_info(&di)) return false;
@@ -193,7 +247,12 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   const int grid_env = env_int("EC_GRID", 0);
   if (grid_env > 0) grid = grid_env;
   if (grid > lp.n_items) grid = lp.n_items;
-  if (compiled) return jit_launch(p, lp, threads, static_cast<int>(grid), smem, stream);
+  if (compiled) {
+    xk::TensorMap tm;
+    lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm) ? 1 : 0;
+    return jit_launch(p, lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem,
+                      stream);
+  }
   return launch_interp(lp, threads, static_cast<int>(grid), smem, stream);
 }
 

@@ -89,7 +89,7 @@ struct InterpBatchBody {
 
 __global__ void __launch_bounds__(256) interp_kernel(LaunchParams p) {
   extern __shared__ __align__(128) u8 smem[];
-  run_pipeline(p, smem, InterpBody());
+  run_pipeline(p, smem, InterpBody(), nullptr);
 }
 
 // Batched interpreter: shared memory = [header][stage: max_in * T]

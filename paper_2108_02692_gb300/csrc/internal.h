@@ -116,8 +116,12 @@ bool jit_available();
 bool jit_ensure(Program* p, int threads, std::string* err);
 bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin);
 bool jit_compile(Program* p, int threads, std::string* err);
-bool jit_launch(Program* p, const xk::LaunchParams& lp, int threads, int grid, size_t smem,
-                cudaStream_t stream);
+bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
+                int grid, size_t smem, cudaStream_t stream);
+// Tensor map of a strided launch's inputs as [stripe][input strip][4-byte
+// word] with a box of one tile of every input strip; false (no map) when the
+// layout or the driver does not allow one.
+bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out);
 int jit_max_ctas_per_sm(Program* p, int threads, size_t smem);
 void jit_release(Program* p);
 int jit_regs(const Program* p);

@@ -213,9 +213,9 @@ std::string gen_source(const xorec::Program& p, int threads) {
   os << gen_body(p, threads);
   os << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
      << (p.minb > 0 ? p.minb : env_or("EC_JIT_MINB", std::max(1, 512 / threads)))
-     << ") xorec_slp(xk::LaunchParams p) {\n"
+     << ") xorec_slp(xk::LaunchParams p, const __grid_constant__ xk::TensorMap tm) {\n"
         "  extern __shared__ __align__(128) xk::u8 smem[];\n"
-        "  xk::run_pipeline(p, smem, SlpBody());\n"
+        "  xk::run_pipeline(p, smem, SlpBody(), &tm);\n"
         "}\n";
   return os.str();
 }
@@ -377,8 +377,8 @@ int jit_max_ctas_per_sm(Program* p, int threads, size_t smem) {
   return n;
 }
 
-bool jit_launch(Program* p, const xk::LaunchParams& lp, int threads, int grid, size_t smem,
-                cudaStream_t stream) {
+bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
+                int grid, size_t smem, cudaStream_t stream) {
   auto* jk = static_cast<JitKernel*>(p->jit);
   if (!jk || jk->threads != threads) {
     set_error("compiled kernel missing or built for another block size");
@@ -389,7 +389,10 @@ bool jit_launch(Program* p, const xk::LaunchParams& lp, int threads, int grid, s
     return false;
   }
   xk::LaunchParams copy = lp;
-  void* args[] = {&copy};
+  xk::TensorMap map;
+  if (tm) map = *tm;
+  else std::memset(&map, 0, sizeof(map));
+  void* args[] = {&copy, &map};
   const cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(jk->kern), dim3(grid),
                                          dim3(threads), args, smem, stream);
   if (e != cudaSuccess) {

@@ -41,11 +41,20 @@ struct IoDesc {
   i64 n_stripes;
 };
 
+// Opaque TMA tensor map (the driver's 128-byte descriptor), passed to
+// kernels as a __grid_constant__ parameter.
+struct alignas(64) TensorMap {
+  u64 opaque[16];
+};
+
 struct LaunchParams {
   IoDesc io;
   int n_in, n_out;       // input / output strips (8 per block)
   int T;                 // tile bytes per strip (multiple of 16)
   int nstage;            // stages in the shared-memory ring
+  int tmap;              // 1: the kernel's tensor map describes the inputs as
+                         // [stripe][input strip][4-byte word] and one 3-D
+                         // copy fills a stage
   i64 tiles_per_strip;
   i64 n_items;
   const u16* code;       // interpreter stream (unused by compiled kernels)
@@ -133,6 +142,16 @@ __device__ __forceinline__ void tma_load_1d(u32 dst, const void* src, u32 bytes,
       ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
+// One tiled 3-D TMA copy (box given by the tensor map) into shared memory;
+// coordinates in elements, innermost first.
+__device__ __forceinline__ void tma_load_3d(u32 dst, const TensorMap* tm, int x, int y, int z,
+                                            u32 bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<u64>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(u32 bar, u32 parity) {
   u32 ok;
   asm volatile(
@@ -152,13 +171,24 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
   }
 }
 
-// Warp 0 issues the copies of one work item into stage `dst`.
-__device__ __forceinline__ void issue_item(const LaunchParams& p, i64 item, u8* dst, u32 bar) {
+// Warp 0 issues the copies of one work item into stage `dst`: one tiled
+// copy of every input strip's tile when the launch has a tensor map (the
+// box is n_in x T bytes; past the end of a strip it is zero-filled and still
+// counts in full), else one 1-D bulk copy per strip.
+__device__ __forceinline__ void issue_item(const LaunchParams& p, const TensorMap* tm, i64 item,
+                                           u8* dst, u32 bar) {
   const i64 s = item / p.tiles_per_strip;
   const i64 c0 = (item % p.tiles_per_strip) * p.T;
+  const int lane = threadIdx.x & 31;
+  if (p.tmap) {
+    if (lane == 0) {
+      mbar_arrive_expect_tx(bar, static_cast<u32>(p.n_in) * static_cast<u32>(p.T));
+      tma_load_3d(smem_addr(dst), tm, static_cast<int>(c0 >> 2), 0, static_cast<int>(s), bar);
+    }
+    return;
+  }
   const i64 rest = p.io.S - c0;
   const int len = rest < p.T ? static_cast<int>(rest) : p.T;
-  const int lane = threadIdx.x & 31;
   if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(p.n_in) * static_cast<u32>(len));
   __syncwarp();
   for (int c = lane; c < p.n_in; c += 32) {
@@ -178,7 +208,8 @@ __device__ __forceinline__ void issue_item(const LaunchParams& p, i64 item, u8* 
 //   void load(const LaunchParams&, int len, const u8* stage, Regs&) const
 //   void compute(const LaunchParams&, i64 stripe, i64 c0, int len, Regs&) const
 template <class Body>
-__device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, const Body& body) {
+__device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, const Body& body,
+                                             const TensorMap* tm) {
   u64* bars = reinterpret_cast<u64*>(smem);
   u8* stages = smem + 128;
   const i64 stage_bytes = static_cast<i64>(p.n_in) * p.T;
@@ -193,7 +224,7 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
   if (tid < 32) {
     for (int s = 0; s < p.nstage; ++s) {
       const i64 it = first + s * step;
-      if (it < p.n_items) issue_item(p, it, stages + s * stage_bytes, smem_addr(&bars[s]));
+      if (it < p.n_items) issue_item(p, tm, it, stages + s * stage_bytes, smem_addr(&bars[s]));
     }
   }
   for (i64 i = 0;; ++i) {
@@ -227,7 +258,7 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
       if (tid < 32 && nxt < p.n_items) {
         if (tid == 0) fence_proxy_async();
         __syncwarp();
-        issue_item(p, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
+        issue_item(p, tm, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
       }
       body.compute(p, s, c0, len, r);
     } else {
@@ -236,7 +267,7 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
       if (tid < 32 && nxt < p.n_items) {
         if (tid == 0) fence_proxy_async();
         __syncwarp();
-        issue_item(p, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
+        issue_item(p, tm, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
       }
     }
   }
