@@ -81,6 +81,7 @@ struct ec_batch {
   xk::u64* d_queues = nullptr;         // one work-queue head per launch
   xk::StripeDesc* d_descs = nullptr;
   xk::u64* d_blocks = nullptr;
+  xk::TensorMap* d_maps = nullptr;     // per-block tensor maps of the stripes' inputs
   int* status = nullptr;
   ec_batch_info info{};
 };
@@ -143,6 +144,7 @@ void free_batch(ec_batch* b) {
   if (b->d_descs) cudaFree(b->d_descs);
   if (b->d_queues) cudaFree(b->d_queues);
   if (b->d_blocks) cudaFree(b->d_blocks);
+  if (b->d_maps) cudaFree(b->d_maps);
   delete b;
 }
 
@@ -360,6 +362,10 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   });
   std::vector<xk::StripeDesc> descs(ents.size());
   std::vector<xk::u64> blocks;
+  // tensor maps of every input block (one tiled copy per block and tile);
+  // map_at[stripe] = index of its first map, -1 = one 1-D copy per strip
+  std::vector<xk::TensorMap> maps;
+  std::vector<long long> map_at(ents.size(), -1);
   long long bytes_in = 0, bytes_out = 0, total_items = 0;
   int cur = -1;
   long long launch_items = 0;
@@ -383,6 +389,18 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     d.code_len = static_cast<int>(e.prog->code.size());
     d.n_slots = e.prog->n_slots;
     for (uint64_t p : e.ptrs) blocks.push_back(p);
+    {
+      const size_t first = maps.size();
+      bool ok = true;
+      for (int j = 0; j < d.n_inblk && ok; ++j) {
+        xk::TensorMap tm;
+        ok = xorec::block_tensor_map(reinterpret_cast<const void*>(e.ptrs[j]), e.S, 4 * L.threads,
+                                     &tm);
+        if (ok) maps.push_back(tm);
+      }
+      if (ok) map_at[oi] = static_cast<long long>(first);
+      else maps.resize(first);
+    }
     launch_items += e.tiles;
     L.n_items = launch_items;
     L.n_stripes += 1;
@@ -401,8 +419,22 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       free_batch(b);
       return fail(EC_ENOMEM, "device allocation of the batch tables failed");
     }
+    if (!maps.empty() &&
+        xorec::dev_malloc(&b->d_maps, maps.size() * sizeof(xk::TensorMap)) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(EC_ENOMEM, "device allocation of the batch tensor maps failed");
+    }
     for (auto& d : descs)
       d.blocks = b->d_blocks + reinterpret_cast<uintptr_t>(d.blocks) / sizeof(xk::u64);
+    for (size_t i = 0; i < descs.size(); ++i)
+      descs[i].maps = map_at[i] >= 0 ? b->d_maps + map_at[i] : nullptr;
+    if (!maps.empty() && cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(xk::TensorMap),
+                                    cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(EC_ECUDA, "upload of the batch tensor maps failed");
+    }
     if (cudaMemcpy(b->d_descs, descs.data(), descs.size() * sizeof(xk::StripeDesc),
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_blocks, blocks.data(), blocks.size() * sizeof(xk::u64),

@@ -185,6 +185,25 @@ bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out)
   return r == CUDA_SUCCESS;
 }
 
+bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out) {
+  if (env_int("EC_TMA_TENSOR", 1) == 0) return false;
+  const uint64_t base = reinterpret_cast<uint64_t>(block);
+  if (!block || base % 16 != 0 || S <= 0 || S % 16 != 0 || S / 4 > 0xffffffffll) return false;
+  if (T % 16 != 0 || T / 4 < 4 || T / 4 > 256) return false;
+  const EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dim[2] = {static_cast<cuuint64_t>(S / 4), 8};
+  const cuuint64_t stride[1] = {static_cast<cuuint64_t>(S)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(T / 4), 8};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r =
+      enc(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+          const_cast<void*>(block), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t stream) {
   DeviceInfo di;
   if (!device_info(&di)) return false;

@@ -122,6 +122,9 @@ bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm,
 // word] with a box of one tile of every input strip; false (no map) when the
 // layout or the driver does not allow one.
 bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out);
+// Tensor map of one block as [strip][4-byte word] (8 strips S bytes apart)
+// with a box of one tile of its 8 strips; false when not allowed.
+bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out);
 int jit_max_ctas_per_sm(Program* p, int threads, size_t smem);
 void jit_release(Program* p);
 int jit_regs(const Program* p);

@@ -75,6 +75,9 @@ struct StripeDesc {
   int n_inblk, n_outblk;
   int prog;              // program index inside a compiled module
   int pad_;
+  const TensorMap* maps; // n_inblk tensor maps (input block j as [strip][4-byte
+                         // word], box = one tile of its 8 strips), or null:
+                         // one 1-D copy per strip
 };
 
 struct BatchParams {
@@ -140,6 +143,15 @@ __device__ __forceinline__ void tma_load_1d(u32 dst, const void* src, u32 bytes,
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// One tiled 2-D TMA copy (box given by the tensor map) into shared memory;
+// coordinates in elements, innermost first.
+__device__ __forceinline__ void tma_load_2d(u32 dst, const TensorMap* tm, int x, int y, u32 bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<u64>(tm)), "r"(x), "r"(y), "r"(bar) : "memory");
 }
 
 // One tiled 3-D TMA copy (box given by the tensor map) into shared memory;
@@ -298,9 +310,11 @@ __device__ __forceinline__ void batch_item_geom(const BatchParams& p, i64 item, 
 // be issued without waiting on descriptor loads.  Codes wider than
 // kMaxPrepared strips are addressed at issue time instead.
 struct NextCopy {
-  u32 bytes;     // n_in * len (expected transaction bytes)
+  u32 bytes;     // expected transaction bytes
   u32 len;
   int n_in;
+  int x;                    // tensor copies: first word of the tile
+  const TensorMap* maps;    // tensor copies: the stripe's block maps, or null
 };
 
 // First stripe cursor for `item` (binary search over item_base).
@@ -321,11 +335,19 @@ __device__ __forceinline__ void prepare_batch_item(const BatchParams& p, i64 ite
   batch_item_geom(p, item, cursor, d, c0, len);
   const int n_in = 8 * d->n_inblk;
   const int lane = threadIdx.x & 31;
+  nc.len = static_cast<u32>(len);
+  nc.n_in = n_in;
+  nc.maps = d->maps;
+  if (nc.maps) {
+    // one tiled copy per input block: the full box lands (zero-filled past
+    // the end of the strips) and counts in full
+    nc.x = static_cast<int>(c0 >> 2);
+    nc.bytes = static_cast<u32>(n_in) * static_cast<u32>(p.T);
+    return;
+  }
   if (n_in <= kMaxPrepared)
     for (int c = lane; c < n_in; c += 32)
       src[c] = reinterpret_cast<const u8*>(d->blocks[c >> 3]) + static_cast<i64>(c & 7) * d->S + c0;
-  nc.len = static_cast<u32>(len);
-  nc.n_in = n_in;
   nc.bytes = static_cast<u32>(n_in) * static_cast<u32>(len);
 }
 
@@ -335,6 +357,11 @@ __device__ __forceinline__ void issue_batch_prepared(const BatchParams& p, i64 i
   const int lane = threadIdx.x & 31;
   if (lane == 0) mbar_arrive_expect_tx(bar, nc.bytes);
   __syncwarp();
+  if (nc.maps) {
+    for (int j = lane; 8 * j < nc.n_in; j += 32)
+      tma_load_2d(smem_addr(dst + static_cast<i64>(8 * j) * p.T), nc.maps + j, nc.x, 0, bar);
+    return;
+  }
   if (nc.n_in <= kMaxPrepared) {
     for (int c = lane; c < nc.n_in; c += 32)
       tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), src[c], nc.len, bar);

@@ -57,8 +57,9 @@ def test_injected_allocation_failures_are_reported_and_recover():
         with pytest.raises(xo.XorecError) as e:
             xo.ec_encode(plan, [t.data_ptr() for t in d], [t.data_ptr() for t in par], B, st)
         assert e.value.status == xo.EC_ENOMEM
-        # a batch makes three allocations: fail each in turn
-        for nth in (1, 2, 3):
+        # a batch makes four allocations (descriptors, queues, block table,
+        # tensor maps): fail each in turn
+        for nth in (1, 2, 3, 4):
             xo.ec_debug_fail_alloc(nth)
             with pytest.raises(xo.XorecError) as e:
                 xo.ec_batch_create([job])
