@@ -390,16 +390,14 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     d.n_slots = e.prog->n_slots;
     for (uint64_t p : e.ptrs) blocks.push_back(p);
     {
-      const size_t first = maps.size();
       bool ok = true;
-      for (int j = 0; j < d.n_inblk && ok; ++j) {
-        xk::TensorMap tm;
-        ok = xorec::block_tensor_map(reinterpret_cast<const void*>(e.ptrs[j]), e.S, 4 * L.threads,
-                                     &tm);
-        if (ok) maps.push_back(tm);
+      for (int j = 0; j < d.n_inblk && ok; ++j)
+        ok = xorec::block_tensor_map_allowed(reinterpret_cast<const void*>(e.ptrs[j]), e.S,
+                                             4 * L.threads);
+      if (ok) {
+        map_at[oi] = static_cast<long long>(maps.size());
+        maps.resize(maps.size() + d.n_inblk);
       }
-      if (ok) map_at[oi] = static_cast<long long>(first);
-      else maps.resize(first);
     }
     launch_items += e.tiles;
     L.n_items = launch_items;
@@ -407,6 +405,33 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     total_items += e.tiles;
     bytes_in += static_cast<long long>(d.n_inblk) * static_cast<long long>(e.job->block_bytes);
     bytes_out += static_cast<long long>(d.n_outblk) * static_cast<long long>(e.job->block_bytes);
+  }
+
+  // encode the tensor maps in parallel host threads (each with the device's
+  // context current); a stripe whose maps the driver refuses falls back to
+  // one copy per strip
+  {
+    std::vector<char> refused(order.size(), 0);
+    parallel_for(order.size(), [&](size_t oi) {
+      if (map_at[oi] < 0) return;
+      thread_local int current = -1;
+      if (current != di.device) {
+        if (cudaSetDevice(di.device) != cudaSuccess) {
+          cudaGetLastError();
+          refused[oi] = 1;
+          return;
+        }
+        current = di.device;
+      }
+      const Entry& e = ents[order[oi]];
+      const int T = 4 * b->launches[e.launch].threads;
+      for (int j = 0; j < descs[oi].n_inblk; ++j)
+        if (!xorec::block_tensor_map(reinterpret_cast<const void*>(e.ptrs[j]), e.S, T,
+                                     &maps[map_at[oi] + j]))
+          refused[oi] = 1;
+    });
+    for (size_t oi = 0; oi < order.size(); ++oi)
+      if (refused[oi]) map_at[oi] = -1;
   }
 
   // 6. device copies (owned by the batch)

@@ -185,13 +185,17 @@ bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out)
   return r == CUDA_SUCCESS;
 }
 
-bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out) {
+bool block_tensor_map_allowed(const void* block, long long S, int T) {
   if (env_int("EC_TMA_TENSOR", 1) == 0) return false;
   const uint64_t base = reinterpret_cast<uint64_t>(block);
   if (!block || base % 16 != 0 || S <= 0 || S % 16 != 0 || S / 4 > 0xffffffffll) return false;
   if (T % 16 != 0 || T / 4 < 4 || T / 4 > 256) return false;
+  return tensor_map_encoder() != nullptr;
+}
+
+bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out) {
+  if (!block_tensor_map_allowed(block, S, T)) return false;
   const EncodeTiledFn enc = tensor_map_encoder();
-  if (!enc) return false;
   const cuuint64_t dim[2] = {static_cast<cuuint64_t>(S / 4), 8};
   const cuuint64_t stride[1] = {static_cast<cuuint64_t>(S)};
   const cuuint32_t box[2] = {static_cast<cuuint32_t>(T / 4), 8};

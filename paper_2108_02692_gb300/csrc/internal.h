@@ -125,6 +125,7 @@ bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out)
 // Tensor map of one block as [strip][4-byte word] (8 strips S bytes apart)
 // with a box of one tile of its 8 strips; false when not allowed.
 bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out);
+bool block_tensor_map_allowed(const void* block, long long S, int T);
 int jit_max_ctas_per_sm(Program* p, int threads, size_t smem);
 void jit_release(Program* p);
 int jit_regs(const Program* p);
