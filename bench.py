@@ -35,10 +35,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 K_DATA, M_PAR, BLOCK, N_STRIPES = 10, 4, 1 << 20, 256
-CONFIG_ID = 2
+ENCODE_WORKLOAD_ID = 2       # seed namespace of the encode inputs
 WORKLOAD = "RS(10,4) Cauchy GF(2^8)/0x11d encode, 256 stripes x 10 x 1 MiB"
 METRIC = "RS(10,4) encode/decode GB/s & % HBM peak; batched vs plain; served p50/p99"
-DECODE_CONFIG_ID = 3
+DECODE_WORKLOAD_ID = 3       # seed namespace of the decode inputs
 
 
 def parse_args():
@@ -177,12 +177,12 @@ def oracle_sample_gbs(n_threads: int, stripes_per_thread: int = 1, decode: bool 
         pats = [p for p in synth.decode_patterns(K_DATA, M_PAR, 4 * n) if len(p) == M_PAR][:n]
         work = []
         for s, er in enumerate(pats):
-            avail = [None if i in er else synth.block_bytes(DECODE_CONFIG_ID, s, i, BLOCK)
+            avail = [None if i in er else synth.block_bytes(DECODE_WORKLOAD_ID, s, i, BLOCK)
                      for i in range(K_DATA + M_PAR)]
             work.append((list(er), avail))
         fn = lambda w: oracle.decode(P, w[0], w[1])
     else:
-        work = [[synth.block_bytes(CONFIG_ID, s, j, BLOCK) for j in range(K_DATA)]
+        work = [[synth.block_bytes(ENCODE_WORKLOAD_ID, s, j, BLOCK) for j in range(K_DATA)]
                 for s in range(n)]
         fn = lambda d: oracle.encode(P, d)
     t0 = time.perf_counter()
@@ -283,7 +283,7 @@ def run_ours(args):
     par = torch.empty((n, m, B), dtype=torch.uint8, device="cuda")
     for s in range(n):
         for j in range(k):
-            xo.ec_synth_fill(data[s, j].data_ptr(), B, synth.block_seed(CONFIG_ID, s, j), 0, sp)
+            xo.ec_synth_fill(data[s, j].data_ptr(), B, synth.block_seed(ENCODE_WORKLOAD_ID, s, j), 0, sp)
     stream.synchronize()
     tune = None
     if not args.no_tune and executor != xo.EC_EXEC_INTERP and args.max_temps == -2 and args.opt == "xorrepair":
@@ -331,7 +331,7 @@ def run_ours(args):
         rng = np.random.default_rng(7)
         for s in rng.choice(n, 4, replace=False):
             w0 = int(rng.integers(0, (S - 64) // 16)) * 16
-            mini = [synth.strip_slice(CONFIG_ID, int(s), j, B, w0, 64) for j in range(k)]
+            mini = [synth.strip_slice(ENCODE_WORKLOAD_ID, int(s), j, B, w0, 64) for j in range(k)]
             ref = oracle.encode(P, mini)
             got = par[int(s)].view(m, 8, S)[:, :, w0:w0 + 64].cpu().numpy()
             ok &= all(np.array_equal(got[i].reshape(-1), ref[i]) for i in range(m))
@@ -427,7 +427,7 @@ def run_decode(args, xo, torch, stream, peak):
     outs = torch.zeros((n, m, B), dtype=torch.uint8, device="cuda")
     for s in range(n):
         for j in range(k):
-            xo.ec_synth_fill(surv[s, j].data_ptr(), B, synth.block_seed(DECODE_CONFIG_ID, s, j),
+            xo.ec_synth_fill(surv[s, j].data_ptr(), B, synth.block_seed(DECODE_WORKLOAD_ID, s, j),
                              0, sp)
     stream.synchronize()
     plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, args.matrix))
@@ -471,7 +471,7 @@ def run_decode(args, xo, torch, stream, peak):
         er = list(pats[int(s)])
         R = oracle.decode_matrix(P, er)
         w0 = int(rng.integers(0, (S - 32) // 16)) * 16
-        mini = [synth.strip_slice(DECODE_CONFIG_ID, int(s), j, B, w0, 32) for j in range(k)]
+        mini = [synth.strip_slice(DECODE_WORKLOAD_ID, int(s), j, B, w0, 32) for j in range(k)]
         ref = oracle.apply(R, mini)
         got = outs[int(s), :len(er)].view(len(er), 8, S)[:, :, w0:w0 + 32].cpu().numpy()
         ok &= all(np.array_equal(got[i].reshape(-1), ref[i]) for i in range(len(er)))
@@ -698,7 +698,7 @@ def serve_stream(xo, torch, reqs, plans, data_arena, out_arena, max_batch, slots
 
 
 def run_served(args):
-    """Config 5: Poisson arrivals, RS(10,4)/RS(6,3), objects log-uniform
+    """Served workload: Poisson arrivals, RS(10,4)/RS(6,3), objects log-uniform
     4 KiB-16 MiB (B = roundup(ceil(L/k), 128)), half of them decodes with
     1..m random erasures; 32 GiB admission budget."""
     import torch
@@ -750,7 +750,7 @@ def run_served(args):
 
 
 def run_batched(args):
-    """Config 4: mixed codes RS(6,3)/(8,4)/(10,4)/(12,4), block sizes
+    """Batched workload: mixed codes RS(6,3)/(8,4)/(10,4)/(12,4), block sizes
     log-uniform 4 KiB-8 MiB, half of the stripes decoded with random
     erasures, all in one batch run, against one launch per stripe."""
     import numpy as np

@@ -55,25 +55,25 @@ def stream_bytes(seed: int, offset: int, n: int) -> np.ndarray:
     return b[s:s + n].copy()
 
 
-def block_seed(config_id: int, stripe: int, block: int) -> int:
-    """Seed of block ``block`` of stripe ``stripe`` in workload ``config_id``."""
-    return (BASE_SEED ^ (config_id << 40) ^ (stripe << 12) ^ block) & _M64
+def block_seed(workload_id: int, stripe: int, block: int) -> int:
+    """Seed of block ``block`` of stripe ``stripe`` in workload ``workload_id``."""
+    return (BASE_SEED ^ (workload_id << 40) ^ (stripe << 12) ^ block) & _M64
 
 
-def block_bytes(config_id: int, stripe: int, block: int, B: int,
+def block_bytes(workload_id: int, stripe: int, block: int, B: int,
                 offset: int = 0, n: int | None = None) -> np.ndarray:
     if n is None:
         n = B - offset
-    return stream_bytes(block_seed(config_id, stripe, block), offset, n)
+    return stream_bytes(block_seed(workload_id, stripe, block), offset, n)
 
 
-def strip_slice(config_id: int, stripe: int, block: int, B: int, w0: int,
+def strip_slice(workload_id: int, stripe: int, block: int, B: int, w0: int,
                 L: int) -> np.ndarray:
     """Bytes [w0, w0+L) of each of the 8 strips of one block, as a block of
     8*L bytes in the same strip layout (columns are independent, so this is a
     valid small block for the oracle)."""
     S = B // 8
-    parts = [block_bytes(config_id, stripe, block, B, t * S + w0, L)
+    parts = [block_bytes(workload_id, stripe, block, B, t * S + w0, L)
              for t in range(8)]
     return np.concatenate(parts)
 
