@@ -50,12 +50,12 @@ struct Slot {
   cudaEvent_t done = nullptr;
   bool busy = false;
   std::vector<Req> reqs;
-  xk::StripeDesc* d_descs = nullptr;
-  xk::u64* d_blocks = nullptr;
-  xk::u64* d_queues = nullptr;
-  xk::StripeDesc* h_descs = nullptr;   // pinned staging
-  xk::u64* h_blocks = nullptr;
-  size_t cap_blocks = 0;
+  // one device table per slot and its pinned staging copy, laid out per
+  // dispatch as [work-queue heads][stripe descriptors][block pointers], so
+  // that one copy carries a whole batch's tables
+  xk::u8* d_tab = nullptr;
+  xk::u8* h_tab = nullptr;
+  size_t cap = 0;   // bytes
 };
 
 int env_int(const char* name, int dflt) {
@@ -100,30 +100,30 @@ namespace {
 void free_slot(Slot& s) {
   if (s.st) cudaStreamDestroy(s.st);
   if (s.done) cudaEventDestroy(s.done);
-  if (s.d_descs) cudaFree(s.d_descs);
-  if (s.d_blocks) cudaFree(s.d_blocks);
-  if (s.d_queues) cudaFree(s.d_queues);
-  if (s.h_descs) cudaFreeHost(s.h_descs);
-  if (s.h_blocks) cudaFreeHost(s.h_blocks);
+  if (s.d_tab) cudaFree(s.d_tab);
+  if (s.h_tab) cudaFreeHost(s.h_tab);
   s = Slot();
 }
 
-bool grow_blocks(Slot& s, size_t need) {
-  if (need <= s.cap_blocks) return true;
-  size_t cap = std::max(need, 2 * s.cap_blocks);
-  if (s.d_blocks) cudaFree(s.d_blocks);
-  if (s.h_blocks) cudaFreeHost(s.h_blocks);
-  s.d_blocks = nullptr;
-  s.h_blocks = nullptr;
-  if (xorec::dev_malloc(&s.d_blocks, cap * sizeof(xk::u64)) != cudaSuccess ||
-      xorec::host_malloc_pinned(&s.h_blocks, cap * sizeof(xk::u64)) != cudaSuccess) {
+// Capacity of the slot's table (bytes); contents are rewritten per dispatch.
+bool grow_table(Slot& s, size_t need) {
+  if (need <= s.cap) return true;
+  const size_t cap = std::max(need, 2 * s.cap);
+  if (s.d_tab) cudaFree(s.d_tab);
+  if (s.h_tab) cudaFreeHost(s.h_tab);
+  s.d_tab = nullptr;
+  s.h_tab = nullptr;
+  s.cap = 0;
+  if (xorec::dev_malloc(&s.d_tab, cap) != cudaSuccess ||
+      xorec::host_malloc_pinned(&s.h_tab, cap) != cudaSuccess) {
     cudaGetLastError();
-    s.cap_blocks = 0;
     return false;
   }
-  s.cap_blocks = cap;
+  s.cap = cap;
   return true;
 }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Launch one batch of requests on a free slot.
 bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
@@ -132,9 +132,21 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
   auto target = [&](const Req& r) -> void* { return r.mod; };
   std::stable_sort(reqs.begin(), reqs.end(),
                    [&](const Req& a, const Req& b) { return target(a) < target(b); });
-  size_t n_blocks = 0;
-  for (const auto& r : reqs) n_blocks += r.ptrs.size();
-  if (!grow_blocks(sl, n_blocks)) return false;
+  size_t n_blocks = 0, n_launches = 0;
+  for (size_t i = 0; i < reqs.size(); ++i) {
+    n_blocks += reqs[i].ptrs.size();
+    if (i == 0 || target(reqs[i]) != target(reqs[i - 1])) ++n_launches;
+  }
+  const size_t desc_off = align_up(n_launches * sizeof(xk::u64), 64);
+  const size_t block_off = desc_off + reqs.size() * sizeof(xk::StripeDesc);
+  const size_t bytes = block_off + n_blocks * sizeof(xk::u64);
+  if (!grow_table(sl, bytes)) return false;
+  std::memset(sl.h_tab, 0, n_launches * sizeof(xk::u64));   // work-queue heads
+  auto* h_descs = reinterpret_cast<xk::StripeDesc*>(sl.h_tab + desc_off);
+  auto* h_blocks = reinterpret_cast<xk::u64*>(sl.h_tab + block_off);
+  auto* d_queues = reinterpret_cast<xk::u64*>(sl.d_tab);
+  auto* d_descs = reinterpret_cast<xk::StripeDesc*>(sl.d_tab + desc_off);
+  auto* d_blocks = reinterpret_cast<xk::u64*>(sl.d_tab + block_off);
   struct L { void* mod; int threads, begin, n; long long items; int max_in, max_slots; };
   std::vector<L> launches;
   size_t off = 0;
@@ -144,9 +156,9 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
     if (launches.empty() || launches.back().mod != mod)
       launches.push_back(L{mod, xorec::launch_threads(mod), static_cast<int>(i), 0, 0, 0, 0});
     L& l = launches.back();
-    xk::StripeDesc& d = sl.h_descs[i];
+    xk::StripeDesc& d = h_descs[i];
     std::memset(&d, 0, sizeof(d));
-    d.blocks = sl.d_blocks + off;
+    d.blocks = d_blocks + off;
     d.S = r.S;
     d.item_base = l.items;
     d.n_inblk = r.prog->n_in / 8;
@@ -155,18 +167,14 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
     d.code = r.prog->d_code;
     d.code_len = static_cast<int>(r.prog->code.size());
     d.n_slots = r.prog->n_slots;
-    std::memcpy(sl.h_blocks + off, r.ptrs.data(), r.ptrs.size() * sizeof(xk::u64));
+    std::memcpy(h_blocks + off, r.ptrs.data(), r.ptrs.size() * sizeof(xk::u64));
     off += r.ptrs.size();
     l.n += 1;
     l.items += r.tiles;
     l.max_in = std::max(l.max_in, r.prog->n_in);
     if (!mod) l.max_slots = std::max(l.max_slots, r.prog->n_slots);
   }
-  if (cudaMemcpyAsync(sl.d_descs, sl.h_descs, reqs.size() * sizeof(xk::StripeDesc),
-                      cudaMemcpyHostToDevice, sl.st) != cudaSuccess ||
-      cudaMemcpyAsync(sl.d_blocks, sl.h_blocks, n_blocks * sizeof(xk::u64), cudaMemcpyHostToDevice,
-                      sl.st) != cudaSuccess ||
-      cudaMemsetAsync(sl.d_queues, 0, launches.size() * sizeof(xk::u64), sl.st) != cudaSuccess) {
+  if (cudaMemcpyAsync(sl.d_tab, sl.h_tab, bytes, cudaMemcpyHostToDevice, sl.st) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -184,10 +192,10 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
     }
     xk::BatchParams bp;
     std::memset(&bp, 0, sizeof(bp));
-    bp.stripes = sl.d_descs + l.begin;
+    bp.stripes = d_descs + l.begin;
     bp.n_stripes = l.n;
     bp.chunk = sv->chunk;
-    bp.queue = sl.d_queues + li;
+    bp.queue = d_queues + li;
     bp.n_items = l.items;
     bp.T = 4 * l.threads;
     bp.max_in = l.max_in;
@@ -337,11 +345,8 @@ ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
   for (Slot& sl : sv->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-        xorec::dev_malloc(&sl.d_descs, sv->max_batch * sizeof(xk::StripeDesc)) != cudaSuccess ||
-        xorec::dev_malloc(&sl.d_queues, sv->max_batch * sizeof(xk::u64)) != cudaSuccess ||
-        xorec::host_malloc_pinned(&sl.h_descs, sv->max_batch * sizeof(xk::StripeDesc)) !=
-            cudaSuccess ||
-        !grow_blocks(sl, static_cast<size_t>(sv->max_batch) * 16)) {
+        !grow_table(sl, static_cast<size_t>(sv->max_batch) *
+                            (sizeof(xk::u64) + sizeof(xk::StripeDesc) + 16 * sizeof(xk::u64)))) {
       cudaGetLastError();
       for (Slot& s2 : sv->slots) free_slot(s2);
       delete sv;

@@ -64,8 +64,9 @@ def test_injected_allocation_failures_are_reported_and_recover():
             with pytest.raises(xo.XorecError) as e:
                 xo.ec_batch_create([job])
             assert e.value.status == xo.EC_ENOMEM
-        # a server makes five per slot: fail the first and one in the last slot
-        for nth in (1, 18):
+        # a server makes two per slot (device table, pinned staging): fail the
+        # first and the last
+        for nth in (1, 8):
             xo.ec_debug_fail_alloc(nth)
             with pytest.raises(xo.XorecError) as e:
                 xo.ec_server_create()
