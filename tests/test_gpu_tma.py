@@ -118,3 +118,37 @@ def test_batch_same_bytes_with_and_without_tensor_copies():
     finally:
         for h in plans.values():
             xo.ec_plan_destroy(h)
+
+
+@pytest.mark.parametrize("pad_stripe,block_gap", [(4096, 0),       # padded stripes: tensor copies
+                                                  (0, 1024),       # gaps between blocks: per-strip
+                                                  (8192, 2048)])
+def test_strided_layouts_with_padding(pad_stripe, block_gap):
+    torch.cuda.set_device(0)
+    k, m, B, n = 10, 4, 8 * 1040, 4
+    bstride = B + block_gap
+    sstride = k * bstride + pad_stripe
+    plan = xo.ec_plan_create(k, m)
+    try:
+        buf = torch.zeros(n * sstride, dtype=torch.uint8, device="cuda")
+        data = [[synth.block_bytes(63, s, j, B) for j in range(k)] for s in range(n)]
+        for s in range(n):
+            for j in range(k):
+                o = s * sstride + j * bstride
+                buf[o:o + B] = torch.from_numpy(data[s][j]).cuda()
+        outs = []
+        for on in (True, False):
+            par = torch.full((n, m, B), 0x11, dtype=torch.uint8, device="cuda")
+            with tensor_copies(on):
+                xo.ec_encode_strided(plan, buf.data_ptr(), sstride, bstride, par.data_ptr(), m * B, B,
+                                     n, B, stream())
+                torch.cuda.synchronize()
+            outs.append(par.cpu().numpy())
+        assert np.array_equal(outs[0], outs[1])
+        P = oracle.cauchy(k, m)
+        for s in range(n):
+            ref = oracle.encode(P, data[s])
+            for i in range(m):
+                assert np.array_equal(outs[0][s, i], ref[i]), (s, i)
+    finally:
+        xo.ec_plan_destroy(plan)
