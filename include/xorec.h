@@ -25,6 +25,11 @@
  * argument errors are returned synchronously.  Errors found by kernels
  * (a bounded wait that timed out) are reported by ec_device_status().
  * ec_last_error() returns a thread-local message for the last failure.
+ *
+ * Threads.  Encode, decode, batch and serving calls may run from several
+ * host threads at once, also on one plan (decoders and compiled kernels are
+ * built once, under the plan's lock); ec_plan_autotune, ec_plan_set_launch
+ * and ec_plan_destroy must not overlap other calls on the same plan.
  */
 #ifndef XOREC_H
 #define XOREC_H
@@ -200,7 +205,9 @@ ec_status ec_encode_strided(ec_plan *plan, const uint8_t *data, size_t data_stri
  * directions and the kernels overlap.  Pinned host memory gives full link
  * speed; pageable memory works but copies synchronously.  Asynchronous with
  * respect to the host: the work is ordered after `stream`'s prior work and
- * `stream` waits for all of it; keep the buffers alive until then. */
+ * `stream` waits for all of it; keep the buffers alive until then.  Calls
+ * on one plan from several host threads are enqueued one at a time (they
+ * share the plan's staging and streams). */
 ec_status ec_encode_host_strided(ec_plan *plan, const uint8_t *data, size_t data_stripe_stride,
                                  size_t data_block_stride, uint8_t *parity,
                                  size_t par_stripe_stride, size_t par_block_stride,

@@ -92,6 +92,9 @@ extern "C" ec_status ec_encode_host_strided(ec_plan* plan, const uint8_t* data,
   if (block_bytes == 0 || block_bytes % 128 != 0)
     return fail(EC_EINVAL, "block_bytes must be a positive multiple of 128");
   if (n_stripes == 0) return EC_OK;
+  // the plan's lanes, staging and fork/join events are shared: enqueue one
+  // call at a time (the lanes' stream order then keeps staging reuse safe)
+  std::lock_guard<std::mutex> io_lock(plan->hostio_mu);
   const int k = plan->k, m = plan->m;
   const int chunk = chunk_stripes > 0 ? std::min(chunk_stripes, n_stripes) : std::min(16, n_stripes);
   const size_t din = static_cast<size_t>(k) * block_bytes;    // device data per stripe

@@ -28,6 +28,7 @@ struct ec_plan {
   std::map<std::vector<int>, std::unique_ptr<xorec::Program>> dec;  // key: sorted erasures
   std::vector<void*> modules;                // compiled multi-program modules (batches)
   xorec_host_io* hostio = nullptr;           // lanes and staging of ec_encode_host_strided
+  std::mutex hostio_mu;                      // one host-memory encode enqueues at a time
   int tuned_threads = 0, tuned_minb = 0;     // compiled-tier launch shape from the autotuner
   std::vector<std::unique_ptr<xorec::Program>> retired;  // encoders replaced by the autotuner
 };
