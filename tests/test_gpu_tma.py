@@ -152,3 +152,52 @@ def test_strided_layouts_with_padding(pad_stripe, block_gap):
                 assert np.array_equal(outs[0][s, i], ref[i]), (s, i)
     finally:
         xo.ec_plan_destroy(plan)
+
+
+def test_large_blocks_strided_sampled():
+    # 64 MiB blocks: strips of 8 MiB, tile coordinates up to 2^21 words
+    torch.cuda.set_device(0)
+    k, m, B, n = 4, 2, 64 << 20, 2
+    S = B // 8
+    plan = xo.ec_plan_create(k, m)
+    try:
+        data = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
+        for s in range(n):
+            for j in range(k):
+                xo.ec_synth_fill(data[s, j].data_ptr(), B, synth.block_seed(65, s, j), 0, stream())
+        par = torch.zeros((n, m, B), dtype=torch.uint8, device="cuda")
+        xo.ec_encode_strided(plan, data.data_ptr(), k * B, B, par.data_ptr(), m * B, B, n, B, stream())
+        torch.cuda.synchronize()
+        P = oracle.cauchy(k, m)
+        for s in range(n):
+            for w0 in (0, S // 2 + 4096, S - 64):
+                mini = [synth.strip_slice(65, s, j, B, w0, 64) for j in range(k)]
+                ref = oracle.encode(P, mini)
+                got = par[s].view(m, 8, S)[:, :, w0:w0 + 64].cpu().numpy()
+                for i in range(m):
+                    assert np.array_equal(got[i].reshape(-1), ref[i]), (s, w0, i)
+        assert xo.ec_device_status() == 0
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+def test_many_tiny_stripes_strided():
+    # 128-byte blocks: 16-byte strips inside 512-byte boxes (mostly zero fill)
+    torch.cuda.set_device(0)
+    k, m, B, n = 10, 4, 128, 5000
+    plan = xo.ec_plan_create(k, m)
+    try:
+        data = np.stack([np.stack([synth.block_bytes(66, s, j, B) for j in range(k)])
+                         for s in range(n)])
+        d = torch.from_numpy(data).cuda()
+        par = torch.zeros((n, m, B), dtype=torch.uint8, device="cuda")
+        xo.ec_encode_strided(plan, d.data_ptr(), k * B, B, par.data_ptr(), m * B, B, n, B, stream())
+        torch.cuda.synchronize()
+        got = par.cpu().numpy()
+        P = oracle.cauchy(k, m)
+        for s in range(n):
+            ref = oracle.encode(P, list(data[s]))
+            for i in range(m):
+                assert np.array_equal(got[s, i], ref[i]), (s, i)
+    finally:
+        xo.ec_plan_destroy(plan)
