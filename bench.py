@@ -71,6 +71,9 @@ def parse_args():
     ap.add_argument("--decode-patterns", type=int, default=0,
                     help="0: erasure sets uniform over all patterns; N > 0: the stripes cycle "
                          "through N distinct sets of m erasures (profiling program diversity)")
+    ap.add_argument("--decode-erasures", default="",
+                    help="comma-separated block ids erased in every decode stripe (e.g. 2,4,5,6, "
+                         "the paper's P_dec)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     return ap.parse_args()
 
@@ -350,7 +353,7 @@ def run_ours(args):
     if not args.no_e2e and n == N_STRIPES:
         e2e = run_e2e(args, xo, plan, data, par, stream, torch)
     decode = None
-    if not args.no_decode and (n == N_STRIPES or args.decode_patterns > 0
+    if not args.no_decode and (n == N_STRIPES or args.decode_patterns > 0 or args.decode_erasures
                                or args.decode_stripes != N_STRIPES):
         del data, par
         torch.cuda.empty_cache()
@@ -414,7 +417,11 @@ def run_decode(args, xo, torch, stream, peak):
     k, m, B, n = K_DATA, M_PAR, BLOCK, args.decode_stripes
     S = B // 8
     sp = stream.cuda_stream
-    if args.decode_patterns > 0:
+    if args.decode_erasures:
+        fixed = tuple(int(x) for x in args.decode_erasures.split(","))
+        pats = [fixed] * n
+        what = f"RS(10,4) decode, {n} stripes x 1 MiB, erased blocks {list(fixed)} in every stripe"
+    elif args.decode_patterns > 0:
         full = list(dict.fromkeys(p for p in synth.decode_patterns(k, m, 4096) if len(p) == m))
         pats = [full[s % min(args.decode_patterns, len(full))] for s in range(n)]
         what = (f"RS(10,4) decode, {n} stripes x 1 MiB, {m} erasures per stripe, cycling "
