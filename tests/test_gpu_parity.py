@@ -274,11 +274,16 @@ def _fill_stripes(buf, cfg, n, nblk, B):
             xo.ec_synth_fill(buf[s, j].data_ptr(), B, synth.block_seed(cfg, s, j), 0, stream())
 
 
-def test_full_size_encode_rs10_4_sampled():
+@pytest.mark.parametrize("shape", [None, (128, 160), (256, 128)],
+                         ids=["default", "128x160", "256x128"])
+def test_full_size_encode_rs10_4_sampled(shape):
     """The benchmark's encode launch: 256 stripes x 10 x 1 MiB in one call,
-    checked on sampled windows of every stripe against the oracle."""
+    checked on sampled windows of every stripe against the oracle, under the
+    default launch shape and the shapes the autotuner picks on GB300."""
     k, m, B, n = FULL_K, FULL_M, FULL_B, FULL_N
     p = Plan(k, m)
+    if shape:
+        xo.ec_plan_set_launch(p.h, *shape)
     try:
         data = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
         _fill_stripes(data, 2, n, k, B)
