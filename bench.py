@@ -227,9 +227,17 @@ def cpu_baseline_obj():
                                  f"per host thread, {dtd:.2f} s wall"}}
 
 
-def kernel_source_hash() -> str:
+# Sources that determine each kernel kind's code (the planner's programs,
+# the shared pipeline and the kernel body).
+KERNEL_SOURCES = {
+    "compiled": ("tile_pipeline.cuh", "jit.cc", "slp.cc", "plan.cc"),
+    "interp": ("tile_pipeline.cuh", "executor.cu", "slp.cc", "plan.cc"),
+}
+
+
+def kernel_source_hash(kind: str = "compiled") -> str:
     h = hashlib.sha256()
-    for f in ("tile_pipeline.cuh", "jit.cc", "executor.cu", "slp.cc", "plan.cc"):
+    for f in KERNEL_SOURCES[kind]:
         h.update(open(os.path.join(ROOT, "paper_2108_02692_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -238,7 +246,7 @@ def traffic_from_profiles(kind: str):
     """dram bytes per launch recorded by an ncu capture of the same kernel
     sources (profiles/*.md line 'traffic_per_launch: <bytes> source_hash:
     <hash> kind: <kind>'); null when the kernel changed since."""
-    want = kernel_source_hash()
+    want = kernel_source_hash(kind)
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None

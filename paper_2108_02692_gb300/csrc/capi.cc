@@ -276,7 +276,9 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     return jit_launch(p, lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem,
                       stream);
   }
-  return launch_interp(lp, threads, static_cast<int>(grid), smem, stream);
+  xk::TensorMap tm;
+  lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm) ? 1 : 0;
+  return launch_interp(lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem, stream);
 }
 
 }  // namespace xorec

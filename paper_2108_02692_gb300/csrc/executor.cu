@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "internal.h"
 #include "tile_pipeline.cuh"
@@ -87,9 +88,10 @@ struct InterpBatchBody {
   }
 };
 
-__global__ void __launch_bounds__(256) interp_kernel(LaunchParams p) {
+__global__ void __launch_bounds__(256)
+    interp_kernel(LaunchParams p, const __grid_constant__ TensorMap tm) {
   extern __shared__ __align__(128) u8 smem[];
-  run_pipeline(p, smem, InterpBody(), nullptr);
+  run_pipeline(p, smem, InterpBody(), &tm);
 }
 
 // Batched interpreter: shared memory = [header][stage: max_in * T]
@@ -162,14 +164,17 @@ int interp_max_ctas_per_sm(int threads, size_t smem) {
   return n;
 }
 
-bool launch_interp(const xk::LaunchParams& lp, int threads, int grid, size_t smem,
-                   cudaStream_t stream) {
+bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads, int grid,
+                   size_t smem, cudaStream_t stream) {
   if (cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     set_error("cudaFuncSetAttribute(interp) failed");
     return false;
   }
-  interp_kernel<<<grid, threads, smem, stream>>>(lp);
+  xk::TensorMap map;
+  if (tm) map = *tm;
+  else std::memset(&map, 0, sizeof(map));
+  interp_kernel<<<grid, threads, smem, stream>>>(lp, map);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("interpreter launch failed: ") + cudaGetErrorString(e));

@@ -101,8 +101,8 @@ struct LaunchShape {
 bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t stream);
 
 // Interpreter launch (executor.cu).
-bool launch_interp(const xk::LaunchParams& lp, int threads, int grid, size_t smem,
-                   cudaStream_t stream);
+bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads, int grid,
+                   size_t smem, cudaStream_t stream);
 size_t interp_smem_bytes(int n_in, int n_slots, int T, int nstage);
 int interp_max_ctas_per_sm(int threads, size_t smem);
 

@@ -147,5 +147,6 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
   if (per_sm < 1) per_sm = 1;
   long long grid = static_cast<long long>(sms) * per_sm;
   if (grid > lp.n_items) grid = lp.n_items;
-  return xorec::launch_interp(lp, threads, static_cast<int>(grid), smem, st) ? EC_OK : EC_ECUDA;
+  return xorec::launch_interp(lp, nullptr, threads, static_cast<int>(grid), smem, st) ? EC_OK
+                                                                                      : EC_ECUDA;
 }
