@@ -236,9 +236,14 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(kind: str = "compiled") -> str:
+    """Fingerprint of the code (comments and blank lines removed) of the
+    sources that determine a kernel kind."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kind]:
-        h.update(open(os.path.join(ROOT, "paper_2108_02692_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2108_02692_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = [re.sub(r"(^|\s)//.*$", "", ln).rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,10 +5,11 @@
 // Work decomposition (blocking, Sec. 6.1, retargeted): every stripe's strips
 // are cut into tiles of T bytes; one work item = (stripe, tile).  A CTA walks
 // items blockIdx.x, blockIdx.x + gridDim.x, ...; for each item one warp
-// issues one 1-D bulk copy (cp.async.bulk, TMA) per input strip into a shared
-// memory stage, completion is tracked by an mbarrier with a transaction
-// count, and every thread then runs the XOR program on its own 4-byte column
-// of the tile.  `nstage` stages form a ring so that the copies of the next
+// stages every input strip's tile in shared memory with TMA (one tiled
+// tensor copy per item for strided inputs, one per input block in batches,
+// else one 1-D bulk copy per strip), completion is tracked by an mbarrier
+// with a transaction count, and every thread then runs the XOR program on
+// its own 4-byte column of the tile.  `nstage` stages form a ring so that the copies of the next
 // items overlap the computation of the current one.  Every input byte is
 // read from HBM once and every output byte written once.
 //
