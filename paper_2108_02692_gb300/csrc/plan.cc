@@ -152,8 +152,22 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
     const bool use_triples = o.opt_level == kOptTriple && triples <= 8000000;
     std::unique_ptr<RepairTrace> rt;
     std::unique_ptr<TripleTrace> tt;
-    if (use_triples) tt = std::make_unique<TripleTrace>(chains);
-    else rt = std::make_unique<RepairTrace>(chains, o.opt_level != kOptRePair);
+    if (use_triples) {
+      tt = std::make_unique<TripleTrace>(chains);
+    } else {
+      // With the automatic budget only the first temporals can fit the
+      // register budget: run a prefix of reg_budget temporals first (the run
+      // is deterministic, so it is the complete run's prefix) and the
+      // complete run only if every temporal of the prefix fits.
+      const bool xc = o.opt_level != kOptRePair;
+      const int cap = o.max_temps == -2 ? o.reg_budget : (o.max_temps >= 0 ? o.max_temps : -1);
+      rt = std::make_unique<RepairTrace>(chains, xc, cap);
+      if (!rt->complete() && o.max_temps == -2) {
+        Slp f = fuse(rt->at(rt->n_temps()), o.cancel_pairs);
+        if (max_live_preloaded(f, schedule_dfs(f, false)) <= o.reg_budget)
+          rt = std::make_unique<RepairTrace>(chains, xc);
+      }
+    }
     auto at = [&](int x) { return use_triples ? tt->at(x) : rt->at(x); };
     int b = use_triples ? tt->n_temps() : rt->n_temps();
     const int all = b;

@@ -311,7 +311,7 @@ struct Ranker {
 // temporal, so the program after b temporals (a budget) is a prefix of this
 // run; the run records the definition changes of every iteration so that
 // any prefix can be rebuilt without running the algorithm again.
-RepairTrace::RepairTrace(const Slp& in, bool xor_cancel)
+RepairTrace::RepairTrace(const Slp& in, bool xor_cancel, int max_temps)
     : nc_(in.n_const), const_names_(in.const_names) {
   const int nc = nc_;
   const Ranker rk{nc};
@@ -408,6 +408,10 @@ RepairTrace::RepairTrace(const Slp& in, bool xor_cancel)
     bool any = false;
     for (int o = 0; o < n_orig; ++o) any |= active[o] != 0;
     if (!any) break;
+    if (max_temps >= 0 && static_cast<int>(tdef_.size()) >= max_temps) {
+      complete_ = false;
+      break;
+    }
     // Terms present in active definitions, in term order.
     std::vector<int> present;
     for (int t = 0; t < static_cast<int>(occ.size()); ++t)

@@ -99,8 +99,12 @@ Slp repair(const Slp& p, bool xor_cancel, int max_temps = -1);
 // first b iterations of the run.
 class RepairTrace {
  public:
-  RepairTrace(const Slp& p, bool xor_cancel);
+  // max_temps >= 0 stops the run after that many temporals (the run is
+  // deterministic, so this is a prefix of the complete run); complete()
+  // says whether the run ended on its own.
+  RepairTrace(const Slp& p, bool xor_cancel, int max_temps = -1);
   int n_temps() const { return static_cast<int>(tdef_.size()); }
+  bool complete() const { return complete_; }
   Slp at(int b) const;   // program after b temporals (b >= n_temps: all)
 
  private:
@@ -109,6 +113,7 @@ class RepairTrace {
   std::vector<std::vector<int>> init_;                        // initial definitions
   std::vector<std::pair<int, int>> tdef_;                     // temporal i = (x, y)
   std::vector<std::vector<std::pair<int, std::vector<int>>>> changes_;  // per iteration
+  bool complete_ = true;
 };
 
 // Triple compression: the RePair idea (Sec. 4.3) with triples of terms in
