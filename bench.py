@@ -75,6 +75,12 @@ def parse_args():
                     help="comma-separated block ids erased in every decode stripe (e.g. 2,4,5,6, "
                          "the paper's P_dec)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--stream-temps", type=int, default=0,
+                    help="codes with more than 12 data blocks: XorRePair temporals per input "
+                         "window of the two-level program (0 = automatic, -1 = none)")
+    ap.add_argument("--codes", default="",
+                    help="--workload codes: comma-separated KxM list in place of the paper's "
+                         "RS(8..10, 2..4), e.g. 16x4,20x4,32x4")
     return ap.parse_args()
 
 
@@ -576,8 +582,10 @@ def run_codes(args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / reps
 
+    codes = [tuple(int(x) for x in c.split("x")) for c in args.codes.split(",")] if args.codes \
+        else CODES
     rows, all_ok = [], True
-    for (k, m) in CODES:
+    for (k, m) in codes:
         data = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
         par = torch.empty((n, m, B), dtype=torch.uint8, device="cuda")
         rec = torch.empty((n, m, B), dtype=torch.uint8, device="cuda")
@@ -586,7 +594,8 @@ def run_codes(args):
                 xo.ec_synth_fill(data[s, j].data_ptr(), B, synth.block_seed(6, s, j), 0, sp)
         er = list(range(m))
         for name in ("cauchy", "cauchy_min"):
-            plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, name))
+            plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, name),
+                                        stream_temps=args.stream_temps)
             ms_enc = timed(lambda: xo.ec_encode_strided(plan, data.data_ptr(), k * B, B, par.data_ptr(),
                                                         m * B, B, n, B, sp))
             jobs = []
@@ -621,18 +630,21 @@ def run_codes(args):
                 "decode_frac": round(n * (k + m) * B / (ms_dec / 1e3) / 1e9 / peak, 4),
                 "enc_xors_raw": ie["raw"]["xors"], "enc_xors_fused": ie["fused"]["xors"],
                 "dec_xors_raw": idd["raw"]["xors"], "dec_xors_fused": idd["fused"]["xors"],
+                "enc_lop3": ie["lop3"], "enc_compiled": ie["compiled"], "enc_regs": ie["regs"],
+                "enc_threads": ie["threads"], "enc_window_temps": ie["window_temps"],
                 "parity": "bit-exact on sampled windows" if ok else "MISMATCH"})
             xo.ec_plan_destroy(plan)
         del data, par, rec
         torch.cuda.empty_cache()
-    head = next(r for r in rows if r["code"] == "RS(10,4)" and r["matrix"] == "cauchy")
+    head = next((r for r in rows if r["code"] == "RS(10,4)" and r["matrix"] == "cauchy"), rows[0])
     print(json.dumps({
         "metric": METRIC, "value": head["encode_GBps"], "unit": "GB/s", "n_gpus": 1,
         "steps": reps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (SplitMix64 bytes generated on the device)",
-        "config": {"workload": f"codes RS(8..10, 2..4), {n} stripes x d x 1 MiB, Cauchy and scaled "
-                               "Cauchy; decode erases data blocks 0..p-1",
+        "config": {"workload": f"codes {', '.join(f'RS({k},{m})' for k, m in codes)}, {n} stripes "
+                               "x d x 1 MiB, Cauchy and scaled Cauchy; decode erases data blocks "
+                               "0..p-1",
                    "l2": "inputs larger than L2 (129 MB); no flush"},
         "codes": rows,
         "parity": "bit-exact on sampled windows" if all_ok else "MISMATCH",

@@ -106,6 +106,22 @@ typedef struct {
                            bounding the registers the program needs          */
   int reg_budget;       /* registers per thread the automatic budget aims at
                            (all input words preloaded); 0 = 128             */
+  int stream_window;    /* codes with more than 96 input strips (12 data
+                           blocks) and automatic temporaries: the input words
+                           do not fit the registers, so the program is
+                           two-level (Sec. 8's multilevel pebble game): rows
+                           in groups of partial sums that fit reg_budget,
+                           inputs in windows of this many strips, each input
+                           word read from the shared-memory tile once per
+                           group, two inputs per three-input XOR.  0 =
+                           automatic (32), -1 = off (one fused statement per
+                           row, operands read from shared memory at every
+                           use), > 0 = explicit                            */
+  int stream_temps;     /* two-level programs: XorRePair temporals per window
+                           (Sec. 4.4 on each window's part of the rows, then
+                           fusion); 0 = automatic (the planner tries 0, 8,
+                           16 and 32 and keeps the cheapest that fits the
+                           registers), -1 = none, > 0 = explicit            */
 } ec_plan_opts;
 
 /* Create a plan for RS(k,m).  matrix: m*k row-major parity rows, or NULL for
@@ -142,11 +158,17 @@ typedef struct {
   int compiled;         /* 1 if a compiled straight-line kernel exists        */
   int regs;             /* registers per thread of the compiled kernel        */
   int temps;            /* temporaries kept by (Xor)RePair                    */
-  int max_live;         /* values live at once with inputs preloaded          */
+  int max_live;         /* values live at once (inputs preloaded; two-level
+                           programs: inputs live within their group)         */
   int threads;          /* threads per CTA of the compiled tier (strip tile =
                            4 x threads bytes): the plan's launch shape        */
   int lop3;             /* three-input XOR instructions of the fused program:
                            sum over statements of ceil((arity - 1) / 2)       */
+  int loads;            /* input words a thread reads from the shared-memory
+                           tile per tile: n_in when preloaded, once per group
+                           for two-level programs, at every use otherwise     */
+  int window;           /* input window of a two-level program, else 0       */
+  int window_temps;     /* XorRePair temporals per window (two-level)        */
 } ec_program_info;
 
 /* Program of the encoder (erasures == NULL) or of the decoder for the given

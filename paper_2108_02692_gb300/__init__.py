@@ -92,10 +92,12 @@ def ec_plan_create(k: int, m: int, matrix=None) -> int:
 def ec_plan_create_ex(k: int, m: int, matrix_kind: int = EC_MATRIX_CAUCHY, matrix=None,
                       opt_level: int = EC_OPT_XORREPAIR, sched: int = EC_SCHED_DFS,
                       greedy_cap: int = 128, executor: int = EC_EXEC_AUTO,
-                      max_temps: int = -2, reg_budget: int = 0) -> int:
+                      max_temps: int = -2, reg_budget: int = 0, stream_window: int = 0,
+                      stream_temps: int = 0) -> int:
     h = ctypes.c_void_p()
     keep = _u8(matrix)
-    opts = _abi.PlanOpts(opt_level, sched, greedy_cap, executor, max_temps, reg_budget)
+    opts = _abi.PlanOpts(opt_level, sched, greedy_cap, executor, max_temps, reg_budget,
+                         stream_window, stream_temps)
     _check(lib().ec_plan_create_ex(k, m, matrix_kind, keep[1] if keep else None,
                                    ctypes.byref(opts), ctypes.byref(h)))
     return h.value
@@ -126,7 +128,8 @@ def ec_plan_info(plan: int, erasures=None) -> dict:
             "raw": _stats(info.raw), "compressed": _stats(info.compressed),
             "fused": _stats(info.fused), "compiled": bool(info.compiled), "regs": info.regs,
             "temps": info.temps, "max_live": info.max_live, "threads": info.threads,
-            "lop3": info.lop3}
+            "lop3": info.lop3, "loads": info.loads, "window": info.window,
+            "window_temps": info.window_temps}
 
 
 def ec_plan_program(plan: int, erasures=None) -> np.ndarray:

@@ -37,7 +37,8 @@ EC_EXEC_AUTO, EC_EXEC_INTERP, EC_EXEC_COMPILED = 0, 1, 2
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("opt_level", c_int), ("sched", c_int), ("greedy_cap", c_int),
-                ("executor", c_int), ("max_temps", c_int), ("reg_budget", c_int)]
+                ("executor", c_int), ("max_temps", c_int), ("reg_budget", c_int),
+                ("stream_window", c_int), ("stream_temps", c_int)]
 
 
 class SlpStats(ctypes.Structure):
@@ -48,7 +49,8 @@ class ProgramInfo(ctypes.Structure):
     _fields_ = [("n_in", c_int), ("n_out", c_int), ("slots", c_int), ("stmts", c_int),
                 ("code_words", c_int), ("sched_nvar", c_int), ("raw", SlpStats),
                 ("compressed", SlpStats), ("fused", SlpStats), ("compiled", c_int),
-                ("regs", c_int), ("temps", c_int), ("max_live", c_int), ("threads", c_int), ("lop3", c_int)]
+                ("regs", c_int), ("temps", c_int), ("max_live", c_int), ("threads", c_int), ("lop3", c_int),
+                ("loads", c_int), ("window", c_int), ("window_temps", c_int)]
 
 
 EC_OP_ENCODE, EC_OP_DECODE = 0, 1

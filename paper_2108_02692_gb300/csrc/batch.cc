@@ -38,7 +38,13 @@ int env_int(const char* name, int dflt) {
 // Threads per CTA of batched launches (tile = 4 * threads bytes per strip)
 // and the occupancy the compiled modules are built for.
 int batch_threads() { return env_int("EC_BATCH_THREADS", 128); }
-int batch_minb() { return env_int("EC_BATCH_MINB", 512 / batch_threads()); }
+// Default module shape for programs of n_in input strips: EC_BATCH_THREADS,
+// else 128 threads halved while two CTAs' tiles do not fit.
+int batch_threads_for(int n_in) {
+  const int th = env_int("EC_BATCH_THREADS", 0);
+  return th > 0 ? th : xorec::tile_threads_for_inputs(n_in, 128);
+}
+int batch_minb_for(int n_in) { return env_int("EC_BATCH_MINB", 512 / batch_threads_for(n_in)); }
 
 struct Launch {
   void* mod = nullptr;                 // compiled module, or nullptr = interpreter
@@ -180,12 +186,12 @@ ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
 // Launch shape of a plan's compiled modules: the autotuner's choice for the
 // plan (threads per CTA, hence the strip tile of 4 x threads bytes, and
 // resident CTAs per SM, hence the register cap), else the defaults.
-int plan_module_threads(const ec_plan* p) {
-  return p->tuned_threads > 0 ? p->tuned_threads : batch_threads();
+int plan_module_threads(const ec_plan* p, int n_in) {
+  return p->tuned_threads > 0 ? p->tuned_threads : batch_threads_for(n_in);
 }
 
-int plan_module_minb(const ec_plan* p) {
-  return p->tuned_threads > 0 && p->tuned_minb > 0 ? p->tuned_minb : batch_minb();
+int plan_module_minb(const ec_plan* p, int n_in) {
+  return p->tuned_threads > 0 && p->tuned_minb > 0 ? p->tuned_minb : batch_minb_for(n_in);
 }
 
 // Threads per CTA of the launch that runs `prog`: its module's, or the
@@ -204,7 +210,7 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
   std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
   std::vector<Program*> seen;
   for (const auto& w : want) {
-    const int threads = plan_module_threads(w.first);
+    const int threads = plan_module_threads(w.first, w.second->n_in);
     if (!compiled_tier_fits(w.second, threads, di.smem_optin)) continue;   // interpreter
     std::lock_guard<std::mutex> lk(w.first->mu);
     if ((w.second->mod && jit_module_threads(w.second->mod) == threads) ||
@@ -225,7 +231,9 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
   parallel_for(to_compile.size(), [&](size_t i) {
     std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
     ec_plan* plan = to_compile[i].first;
-    mods[i] = jit_compile_module(ps, plan_module_threads(plan), plan_module_minb(plan), &errs[i]);
+    const int n_in = ps.front()->n_in;
+    mods[i] = jit_compile_module(ps, plan_module_threads(plan, n_in), plan_module_minb(plan, n_in),
+                                 &errs[i]);
   });
   if (built) *built = static_cast<int>(to_compile.size());
   for (size_t i = 0; i < to_compile.size(); ++i) {

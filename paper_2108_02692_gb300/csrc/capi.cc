@@ -97,8 +97,24 @@ static std::mutex g_jit_mu;
 
 // The compiled tier runs a program only when one tile of all its input
 // strips fits a CTA's shared memory and the straight-line code stays small
-// enough to compile quickly; everything else goes to the interpreter.
-constexpr long kMaxCompiledMemOps = 65536;
+// enough to compile quickly (kMaxCompiledMemOps); everything else goes to
+// the interpreter.
+
+// Shared memory a CTA may use on sm_103 (opt-in limit).
+constexpr size_t kSmemOptin = 232448;
+
+int tile_threads_for_inputs(int n_in, int threads) {
+  while (threads > 64 &&
+         2 * (static_cast<size_t>(n_in) * 4 * threads + xk::kBatchHeader) > kSmemOptin)
+    threads /= 2;
+  return threads;
+}
+
+int program_threads(const Program* p) {
+  if (p->threads > 0) return p->threads;
+  const int th = env_int("EC_JIT_THREADS", 0);
+  return th > 0 ? th : tile_threads_for_inputs(p->n_in, 128);
+}
 
 bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin) {
   const size_t smem = 128 + static_cast<size_t>(p->n_in) * 4 * threads + xk::kBatchHeader;
@@ -119,6 +135,7 @@ bool jit_ensure(Program* p, int threads, std::string* err) {
   Program tmp;   // compile into a scratch holder, then publish
   tmp.fused = p->fused;
   tmp.sched = p->sched;
+  tmp.load_group = p->load_group;
   tmp.n_in = p->n_in;
   tmp.n_out = p->n_out;
   tmp.minb = p->minb;
@@ -156,33 +173,41 @@ EncodeTiledFn tensor_map_encoder() {
 
 }  // namespace
 
-bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out) {
+int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out) {
   static_assert(sizeof(xk::TensorMap) == sizeof(CUtensorMap), "tensor map size");
-  if (env_int("EC_TMA_TENSOR", 1) == 0) return false;
-  if (io.tab || !io.in_base || io.n_stripes < 1) return false;
+  if (env_int("EC_TMA_TENSOR", 1) == 0) return 0;
+  if (io.tab || !io.in_base || io.n_stripes < 1) return 0;
   const long long S = io.S;
   const uint64_t base = reinterpret_cast<uint64_t>(io.in_base);
   // strips equally spaced by S across the stripe's blocks; 16-byte rules
-  if (n_in < 1 || n_in > 256 || n_in != 8 * io.n_inblk) return false;
-  if (T % 16 != 0 || T / 4 < 4 || T / 4 > 256) return false;
-  if (S <= 0 || S % 16 != 0 || base % 16 != 0 || io.in_bstride != 8 * S) return false;
+  if (n_in < 8 || n_in % 8 != 0 || n_in != 8 * io.n_inblk) return 0;
+  if (T % 16 != 0 || T / 4 < 4 || T / 4 > 256) return 0;
+  if (S <= 0 || S % 16 != 0 || base % 16 != 0 || io.in_bstride != 8 * S) return 0;
   const long long plane = static_cast<long long>(n_in) * S;
   const long long sstride = io.n_stripes > 1 ? io.in_sstride : plane;
-  if (sstride % 16 != 0 || sstride < plane || sstride >= (1ll << 40)) return false;
-  if (S / 4 > 0xffffffffll || io.n_stripes > 0xffffffffll) return false;
+  if (sstride % 16 != 0 || sstride < plane || sstride >= (1ll << 40)) return 0;
+  if (S / 4 > 0xffffffffll || io.n_stripes > 0xffffffffll) return 0;
   const EncodeTiledFn enc = tensor_map_encoder();
-  if (!enc) return false;
+  if (!enc) return 0;
+  // box rows: the largest multiple of 8 strips that divides n_in and fits
+  // a box dimension (256), so that the boxes tile the stage exactly
+  int rows = 8;
+  for (int r = 256; r >= 8; r -= 8)
+    if (n_in % r == 0) {
+      rows = r;
+      break;
+    }
   const cuuint64_t dim[3] = {static_cast<cuuint64_t>(S / 4), static_cast<cuuint64_t>(n_in),
                              static_cast<cuuint64_t>(io.n_stripes)};
   const cuuint64_t stride[2] = {static_cast<cuuint64_t>(S), static_cast<cuuint64_t>(sstride)};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(T / 4), static_cast<cuuint32_t>(n_in), 1};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(T / 4), static_cast<cuuint32_t>(rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r =
       enc(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
           const_cast<uint8_t*>(io.in_base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
+  return r == CUDA_SUCCESS ? rows : 0;
 }
 
 bool block_tensor_map_allowed(const void* block, long long S, int T) {
@@ -215,7 +240,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   bool compiled = false;
   int threads = 0, nstage = 0;
   if (executor != EC_EXEC_INTERP) {
-    threads = p->threads > 0 ? p->threads : env_int("EC_JIT_THREADS", 128);
+    threads = program_threads(p);
     nstage = env_int("EC_JIT_NSTAGE", 1);
     std::string err = "program too large for the compiled tier";
     compiled = compiled_tier_fits(p, threads, di.smem_optin) && jit_ensure(p, threads, &err);
@@ -272,12 +297,12 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   if (grid > lp.n_items) grid = lp.n_items;
   if (compiled) {
     xk::TensorMap tm;
-    lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm) ? 1 : 0;
+    lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm);
     return jit_launch(p, lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem,
                       stream);
   }
   xk::TensorMap tm;
-  lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm) ? 1 : 0;
+  lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm);
   return launch_interp(lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem, stream);
 }
 
@@ -444,6 +469,10 @@ ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix
     if (opts->max_temps < -2) return fail(EC_EINVAL, "bad max_temps");
     plan->opts.max_temps = opts->max_temps;
     plan->opts.reg_budget = opts->reg_budget > 0 ? opts->reg_budget : 128;
+    if (opts->stream_window < -1) return fail(EC_EINVAL, "bad stream_window");
+    plan->opts.stream_window = opts->stream_window;
+    if (opts->stream_temps < -1) return fail(EC_EINVAL, "bad stream_temps");
+    plan->opts.stream_temps = opts->stream_temps;
   }
   plan->enc = std::make_unique<Program>();
   std::string err;
@@ -520,8 +549,11 @@ ec_status ec_plan_info(ec_plan* plan, const int* erasures, int n_erasures, ec_pr
   out->regs = xorec::jit_regs(p);
   out->temps = p->stats.temps;
   out->max_live = p->stats.max_live;
-  out->threads = p->threads > 0 ? p->threads : xorec::env_int("EC_JIT_THREADS", 128);
+  out->threads = xorec::program_threads(p);
   out->lop3 = static_cast<int>(p->stats.lop3);
+  out->loads = static_cast<int>(p->stats.loads);
+  out->window = p->stats.window;
+  out->window_temps = p->stats.window_temps;
   return EC_OK;
 }
 
@@ -670,18 +702,13 @@ ec_status ec_plan_compile(ec_plan* plan, const int* sets, const int* counts, int
   }
   xorec::DeviceInfo di;
   if (!xorec::device_info(&di)) return EC_ECUDA;
-  {
-    const char* v = std::getenv("EC_JIT_THREADS");
-    const int th = v && *v ? std::atoi(v) : 128;
-    progs.erase(std::remove_if(progs.begin(), progs.end(),
-                               [&](Program* p) { return !xorec::compiled_tier_fits(p, th, di.smem_optin); }),
-                progs.end());
-  }
+  progs.erase(std::remove_if(progs.begin(), progs.end(),
+                             [&](Program* p) {
+                               return !xorec::compiled_tier_fits(p, xorec::program_threads(p),
+                                                                 di.smem_optin);
+                             }),
+              progs.end());
   if (n_threads <= 0) n_threads = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
-  const int threads = [] {
-    const char* v = std::getenv("EC_JIT_THREADS");
-    return v && *v ? std::atoi(v) : 128;
-  }();
   std::atomic<size_t> next{0};
   std::atomic<int> rc{EC_OK};
   std::string first_err;
@@ -693,7 +720,7 @@ ec_status ec_plan_compile(ec_plan* plan, const int* sets, const int* counts, int
         const size_t i = next.fetch_add(1);
         if (i >= progs.size()) return;
         std::string err;
-        if (!xorec::jit_ensure(progs[i], threads, &err)) {
+        if (!xorec::jit_ensure(progs[i], xorec::program_threads(progs[i]), &err)) {
           rc.store(EC_ECUDA);
           std::lock_guard<std::mutex> lk(err_mu);
           if (first_err.empty()) first_err = err;

@@ -116,13 +116,22 @@ bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_
 bool jit_available();
 bool jit_ensure(Program* p, int threads, std::string* err);
 bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin);
+// Threads per CTA of a launch whose tile holds n_in input strips when no
+// shape was chosen: `threads`, halved (not below 64) while two CTAs' tiles
+// do not fit one CTA's shared memory, so that an SM keeps at least two CTAs
+// and overlaps one's copies with the other's XORs.
+int tile_threads_for_inputs(int n_in, int threads);
+// Threads per CTA of p's compiled tier: the tuned or pinned shape, else
+// EC_JIT_THREADS, else tile_threads_for_inputs(n_in, 128).
+int program_threads(const Program* p);
 bool jit_compile(Program* p, int threads, std::string* err);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
                 int grid, size_t smem, cudaStream_t stream);
 // Tensor map of a strided launch's inputs as [stripe][input strip][4-byte
-// word] with a box of one tile of every input strip; false (no map) when the
-// layout or the driver does not allow one.
-bool input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out);
+// word] with a box of one tile of up to 256 input strips; returns the strips
+// per box (a multiple of 8 that divides n_in), or 0 (no map) when the layout
+// or the driver does not allow one.
+int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out);
 // Tensor map of one block as [strip][4-byte word] (8 strips S bytes apart)
 // with a box of one tile of its 8 strips; false when not allowed.
 bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out);

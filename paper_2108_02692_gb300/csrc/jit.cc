@@ -24,6 +24,24 @@ const char* kPipelineSrc =
 #include "tile_pipeline_src.inc"
     ;
 
+// XORs of two-level programs as inline PTX: the compiler front end would
+// otherwise reassociate each row's chain of partial sums (its intermediate
+// values have one use) into one expression over all of the row's inputs and
+// load every input at once, which is the register pressure the grouping
+// avoids.
+const char* kOpaqueXorSrc = R"XKSRC(
+__device__ __forceinline__ xk::u32 xk_x3(xk::u32 a, xk::u32 b, xk::u32 c) {
+  xk::u32 d;
+  asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ xk::u32 xk_x2(xk::u32 a, xk::u32 b) {
+  xk::u32 d;
+  asm("xor.b32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+)XKSRC";
+
 struct JitKernel {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kern = nullptr;
@@ -35,23 +53,47 @@ struct JitKernel {
 
 // Straight-line statements of a scheduled program: one SSA register per
 // statement, stores to output strip t of output block b through O(b, t, v)
-// as soon as a returned value is ready.  Inputs come from I(c).
+// as soon as a returned value is ready.  Inputs come from I(c); a two-level
+// program (load groups) reads each input word once per group, into a
+// register named for the input and the group, at its first use there.
 void emit_statements(std::ostringstream& os, const xorec::Program& p) {
   const xorec::Slp& q = p.fused;
   const int nc = q.n_const;
+  const bool grouped = !p.load_group.empty();
+  std::vector<int> loaded(nc, -1);
   std::vector<std::vector<int>> outs_of(q.n_var);
   for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
     if (q.ret[r] >= nc) outs_of[q.ret[r] - nc].push_back(r);
-  for (const auto& st : p.sched.steps) {
+  for (size_t k = 0; k < p.sched.steps.size(); ++k) {
+    const auto& st = p.sched.steps[k];
+    const int g = grouped ? p.load_group[k] : 0;
+    if (grouped)
+      for (int a : st.args)
+        if (a < nc && loaded[a] != g) {
+          os << "    const xk::u32 i" << a << "_" << g << " = I(" << a << ");\n";
+          loaded[a] = g;
+        }
     os << "    const xk::u32 v" << st.node << " = ";
-    if (st.args.empty()) os << "0u";
-    for (size_t i = 0; i < st.args.size(); ++i) {
-      const int a = st.args[i];
-      if (i) os << " ^ ";
-      if (a < nc) os << "I(" << a << ")";
-      else os << "v" << (a - nc);
+    if (grouped && st.args.size() >= 2 && st.args.size() <= 3) {
+      os << (st.args.size() == 3 ? "xk_x3(" : "xk_x2(");
+      for (size_t i = 0; i < st.args.size(); ++i) {
+        const int a = st.args[i];
+        if (i) os << ", ";
+        if (a < nc) os << "i" << a << "_" << g;
+        else os << "v" << (a - nc);
+      }
+      os << ");\n";
+    } else {
+      if (st.args.empty()) os << "0u";
+      for (size_t i = 0; i < st.args.size(); ++i) {
+        const int a = st.args[i];
+        if (i) os << " ^ ";
+        if (a < nc && grouped) os << "i" << a << "_" << g;
+        else if (a < nc) os << "I(" << a << ")";
+        else os << "v" << (a - nc);
+      }
+      os << ";\n";
     }
-    os << ";\n";
     for (int r : outs_of[st.node]) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", v" << st.node << ");\n";
   }
   for (int r = 0; r < static_cast<int>(q.ret.size()); ++r) {
@@ -61,11 +103,6 @@ void emit_statements(std::ostringstream& os, const xorec::Program& p) {
   }
 }
 
-// Programs with more input strips than this read their operands from the
-// shared-memory stage at each use instead of preloading every input word
-// into registers (which would not fit the register file).
-constexpr int kPreloadMaxInputs = 96;
-
 // Single-program body.  Narrow programs (n_in <= kPreloadMaxInputs):
 // load() copies each thread's 4-byte column of every input strip from the
 // stage into registers and compute() runs the statements from registers.
@@ -74,7 +111,7 @@ std::string gen_body(const xorec::Program& p, int threads) {
   const int nc = p.fused.n_const;
   const int T = 4 * threads;
   std::ostringstream os;
-  if (nc > kPreloadMaxInputs) {
+  if (nc > xorec::kPreloadMaxInputs) {
     os << "struct SlpBody {\n"
           "  static constexpr bool kEarlyRelease = false;\n"
           "  __device__ __forceinline__ void operator()(const xk::LaunchParams& p, xk::i64 s,\n"
@@ -136,10 +173,13 @@ std::string gen_module_source(const std::vector<const xorec::Program*>& progs, i
     emit_statements(os, *progs[i]);
     os << "#undef I\n#undef O\n}\n";
   }
-  if (nc > kPreloadMaxInputs) {
+  if (nc > xorec::kPreloadMaxInputs) {
     // wide programs: operands from the stage at each use
     std::ostringstream ws;
     ws << kPipelineSrc << "\n";
+    if (std::any_of(progs.begin(), progs.end(),
+                    [](const xorec::Program* q) { return !q->load_group.empty(); }))
+      ws << kOpaqueXorSrc;
     for (size_t i = 0; i < progs.size(); ++i) {
       ws << "__device__ __forceinline__ void prog_" << i
          << "(const xk::StripeDesc& d, xk::i64 c0, int col, const xk::u8* in) {\n"
@@ -210,6 +250,7 @@ int env_or(const char* name, int dflt) {
 std::string gen_source(const xorec::Program& p, int threads) {
   std::ostringstream os;
   os << kPipelineSrc << "\n";
+  if (!p.load_group.empty()) os << kOpaqueXorSrc;
   os << gen_body(p, threads);
   os << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
      << (p.minb > 0 ? p.minb : env_or("EC_JIT_MINB", std::max(1, 512 / threads)))

@@ -134,7 +134,50 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   Program p;
   p.stats.raw = metrics(chains);
   Slp fused;
-  if (o.opt_level == kOptRaw) {
+  // Two-level program for wide codes (inputs do not fit the registers):
+  // groups of partial sums as large as the register budget allows.
+  bool two_level = false;
+  Schedule stream_sched;
+  if (n_in > kPreloadMaxInputs && o.stream_window >= 0 &&
+      (o.opt_level == kOptRaw || o.max_temps == -2)) {
+    const int window = o.stream_window > 0 ? o.stream_window : 32;
+    // candidates: temporals per window x rows per group (halved from all
+    // rows); each keeps the values live within reg_budget - 32 (addresses
+    // and loop state need the rest), and the cheapest by three-input XORs
+    // plus twice the shared-memory loads (the narrower pipe) wins
+    std::vector<int> temps_c;
+    if (o.stream_temps > 0) temps_c = {o.stream_temps};
+    else if (o.stream_temps < 0) temps_c = {0};
+    else temps_c = {0, 8, 16, 32};
+    long best_cost = -1;
+    for (int wt : temps_c) {
+      for (int rows_per_group = n_out;; rows_per_group = (rows_per_group + 1) / 2) {
+        std::vector<int> group;
+        long loads = 0;
+        Slp st = slp_rows_stream(n_in, R, window, rows_per_group, &group, wt);
+        Schedule sc = schedule_in_order(st, false);
+        const int live = max_live_grouped(st, sc, group, &loads);
+        if (live + 32 <= o.reg_budget || rows_per_group <= 8) {
+          const long cost = lop3_count(st) + 2 * loads;
+          if (metrics(st).mem <= kMaxCompiledMemOps && (best_cost < 0 || cost < best_cost)) {
+            best_cost = cost;
+            two_level = true;
+            fused = std::move(st);
+            stream_sched = std::move(sc);
+            p.load_group = std::move(group);
+            p.stats.max_live = live;
+            p.stats.loads = loads;
+            p.stats.window = window;
+            p.stats.window_temps = wt;
+          }
+          break;
+        }
+      }
+    }
+  }
+  if (two_level) {
+    p.stats.compressed = p.stats.raw;
+  } else if (o.opt_level == kOptRaw) {
     fused = slp_rows_fused(n_in, R, order);
     p.stats.compressed = p.stats.raw;
   } else if (o.max_temps == -2 && n_in >= o.reg_budget) {
@@ -199,13 +242,27 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
     *err = "internal: optimised program is not equivalent to the bitmatrix";
     return false;
   }
-  Schedule paper = o.sched == kSchedGreedy ? schedule_greedy(fused, o.greedy_cap, true)
-                                           : schedule_dfs(fused, true);
-  p.stats.sched_nvar = paper.n_pebbles;
-  Schedule gpu = o.sched == kSchedGreedy ? schedule_greedy(fused, o.greedy_cap, false)
-                                         : schedule_dfs(fused, false);
+  Schedule gpu;
+  if (two_level) {
+    // the statements are already in the order of the two-level game
+    p.stats.sched_nvar = schedule_in_order(fused, true).n_pebbles;
+    gpu = std::move(stream_sched);
+  } else {
+    Schedule paper = o.sched == kSchedGreedy ? schedule_greedy(fused, o.greedy_cap, true)
+                                             : schedule_dfs(fused, true);
+    p.stats.sched_nvar = paper.n_pebbles;
+    gpu = o.sched == kSchedGreedy ? schedule_greedy(fused, o.greedy_cap, false)
+                                  : schedule_dfs(fused, false);
+    p.stats.max_live = max_live_preloaded(fused, gpu);
+    // inputs preloaded once, or (wide programs) read at every use
+    if (n_in <= kPreloadMaxInputs) {
+      p.stats.loads = n_in;
+    } else {
+      for (const auto& st : fused.body)
+        for (int a : st.args) p.stats.loads += a < n_in;
+    }
+  }
   p.stats.slots = gpu.n_pebbles;
-  p.stats.max_live = max_live_preloaded(fused, gpu);
   if (!lower(fused, gpu, n_in, n_out, &p, err)) return false;
   if (!check_program_stream(p.code.data(), p.code.size(), n_in, n_out, p.n_slots, err))
     return false;

@@ -16,6 +16,14 @@ namespace xorec {
 // bit s of A[i][j] * 2^t (Sec. 1, property (ii)).
 std::vector<Bits> bitmatrix_rows(int rows, int cols, const uint8_t* A);
 
+// Programs with more input strips than this do not preload every input word
+// into registers: their compiled body reads operands from the shared-memory
+// stage.
+constexpr int kPreloadMaxInputs = 96;
+// Largest program (#_M memory operations) the compiled tier takes, so that
+// NVRTC compiles it in seconds.
+constexpr long kMaxCompiledMemOps = 65536;
+
 enum OptLevel { kOptRaw = 0, kOptRePair = 1, kOptXorRePair = 2, kOptTriple = 3 };
 enum SchedKind { kSchedDfs = 0, kSchedGreedy = 1 };
 
@@ -27,6 +35,9 @@ struct PipelineStats {
   int temps = 0;           // temporaries kept by (Xor)RePair
   int max_live = 0;        // registers with all inputs preloaded
   long lop3 = 0;           // three-input XOR instructions of the fused program
+  long loads = 0;          // input words a thread loads from the stage per tile
+  int window = 0;          // input window of a two-level program (0 = not one)
+  int window_temps = 0;    // XorRePair temporals per window of a two-level program
 };
 
 // An executable program for one linear map from n_in input strips to n_out
@@ -43,6 +54,10 @@ struct Program {
   PipelineStats stats;
   Slp fused;                 // single-assignment fused program
   Schedule sched;            // GPU schedule of `fused`
+  // two-level programs (slp_rows_stream): load group of each schedule step;
+  // the compiled body loads an input word at its first use in a group.
+  // Empty: inputs preloaded (narrow) or read at every use (wide).
+  std::vector<int> load_group;
   uint64_t hash = 0;         // content hash of the fused program
   // device copy of `code` (owned; freed by the plan)
   uint16_t* d_code = nullptr;
@@ -66,6 +81,13 @@ struct PlanOptions {
   // registers with all inputs preloaded), >= 0 = explicit.
   int max_temps = -2;
   int reg_budget = 128;
+  // Programs with more than kPreloadMaxInputs inputs and automatic
+  // temporaries: input window of the two-level program (0 = automatic,
+  // -1 = off: one fused statement per row, operands read at every use).
+  int stream_window = 0;
+  // XorRePair temporals per window of a two-level program (0 = automatic,
+  // -1 = none, > 0 = explicit).
+  int stream_temps = 0;
 };
 
 // Build the program for the linear map A (rows x cols over GF(2^8)).

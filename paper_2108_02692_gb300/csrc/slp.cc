@@ -293,6 +293,121 @@ Slp slp_rows_chains(int n_const, const std::vector<Bits>& rows,
   return p;
 }
 
+Slp slp_rows_stream(int n_const, const std::vector<Bits>& rows, int window, int group_rows,
+                    std::vector<int>* stmt_group, int window_temps) {
+  Slp p;
+  p.n_const = n_const;
+  const int n_rows = static_cast<int>(rows.size());
+  p.ret.assign(n_rows, -1);
+  stmt_group->clear();
+  if (window < 1) window = 1;
+  if (group_rows < 1) group_rows = 1;
+  std::vector<int> acc(n_rows, -1);   // current partial sum of each row
+  auto add = [&](int g, std::vector<int> args) {
+    const int v = n_const + p.n_var++;
+    p.body.push_back(Stmt{v, std::move(args)});
+    stmt_group->push_back(g);
+    return v;
+  };
+  // acc <- acc + XOR(args) as a chain of three-input statements; a row's
+  // first statement (acc < 0) takes up to three arguments
+  auto chain = [&](int g, const std::vector<int>& args, int start) {
+    size_t i = 0;
+    int cur = start;
+    if (cur < 0) {
+      const size_t n = std::min<size_t>(3, args.size());
+      cur = add(g, std::vector<int>(args.begin(), args.begin() + n));
+      i = n;
+    }
+    for (; i < args.size(); i += 2) {
+      std::vector<int> a{cur, args[i]};
+      if (i + 1 < args.size()) a.push_back(args[i + 1]);
+      cur = add(g, a);
+    }
+    return cur;
+  };
+  for (int g = 0, r0 = 0; r0 < n_rows; ++g, r0 += group_rows) {
+    const int r1 = std::min(n_rows, r0 + group_rows);
+    for (int c0 = 0; c0 < n_const; c0 += window) {
+      const int c1 = std::min(n_const, c0 + window);
+      if (window_temps > 0) {
+        // the group's rows restricted to the window form a small MultiSLP;
+        // XorRePair (at most window_temps temporals) and fusion shorten it
+        const int wn = c1 - c0;
+        std::vector<int> rid;
+        std::vector<Bits> sub;
+        for (int r = r0; r < r1; ++r) {
+          Bits b(wn);
+          bool any = false;
+          for (int c = c0; c < c1; ++c)
+            if (rows[r].test(c)) {
+              b.set(c - c0);
+              any = true;
+            }
+          if (any) {
+            rid.push_back(r);
+            sub.push_back(b);
+          }
+        }
+        if (rid.empty()) continue;
+        std::vector<int> ord(rid.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = static_cast<int>(i);
+        RepairTrace rt(slp_rows_chains(wn, sub, ord), true, window_temps);
+        const Slp f = fuse(rt.at(rt.n_temps()), true);
+        std::vector<int> val(f.n_var, -1), users(f.n_var, 0), n_goal(f.n_var, 0),
+            goal_row(f.n_var, -1);
+        for (const Stmt& st : f.body)
+          for (int a : st.args)
+            if (a >= wn) users[a - wn] += 1;
+        for (size_t i = 0; i < f.ret.size(); ++i)
+          if (f.ret[i] >= wn) {
+            n_goal[f.ret[i] - wn] += 1;
+            goal_row[f.ret[i] - wn] = rid[i];
+          }
+        auto folded = [&](int v) { return n_goal[v] == 1 && users[v] == 0; };
+        for (const Stmt& st : f.body) {
+          const int v = st.dst - wn;
+          std::vector<int> args;
+          for (int a : st.args) args.push_back(a < wn ? c0 + a : val[a - wn]);
+          if (folded(v)) {
+            // one row's part with no other use: straight into its partial sum
+            const int r = goal_row[v];
+            acc[r] = chain(g, args, acc[r]);
+          } else {
+            val[v] = chain(g, args, -1);
+          }
+        }
+        for (size_t i = 0; i < f.ret.size(); ++i) {
+          const int t = f.ret[i], r = rid[i];
+          if (t < 0 || (t >= wn && folded(t - wn))) continue;
+          const int term = t < wn ? c0 + t : val[t - wn];
+          acc[r] = acc[r] < 0 && t >= wn ? term : chain(g, {term}, acc[r]);
+        }
+        continue;
+      }
+      for (int r = r0; r < r1; ++r) {
+        std::vector<int> cs;
+        for (int c = c0; c < c1; ++c)
+          if (rows[r].test(c)) cs.push_back(c);
+        size_t i = 0;
+        if (acc[r] < 0 && !cs.empty()) {
+          // the first statement of a row takes up to three inputs
+          const size_t n = std::min<size_t>(3, cs.size());
+          acc[r] = add(g, std::vector<int>(cs.begin(), cs.begin() + n));
+          i = n;
+        }
+        for (; i < cs.size(); i += 2) {
+          std::vector<int> args{acc[r], cs[i]};
+          if (i + 1 < cs.size()) args.push_back(cs[i + 1]);
+          acc[r] = add(g, args);
+        }
+      }
+    }
+  }
+  for (int r = 0; r < n_rows; ++r) p.ret[r] = acc[r];
+  return p;
+}
+
 // --------------------------------------------------- RePair / XorRePair
 
 namespace {
@@ -760,21 +875,12 @@ std::vector<int> distinct_vars(const std::vector<int>& args, int nc) {
 
 }  // namespace
 
-Schedule schedule_dfs(const Slp& p, bool goals_hold) {
-  Graph g = build_graph(p);
+// Pebbles for the statements of g taken in `order`: a pebble is given back
+// when the last parent of its node has been computed (goals keep theirs when
+// goals_hold), and a new node takes the pebble of the most recently computed
+// dead node.
+static Schedule assign_pebbles(const Graph& g, const std::vector<int>& order, bool goals_hold) {
   const int nc = g.nc;
-  std::vector<int> order;
-  std::vector<char> visited(g.nv, 0);
-  std::function<void(int)> visit = [&](int v) {
-    if (visited[v]) return;
-    visited[v] = 1;
-    for (int a : g.kids[v])
-      if (a >= nc) visit(a - nc);
-    order.push_back(v);
-  };
-  for (int v = 0; v < g.nv; ++v)  // roots in term order
-    if (g.def_idx[v] >= 0 && g.n_parents[v] == 0) visit(v);
-
   Schedule s;
   std::vector<int> remaining = g.n_parents, pebble(g.nv, -1), when(g.nv, -1);
   std::vector<std::pair<int, int>> free_list;  // (time its node was computed, pebble)
@@ -803,6 +909,30 @@ Schedule schedule_dfs(const Slp& p, bool goals_hold) {
     s.steps.push_back(Schedule::Step{n, peb, g.kids[n]});
   }
   return s;
+}
+
+Schedule schedule_dfs(const Slp& p, bool goals_hold) {
+  Graph g = build_graph(p);
+  const int nc = g.nc;
+  std::vector<int> order;
+  std::vector<char> visited(g.nv, 0);
+  std::function<void(int)> visit = [&](int v) {
+    if (visited[v]) return;
+    visited[v] = 1;
+    for (int a : g.kids[v])
+      if (a >= nc) visit(a - nc);
+    order.push_back(v);
+  };
+  for (int v = 0; v < g.nv; ++v)  // roots in term order
+    if (g.def_idx[v] >= 0 && g.n_parents[v] == 0) visit(v);
+  return assign_pebbles(g, order, goals_hold);
+}
+
+Schedule schedule_in_order(const Slp& p, bool goals_hold) {
+  Graph g = build_graph(p);
+  std::vector<int> order;
+  for (const auto& st : p.body) order.push_back(st.dst - p.n_const);
+  return assign_pebbles(g, order, goals_hold);
 }
 
 Schedule schedule_greedy(const Slp& p, int cap, bool goals_hold) {
@@ -912,6 +1042,53 @@ int max_live_preloaded(const Slp& q, const Schedule& s) {
       }
     }
   }
+  return peak;
+}
+
+int max_live_grouped(const Slp& q, const Schedule& s, const std::vector<int>& group,
+                     long* loads) {
+  const int nc = q.n_const;
+  const size_t n = s.steps.size();
+  // an input is live from its first to its last use within a group; a
+  // variable from its statement to its last use
+  std::vector<int> last_v(q.n_var, -1);
+  std::vector<std::vector<int>> in_end(n);   // inputs whose group-range ends at step i
+  std::vector<int> in_start(n, 0);
+  std::vector<int> first(nc, -1), last(nc, -1), seen_group(nc, -1);
+  long nload = 0;
+  auto close = [&](int c) {
+    if (first[c] >= 0) in_end[last[c]].push_back(c);
+    first[c] = last[c] = -1;
+  };
+  for (size_t i = 0; i < n; ++i) {
+    const int g = i < group.size() ? group[i] : 0;
+    for (int a : s.steps[i].args) {
+      if (a >= nc) {
+        last_v[a - nc] = static_cast<int>(i);
+        continue;
+      }
+      if (seen_group[a] != g) {
+        close(a);
+        seen_group[a] = g;
+        first[a] = static_cast<int>(i);
+        ++in_start[i];
+        ++nload;
+      }
+      last[a] = static_cast<int>(i);
+    }
+  }
+  for (int c = 0; c < nc; ++c) close(c);
+  int live = 0, peak = 0;
+  for (size_t i = 0; i < n; ++i) {
+    live += in_start[i];
+    const int v = s.steps[i].node;
+    peak = std::max(peak, live + 1);   // the result is written while operands are live
+    if (last_v[v] > static_cast<int>(i)) ++live;
+    live -= static_cast<int>(in_end[i].size());
+    for (int a : distinct_vars(s.steps[i].args, nc))
+      if (last_v[a - nc] == static_cast<int>(i)) --live;
+  }
+  if (loads) *loads = nload;
   return peak;
 }
 

@@ -85,6 +85,25 @@ Slp slp_rows_fused(int n_const, const std::vector<Bits>& rows,
 Slp slp_rows_chains(int n_const, const std::vector<Bits>& rows,
                     const std::vector<int>& row_order);
 
+// Two-level program for rows whose input words do not all fit the
+// registers: the multilevel pebble game named as future work in Sec. 8, with
+// the registers as the first level and the shared-memory tile of the inputs
+// (Sec. 6.1's blocking) as the second.  Rows are taken in groups of
+// group_rows partial sums and the inputs in windows of `window` columns; for
+// each group and window, every row of the group adds the window's inputs it
+// contains, two per statement (acc <- acc + a + b, one three-input XOR; a
+// row's first statement takes up to three inputs).  Within a group every
+// input is needed in one window only, so it is loaded once per group.
+// Single assignment, not fused (fusion would merge each row back into one
+// statement that needs all its inputs at once).  stmt_group receives the
+// group of each statement.
+// window_temps > 0: the group's rows restricted to each window are first
+// shortened by XorRePair with at most window_temps temporals, and fusion
+// (Sec. 4.4, Sec. 5.2); temporals live within their window, and a row's
+// fused window part is added into its partial sum.
+Slp slp_rows_stream(int n_const, const std::vector<Bits>& rows, int window, int group_rows,
+                    std::vector<int>* stmt_group, int window_temps = 0);
+
 // RePair (xor_cancel = false) or XorRePair (true) on the flattened
 // semantics of p.  Returns a single-assignment program of binary
 // temporals; returned terms become the temporal, constant or zero that
@@ -169,6 +188,17 @@ Schedule schedule_greedy(const Slp& p, int cap, bool goals_hold);
 // from their statement until their last use (Sec. 6.2's cache capacity with
 // the register file as the cache and no reloading).
 int max_live_preloaded(const Slp& q, const Schedule& s);
+
+// The schedule that computes p's statements in program order (p single
+// assignment), pebbles assigned as in schedule_dfs.
+Schedule schedule_in_order(const Slp& p, bool goals_hold);
+// Registers a thread needs to run schedule s of q when an input word is
+// loaded at its first use in each group (group[i] = group of step i) and kept
+// until its last use in that group; *loads receives the number of input
+// loads.  With one group this is the single-level game with inputs loaded on
+// first use and never evicted.
+int max_live_grouped(const Slp& q, const Schedule& s, const std::vector<int>& group,
+                     long* loads);
 
 // The program of a schedule, with variables renamed to pebbles.  Requires
 // goals_hold schedules so that returned values are still on their pebble.

@@ -53,9 +53,10 @@ struct LaunchParams {
   int n_in, n_out;       // input / output strips (8 per block)
   int T;                 // tile bytes per strip (multiple of 16)
   int nstage;            // stages in the shared-memory ring
-  int tmap;              // 1: the kernel's tensor map describes the inputs as
-                         // [stripe][input strip][4-byte word] and one 3-D
-                         // copy fills a stage
+  int tmap;              // > 0: the kernel's tensor map describes the inputs
+                         // as [stripe][input strip][4-byte word] with boxes
+                         // of tmap strips (tmap divides n_in), and n_in/tmap
+                         // 3-D copies fill a stage; 0: per-strip copies
   i64 tiles_per_strip;
   i64 n_items;
   const u16* code;       // interpreter stream (unused by compiled kernels)
@@ -193,11 +194,21 @@ __device__ __forceinline__ void issue_item(const LaunchParams& p, const TensorMa
   const i64 s = item / p.tiles_per_strip;
   const i64 c0 = (item % p.tiles_per_strip) * p.T;
   const int lane = threadIdx.x & 31;
-  if (p.tmap) {
+  if (p.tmap == p.n_in) {
     if (lane == 0) {
       mbar_arrive_expect_tx(bar, static_cast<u32>(p.n_in) * static_cast<u32>(p.T));
       tma_load_3d(smem_addr(dst), tm, static_cast<int>(c0 >> 2), 0, static_cast<int>(s), bar);
     }
+    return;
+  }
+  if (p.tmap > 0) {
+    // more strips than one box holds: one copy per box of tmap strips,
+    // spread over the warp's lanes
+    if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(p.n_in) * static_cast<u32>(p.T));
+    __syncwarp();
+    for (int y = lane * p.tmap; y < p.n_in; y += 32 * p.tmap)
+      tma_load_3d(smem_addr(dst + static_cast<i64>(y) * p.T), tm, static_cast<int>(c0 >> 2), y,
+                  static_cast<int>(s), bar);
     return;
   }
   const i64 rest = p.io.S - c0;

@@ -1,9 +1,10 @@
 """TMA tensor copies against per-strip bulk copies: the same bytes, both
 equal to the oracle.  EC_TMA_TENSOR=0 makes the library stage every input
 strip with its own 1-D copy; covered: strided launches (one 3-D copy per
-tile), the largest box (32 data blocks = 256 strips), the fallback past it,
-ragged strip tails (zero-filled boxes), and batches (one 2-D copy per input
-block and tile)."""
+tile), the largest box (32 data blocks = 256 strips), stages of more strips
+than a box holds (several boxes per tile, down to 8 strips per box when k is
+prime), ragged strip tails (zero-filled boxes), and batches (one 2-D copy
+per input block and tile)."""
 import os
 
 import numpy as np
@@ -39,7 +40,10 @@ class tensor_copies:
 
 @pytest.mark.parametrize("k,m,B,n", [(10, 4, 8 * 1552, 5),     # ragged tail (1552 = 3 x 512 + 16)
                                      (32, 4, 8 * 528, 3),      # box of 256 strips
-                                     (40, 4, 8 * 528, 2),      # too many strips: per-strip copies
+                                     (40, 4, 8 * 528, 2),      # two boxes of 160 strips
+                                     (48, 4, 8 * 1552, 2),     # two boxes of 192, ragged tail
+                                     (37, 3, 8 * 528, 2),      # k prime: 37 boxes of 8 strips
+                                     (100, 4, 8 * 400, 2),     # four boxes of 200 strips
                                      (6, 3, 8 * 2048, 4)])
 def test_strided_encode_same_bytes_with_and_without_tensor_copies(k, m, B, n):
     torch.cuda.set_device(0)

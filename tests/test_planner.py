@@ -472,3 +472,110 @@ def test_program_stream_check():
                                 info["slots"])
     finally:
         xo.ec_plan_destroy(plan)
+
+
+def _two_level_lop3(bits, window, group_rows):
+    """Instructions of the two-level program as its construction states it:
+    per group of rows and window of inputs, a row's first statement takes up
+    to three inputs, every later one the partial sum and two inputs."""
+    n_out, n_in = bits.shape
+    total, loads = 0, 0
+    for r0 in range(0, n_out, group_rows):
+        started = set()
+        used = set()
+        for c0 in range(0, n_in, window):
+            for r in range(r0, min(n_out, r0 + group_rows)):
+                cs = [c for c in range(c0, min(n_in, c0 + window)) if bits[r, c]]
+                used.update(cs)
+                if not cs:
+                    continue
+                if r not in started:
+                    started.add(r)
+                    total += 1 if len(cs) > 1 else 0
+                    cs = cs[3:]
+                total += (len(cs) + 1) // 2
+        loads += len(used)
+    return total, loads
+
+
+@pytest.mark.parametrize("k,m", [(13, 4), (16, 4), (32, 4), (40, 8)])
+@pytest.mark.parametrize("temps", [-1, 0], ids=["plain", "auto"])
+def test_two_level_programs_for_wide_codes(k, m, temps):
+    """More than 96 input strips: the planner builds the two-level program
+    (windows of 32 inputs, groups of partial sums within the register
+    budget); its lowered stream computes the oracle's parity, every input is
+    loaded once per group, and the live values leave room in 128 registers.
+    Without temporals per window its instruction count is the construction's;
+    with XorRePair per window (automatic) it is no larger."""
+    plan = xo.ec_plan_create_ex(k, m, stream_temps=temps)
+    try:
+        info = xo.ec_plan_info(plan)
+        assert info["window"] == 32
+        assert info["max_live"] + 32 <= 128
+        bits = oracle.bitmatrix(oracle.cauchy(k, m))
+        groups = info["loads"] // (8 * k)
+        assert info["loads"] == groups * 8 * k and groups >= 1
+        G = -(-8 * m // groups)
+        plain = _two_level_lop3(bits, 32, G)
+        if temps == -1:
+            assert info["window_temps"] == 0
+            assert info["fused"]["xors"] == info["raw"]["xors"]      # no compression
+            assert (info["lop3"], info["loads"]) == plain
+        else:
+            assert info["window_temps"] in (0, 8, 16, 32)
+            assert info["lop3"] + 2 * info["loads"] <= plain[0] + 2 * plain[1]
+            assert info["fused"]["xors"] < info["raw"]["xors"]
+        B = 128
+        data = [synth.block_bytes(13, 0, j, B) for j in range(k)]
+        code = xo.ec_plan_program(plan)
+        got = _unstrip(emulate_stream(code, 8 * k, 8 * m, _strips(data)), m)
+        ref = oracle.encode(oracle.cauchy(k, m), data)
+        for i in range(m):
+            assert np.array_equal(got[i], ref[i])
+        # a decoder of the same code is two-level too
+        er = list(range(1, m + 1))
+        dinfo = xo.ec_plan_info(plan, er)
+        assert dinfo["window"] == 32
+        blocks = data + ref
+        surv = [i for i in range(k + m) if i not in er][:k]
+        got = _unstrip(emulate_stream(xo.ec_plan_program(plan, er), 8 * k, 8 * len(er),
+                                      _strips([blocks[i] for i in surv])), len(er))
+        for i, e in enumerate(er):
+            assert np.array_equal(got[i], blocks[e])
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+def test_two_level_window_option():
+    k, m = 16, 4
+    bits = oracle.bitmatrix(oracle.cauchy(k, m))
+    off = xo.ec_plan_create_ex(k, m, stream_window=-1)
+    w8 = xo.ec_plan_create_ex(k, m, stream_window=8, stream_temps=-1)
+    try:
+        i_off, i8 = xo.ec_plan_info(off), xo.ec_plan_info(w8)
+        # off: one fused statement per row, every operand read at its use
+        assert i_off["window"] == 0 and i_off["stmts"] == 8 * m
+        assert i_off["loads"] == int(bits.sum())
+        assert i8["window"] == 8
+        assert (i8["lop3"], i8["loads"]) == _two_level_lop3(bits, 8, 8 * m)
+        for t in (8, 32):
+            h = xo.ec_plan_create_ex(k, m, stream_temps=t)
+            try:
+                assert xo.ec_plan_info(h)["window_temps"] == t
+            finally:
+                xo.ec_plan_destroy(h)
+        with pytest.raises(xo.XorecError):
+            xo.ec_plan_create_ex(k, m, stream_temps=-2)
+        # narrow codes never take the two-level form
+        for kk in (10, 12):
+            h = xo.ec_plan_create_ex(kk, 4, stream_window=8)
+            try:
+                assert xo.ec_plan_info(h)["window"] == 0
+                assert xo.ec_plan_info(h)["loads"] == 8 * kk
+            finally:
+                xo.ec_plan_destroy(h)
+        with pytest.raises(xo.XorecError):
+            xo.ec_plan_create_ex(k, m, stream_window=-2)
+    finally:
+        xo.ec_plan_destroy(off)
+        xo.ec_plan_destroy(w8)
