@@ -87,7 +87,12 @@ extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_s
     cudaFree(d_out);
     return EC_ECUDA;
   }
-  const Candidate cands[] = {{128, 128}, {128, 112}, {128, 96}, {128, 160}, {256, 128}, {256, 112}};
+  std::vector<Candidate> cands = {{128, 128}, {128, 112}, {128, 96}, {128, 160}, {256, 128},
+                                  {256, 112}};
+  // wide codes: also the narrower tiles that keep two CTAs per SM
+  const int wide_threads = xorec::tile_threads_for_inputs(8 * k, 128);
+  if (wide_threads < 128)
+    for (int b : {128, 160, 112}) cands.push_back(Candidate{wide_threads, b});
   std::vector<uint8_t> ref, got(n_stripes * dout);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -108,7 +113,7 @@ extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_s
   int best = -1, tried = 0;
   std::unique_ptr<Program> best_prog;
   ec_status rc = EC_OK;
-  for (int c = 0; c < static_cast<int>(sizeof(cands) / sizeof(cands[0])); ++c) {
+  for (int c = 0; c < static_cast<int>(cands.size()); ++c) {
     xorec::PlanOptions o = plan->opts;
     o.reg_budget = cands[c].reg_budget;
     if (o.max_temps != -2) o.max_temps = -2;

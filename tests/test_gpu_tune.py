@@ -118,3 +118,34 @@ def test_set_launch_shape_runs_plain_batched_and_served():
     finally:
         xo.ec_plan_destroy(tuned)
         xo.ec_plan_destroy(plain)
+
+
+def test_autotune_wide_code_keeps_parity():
+    """RS(32,4): the candidates include the 64-thread tiles that keep two CTAs
+    per SM; whichever shape wins, encode and decode stay bit-exact."""
+    torch.cuda.set_device(0)
+    k, m = 32, 4
+    plan = xo.ec_plan_create(k, m)
+    try:
+        st = torch.cuda.current_stream().cuda_stream
+        r = xo.ec_plan_autotune(plan, 64 << 10, 8, st)
+        assert r["candidates"] >= 7 and r["threads"] in (64, 128, 256)
+        assert xo.ec_plan_info(plan)["threads"] == r["threads"]
+        B = 8 * 1552
+        data = [synth.block_bytes(73, 0, j, B) for j in range(k)]
+        blocks = data + oracle.encode(oracle.cauchy(k, m), data)
+        d = [torch.from_numpy(x).cuda() for x in blocks]
+        par = [torch.zeros(B, dtype=torch.uint8, device="cuda") for _ in range(m)]
+        xo.ec_encode(plan, [t.data_ptr() for t in d[:k]], [t.data_ptr() for t in par], B, st)
+        er = [0, 13, 31, 34]
+        outs = [torch.zeros(B, dtype=torch.uint8, device="cuda") for _ in er]
+        xo.ec_decode(plan, er, [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                     [t.data_ptr() for t in outs], B, st)
+        torch.cuda.synchronize()
+        for i in range(m):
+            assert np.array_equal(par[i].cpu().numpy(), blocks[k + i])
+        for t, e in zip(outs, er):
+            assert np.array_equal(t.cpu().numpy(), blocks[e])
+        assert xo.ec_device_status() == 0
+    finally:
+        xo.ec_plan_destroy(plan)
