@@ -145,16 +145,18 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
     // rows); each keeps the values live within reg_budget - 32 (addresses
     // and loop state need the rest), and the cheapest by three-input XORs
     // plus twice the shared-memory loads (the narrower pipe) wins
+    // (the unoptimised level keeps every window uncompressed)
     std::vector<int> temps_c;
-    if (o.stream_temps > 0) temps_c = {o.stream_temps};
-    else if (o.stream_temps < 0) temps_c = {0};
+    if (o.opt_level == kOptRaw || o.stream_temps < 0) temps_c = {0};
+    else if (o.stream_temps > 0) temps_c = {o.stream_temps};
     else temps_c = {0, 8, 16, 32};
     long best_cost = -1;
     for (int wt : temps_c) {
       for (int rows_per_group = n_out;; rows_per_group = (rows_per_group + 1) / 2) {
         std::vector<int> group;
         long loads = 0;
-        Slp st = slp_rows_stream(n_in, R, window, rows_per_group, &group, wt);
+        Slp st = slp_rows_stream(n_in, R, window, rows_per_group, &group, wt,
+                                 o.opt_level != kOptRePair);
         Schedule sc = schedule_in_order(st, false);
         const int live = max_live_grouped(st, sc, group, &loads);
         if (live + 32 <= o.reg_budget || rows_per_group <= 8) {

@@ -294,7 +294,7 @@ Slp slp_rows_chains(int n_const, const std::vector<Bits>& rows,
 }
 
 Slp slp_rows_stream(int n_const, const std::vector<Bits>& rows, int window, int group_rows,
-                    std::vector<int>* stmt_group, int window_temps) {
+                    std::vector<int>* stmt_group, int window_temps, bool xor_cancel) {
   Slp p;
   p.n_const = n_const;
   const int n_rows = static_cast<int>(rows.size());
@@ -352,7 +352,7 @@ Slp slp_rows_stream(int n_const, const std::vector<Bits>& rows, int window, int 
         if (rid.empty()) continue;
         std::vector<int> ord(rid.size());
         for (size_t i = 0; i < ord.size(); ++i) ord[i] = static_cast<int>(i);
-        RepairTrace rt(slp_rows_chains(wn, sub, ord), true, window_temps);
+        RepairTrace rt(slp_rows_chains(wn, sub, ord), xor_cancel, window_temps);
         const Slp f = fuse(rt.at(rt.n_temps()), true);
         std::vector<int> val(f.n_var, -1), users(f.n_var, 0), n_goal(f.n_var, 0),
             goal_row(f.n_var, -1);

@@ -98,11 +98,13 @@ Slp slp_rows_chains(int n_const, const std::vector<Bits>& rows,
 // statement that needs all its inputs at once).  stmt_group receives the
 // group of each statement.
 // window_temps > 0: the group's rows restricted to each window are first
-// shortened by XorRePair with at most window_temps temporals, and fusion
-// (Sec. 4.4, Sec. 5.2); temporals live within their window, and a row's
-// fused window part is added into its partial sum.
+// shortened by XorRePair (RePair when xor_cancel is false) with at most
+// window_temps temporals, and fusion (Sec. 4.3-4.4, Sec. 5.2); temporals live
+// within their window, and a row's fused window part is added into its
+// partial sum.
 Slp slp_rows_stream(int n_const, const std::vector<Bits>& rows, int window, int group_rows,
-                    std::vector<int>* stmt_group, int window_temps = 0);
+                    std::vector<int>* stmt_group, int window_temps = 0,
+                    bool xor_cancel = true);
 
 // RePair (xor_cancel = false) or XorRePair (true) on the flattened
 // semantics of p.  Returns a single-assignment program of binary

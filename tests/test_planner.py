@@ -566,6 +566,17 @@ def test_two_level_window_option():
                 xo.ec_plan_destroy(h)
         with pytest.raises(xo.XorecError):
             xo.ec_plan_create_ex(k, m, stream_temps=-2)
+        # the unoptimised level keeps every window uncompressed; RePair
+        # (without cancellation) still shortens them
+        for opt, compressed in ((xo.EC_OPT_RAW, False), (xo.EC_OPT_REPAIR, True)):
+            h = xo.ec_plan_create_ex(k, m, opt_level=opt)
+            try:
+                i = xo.ec_plan_info(h)
+                assert i["window"] == 32
+                assert (i["window_temps"] > 0) == compressed
+                assert (i["fused"]["xors"] < i["raw"]["xors"]) == compressed
+            finally:
+                xo.ec_plan_destroy(h)
         # narrow codes never take the two-level form
         for kk in (10, 12):
             h = xo.ec_plan_create_ex(kk, 4, stream_window=8)
