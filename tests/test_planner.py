@@ -575,6 +575,11 @@ def test_two_level_window_option():
                 assert i["window"] == 32
                 assert (i["window_temps"] > 0) == compressed
                 assert (i["fused"]["xors"] < i["raw"]["xors"]) == compressed
+                data = [synth.block_bytes(14, opt, j, 128) for j in range(k)]
+                got = _unstrip(emulate_stream(xo.ec_plan_program(h), 8 * k, 8 * m,
+                                              _strips(data)), m)
+                ref = oracle.encode(oracle.cauchy(k, m), data)
+                assert all(np.array_equal(a, b) for a, b in zip(got, ref))
             finally:
                 xo.ec_plan_destroy(h)
         # narrow codes never take the two-level form
