@@ -176,6 +176,15 @@ typedef struct {
 ec_status ec_plan_info(ec_plan *plan, const int *erasures, int n_erasures,
                        ec_program_info *out);
 
+/* CUDA C++ source of the compiled tier's kernel for the encoder (erasures ==
+ * NULL) or a decoder, as the plan compiles it at its launch shape (NVRTC,
+ * sm_103a): the tile pipeline, the program's straight-line statements and
+ * the kernel entry.  Copies at most len - 1 characters and a terminating NUL
+ * into buf (NULL: none); *need receives the full length including the NUL.
+ * Host only; for inspection and for checking the compile without a GPU. */
+ec_status ec_plan_kernel_source(ec_plan *plan, const int *erasures, int n_erasures, char *buf,
+                                size_t len, size_t *need);
+
 /* Copy the interpreter instruction stream of the encoder (erasures == NULL)
  * or of a decoder into buf (len 16-bit words); *need receives the length.
  * Stream format, statement by statement: n_args; n_outs | has_slot << 15;

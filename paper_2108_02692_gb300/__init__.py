@@ -144,6 +144,17 @@ def ec_plan_program(plan: int, erasures=None) -> np.ndarray:
     return out
 
 
+def ec_plan_kernel_source(plan: int, erasures=None) -> str:
+    """CUDA source of the compiled tier's kernel for the encoder or a decoder."""
+    need = ctypes.c_size_t()
+    er = _int_array(erasures) if erasures is not None else None
+    ne = len(erasures) if erasures is not None else 0
+    _check(lib().ec_plan_kernel_source(plan, er, ne, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().ec_plan_kernel_source(plan, er, ne, buf, need.value, None))
+    return buf.value.decode()
+
+
 def ec_plan_autotune(plan: int, block_bytes: int, n_stripes: int = 16, stream: int = 0) -> dict:
     r = _abi.TuneResult()
     _check(lib().ec_plan_autotune(plan, block_bytes, n_stripes, stream or None, ctypes.byref(r)))

@@ -96,6 +96,8 @@ SIGNATURES = {
     "ec_plan_info": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ProgramInfo)]),
     "ec_plan_program": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ctypes.c_uint16), c_size,
                                 ctypes.POINTER(c_size)]),
+    "ec_plan_kernel_source": (c_int, [c_vp, intp, c_int, ctypes.c_char_p, c_size,
+                                      ctypes.POINTER(c_size)]),
     "ec_encode": (c_int, [c_vp, vpp, vpp, c_size, c_vp]),
     "ec_encode_noalloc": (c_int, [c_vp, vpp, vpp, c_size, c_vp]),
     "ec_encode_strided": (c_int, [c_vp, c_vp, c_size, c_size, c_vp, c_size, c_size, c_int,

@@ -573,6 +573,27 @@ ec_status ec_plan_program(ec_plan* plan, const int* erasures, int n_erasures, ui
   return EC_OK;
 }
 
+ec_status ec_plan_kernel_source(ec_plan* plan, const int* erasures, int n_erasures, char* buf,
+                                size_t len, size_t* need) {
+  if (!plan) return fail(EC_EINVAL, "NULL plan");
+  Program* p = plan->enc.get();
+  if (erasures) {
+    std::vector<int> er;
+    ec_status s = canon_erasures(plan, erasures, n_erasures, &er);
+    if (s != EC_OK) return s;
+    s = get_decode_program(plan, er, &p);
+    if (s != EC_OK) return s;
+  }
+  const std::string src = xorec::jit_source(*p, xorec::program_threads(p));
+  if (need) *need = src.size() + 1;
+  if (buf && len > 0) {
+    const size_t n = std::min(len - 1, src.size());
+    std::memcpy(buf, src.data(), n);
+    buf[n] = '\0';
+  }
+  return EC_OK;
+}
+
 ec_status ec_encode(ec_plan* plan, const uint8_t* const* data, uint8_t* const* parity,
                     size_t block_bytes, void* stream) {
   xorec::TraceRange trace_("xorec encode");

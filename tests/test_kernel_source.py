@@ -1,0 +1,95 @@
+"""The compiled tier's kernels compile for sm_103a without spilling: the
+source each plan would compile (ec_plan_kernel_source) goes through NVRTC on
+the host, with the library's options and ptxas's report.  Covers the
+register-budgeted narrow programs (default and autotuned shapes) and the
+two-level programs of wide codes, encoders and a decoder.  No GPU needed."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2108_02692_gb300 as xo
+
+OPTS = [b"-arch=sm_103a", b"-std=c++17", b"-default-device", b"--extra-device-vectorization",
+        b"--ptxas-options=-v"]
+
+
+def _nvrtc():
+    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    for name in ("libnvrtc.so", "libnvrtc.so.13", "libnvrtc.so.12"):
+        for d in (os.path.join(home, "lib64"), os.path.join(home, "lib"), ""):
+            try:
+                return ctypes.CDLL(os.path.join(d, name) if d else name)
+            except OSError:
+                continue
+    pytest.skip("NVRTC not found")
+
+
+def compile_report(src: str) -> str:
+    lib = _nvrtc()
+    prog = ctypes.c_void_p()
+    assert lib.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"xorec_slp.cu", 0, None,
+                                  None) == 0
+    try:
+        opts = (ctypes.c_char_p * len(OPTS))(*OPTS)
+        rc = lib.nvrtcCompileProgram(prog, len(OPTS), opts)
+        n = ctypes.c_size_t()
+        lib.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+        log = ctypes.create_string_buffer(n.value)
+        lib.nvrtcGetProgramLog(prog, log)
+        text = log.value.decode(errors="replace")
+        assert rc == 0, text
+        return text
+    finally:
+        lib.nvrtcDestroyProgram(ctypes.byref(prog))
+
+
+def check_no_spill(src: str):
+    rep = compile_report(src)
+    spills = [int(x) for x in re.findall(r"(\d+) bytes spill stores", rep)]
+    regs = [int(x) for x in re.findall(r"Used (\d+) registers", rep)]
+    assert spills and max(spills) == 0, rep
+    m = re.search(r"__launch_bounds__\((\d+), (\d+)\)", src)
+    threads, minb = int(m.group(1)), int(m.group(2))
+    assert regs and max(regs) <= 65536 // (threads * minb), rep
+    return max(regs)
+
+
+@pytest.mark.parametrize("k,m,shape,erasures", [
+    (10, 4, None, None),            # default shape, register budget 128
+    (10, 4, (128, 160), None),      # the autotuner's RS(10,4) shape
+    (10, 4, None, [1, 4, 9, 12]),
+    (16, 4, None, None),            # two-level programs from here on
+    (24, 8, None, None),
+    (32, 4, None, [0, 5, 9, 33]),
+    (48, 4, None, None),
+])
+def test_kernel_compiles_without_spills(k, m, shape, erasures):
+    plan = xo.ec_plan_create(k, m)
+    try:
+        if shape:
+            xo.ec_plan_set_launch(plan, *shape)
+        src = xo.ec_plan_kernel_source(plan, erasures)
+        info = xo.ec_plan_info(plan, erasures)
+        assert f"__launch_bounds__({info['threads']}," in src
+        assert ("xk_x3(" in src) == (info["window"] > 0)
+        check_no_spill(src)
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
+def test_kernel_source_buffer_protocol():
+    plan = xo.ec_plan_create(4, 2)
+    try:
+        need = ctypes.c_size_t()
+        lib = xo.lib()
+        assert lib.ec_plan_kernel_source(plan, None, 0, None, 0, ctypes.byref(need)) == 0
+        small = ctypes.create_string_buffer(16)
+        assert lib.ec_plan_kernel_source(plan, None, 0, small, 16, None) == 0
+        full = xo.ec_plan_kernel_source(plan)
+        assert len(full) + 1 == need.value and small.value.decode() == full[:15]
+        with pytest.raises(xo.XorecError):
+            xo.ec_plan_kernel_source(plan, [0, 0])
+    finally:
+        xo.ec_plan_destroy(plan)
