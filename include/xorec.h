@@ -105,7 +105,10 @@ typedef struct {
                            budget keeps the most valuable temporaries while
                            bounding the registers the program needs          */
   int reg_budget;       /* registers per thread the automatic budget aims at
-                           (all input words preloaded); 0 = 128             */
+                           (all input words preloaded); 0 = 128, else in
+                           [32, 255].  Above 128 it also raises the compiled
+                           kernels' register cap (fewer CTAs per SM), as
+                           ec_plan_set_launch does                          */
   int stream_window;    /* codes with more than 96 input strips (12 data
                            blocks) and automatic temporaries: the input words
                            do not fit the registers, so the program is

@@ -468,6 +468,8 @@ ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix
     plan->executor = opts->executor;
     if (opts->max_temps < -2) return fail(EC_EINVAL, "bad max_temps");
     plan->opts.max_temps = opts->max_temps;
+    if (opts->reg_budget != 0 && (opts->reg_budget < 32 || opts->reg_budget > 255))
+      return fail(EC_EINVAL, "reg_budget must be 0 or in [32, 255]");
     plan->opts.reg_budget = opts->reg_budget > 0 ? opts->reg_budget : 128;
     if (opts->stream_window < -1) return fail(EC_EINVAL, "bad stream_window");
     plan->opts.stream_window = opts->stream_window;
@@ -478,6 +480,16 @@ ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix
   std::string err;
   if (!xorec::build_program(m, k, plan->P.data(), plan->opts, plan->enc.get(), &err))
     return fail(EC_EINVAL, err);
+  if (plan->opts.reg_budget > 128) {
+    // a register budget above the default cap of 128 registers also raises
+    // the compiled kernels' cap (fewer resident CTAs per SM), as
+    // ec_plan_set_launch does; smaller budgets keep the default cap
+    const int th = xorec::program_threads(plan->enc.get());
+    plan->tuned_threads = th;
+    plan->tuned_minb = xorec::minb_for(th, plan->opts.reg_budget);
+    plan->enc->threads = th;
+    plan->enc->minb = plan->tuned_minb;
+  }
   *out = plan.release();
   return EC_OK;
 }

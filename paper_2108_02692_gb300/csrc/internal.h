@@ -124,6 +124,9 @@ int tile_threads_for_inputs(int n_in, int threads);
 // Threads per CTA of p's compiled tier: the tuned or pinned shape, else
 // EC_JIT_THREADS, else tile_threads_for_inputs(n_in, 128).
 int program_threads(const Program* p);
+// Resident CTAs per SM (the __launch_bounds__ minimum) that leave each of
+// `threads` threads reg_budget registers of the SM's 65,536.
+int minb_for(int threads, int reg_budget);
 bool jit_compile(Program* p, int threads, std::string* err);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
                 int grid, size_t smem, cudaStream_t stream);

@@ -15,11 +15,7 @@
 
 using xorec::Program;
 
-namespace {
-
-struct Candidate {
-  int threads, reg_budget;
-};
+namespace xorec {
 
 int minb_for(int threads, int reg_budget) {
   const int per_sm_regs = 65536;
@@ -28,6 +24,15 @@ int minb_for(int threads, int reg_budget) {
   if (minb * threads > 1024) minb = 1024 / threads;
   return minb;
 }
+
+}  // namespace xorec
+
+namespace {
+
+struct Candidate {
+  int threads, reg_budget;
+};
+
 
 // Make `prog` the plan's encoder and (threads, reg_budget) the launch shape
 // of the plan's compiled programs and batch modules built from now on.
@@ -39,7 +44,7 @@ void install(ec_plan* plan, std::unique_ptr<Program> prog, int threads, int reg_
   plan->opts.reg_budget = reg_budget;
   plan->opts.max_temps = -2;
   plan->tuned_threads = threads;
-  plan->tuned_minb = minb_for(threads, reg_budget);
+  plan->tuned_minb = xorec::minb_for(threads, reg_budget);
 }
 
 }  // namespace
@@ -57,7 +62,7 @@ extern "C" ec_status ec_plan_set_launch(ec_plan* plan, int threads, int reg_budg
   if (!xorec::build_program(plan->m, plan->k, plan->P.data(), o, prog.get(), &err))
     return fail(EC_EINVAL, err);
   prog->threads = threads;
-  prog->minb = minb_for(threads, reg_budget);
+  prog->minb = xorec::minb_for(threads, reg_budget);
   install(plan, std::move(prog), threads, reg_budget);
   return EC_OK;
 }
@@ -124,7 +129,7 @@ extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_s
       break;
     }
     prog->threads = cands[c].threads;
-    prog->minb = minb_for(cands[c].threads, cands[c].reg_budget);
+    prog->minb = xorec::minb_for(cands[c].threads, cands[c].reg_budget);
     if (!xorec::compiled_tier_fits(prog.get(), prog->threads, di.smem_optin)) continue;
     if (!xorec::launch_program(prog.get(), io, EC_EXEC_COMPILED, st)) {   // compiles
       xorec::jit_release(prog.get());
@@ -176,7 +181,7 @@ extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_s
   if (out) {
     out->threads = cands[best].threads;
     out->reg_budget = cands[best].reg_budget;
-    out->min_ctas_per_sm = minb_for(cands[best].threads, cands[best].reg_budget);
+    out->min_ctas_per_sm = xorec::minb_for(cands[best].threads, cands[best].reg_budget);
     out->candidates = tried;
     out->ms = best_ms;
     out->gbps_in = static_cast<double>(n_stripes) * din / (best_ms / 1e3) / 1e9;

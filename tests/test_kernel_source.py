@@ -79,6 +79,25 @@ def test_kernel_compiles_without_spills(k, m, shape, erasures):
         xo.ec_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("budget", [96, 160, 200])
+def test_explicit_register_budget_sets_the_cap(budget):
+    """A plan asking for more than 128 registers per thread gets kernels
+    whose register cap holds them (fewer CTAs per SM); smaller budgets keep
+    the default cap.  Encoder and decoder compile without spills."""
+    plan = xo.ec_plan_create_ex(10, 4, reg_budget=budget)
+    try:
+        for er in (None, [0, 3, 7, 11]):
+            src = xo.ec_plan_kernel_source(plan, er)
+            m = re.search(r"__launch_bounds__\((\d+), (\d+)\)", src)
+            cap = 65536 // (int(m.group(1)) * int(m.group(2)))
+            assert cap >= max(budget, 128)
+            check_no_spill(src)
+        with pytest.raises(xo.XorecError):
+            xo.ec_plan_create_ex(10, 4, reg_budget=300)
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
 def test_kernel_source_buffer_protocol():
     plan = xo.ec_plan_create(4, 2)
     try:
