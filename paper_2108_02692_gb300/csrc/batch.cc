@@ -44,7 +44,9 @@ int batch_threads_for(int n_in) {
   const int th = env_int("EC_BATCH_THREADS", 0);
   return th > 0 ? th : xorec::tile_threads_for_inputs(n_in, 128);
 }
-int batch_minb_for(int n_in) { return env_int("EC_BATCH_MINB", 512 / batch_threads_for(n_in)); }
+int batch_minb_for(int n_in) {
+  return env_int("EC_BATCH_MINB", xorec::default_minb(batch_threads_for(n_in), n_in));
+}
 
 struct Launch {
   void* mod = nullptr;                 // compiled module, or nullptr = interpreter

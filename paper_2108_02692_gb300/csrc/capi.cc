@@ -110,6 +110,11 @@ int tile_threads_for_inputs(int n_in, int threads) {
   return threads;
 }
 
+int default_minb(int threads, int n_in) {
+  const bool wide_preload = n_in > kPreloadCap128Inputs && n_in <= kPreloadMaxInputs;
+  return minb_for(threads, wide_preload ? 168 : 128);
+}
+
 int program_threads(const Program* p) {
   if (p->threads > 0) return p->threads;
   const int th = env_int("EC_JIT_THREADS", 0);

@@ -127,6 +127,10 @@ int program_threads(const Program* p);
 // Resident CTAs per SM (the __launch_bounds__ minimum) that leave each of
 // `threads` threads reg_budget registers of the SM's 65,536.
 int minb_for(int threads, int reg_budget);
+// Resident CTAs per SM of a compiled kernel with no tuned shape: a
+// 128-register cap, or 168 for preloaded programs of more than
+// kPreloadCap128Inputs input strips.
+int default_minb(int threads, int n_in);
 bool jit_compile(Program* p, int threads, std::string* err);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
                 int grid, size_t smem, cudaStream_t stream);

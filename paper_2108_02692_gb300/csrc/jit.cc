@@ -253,7 +253,7 @@ std::string gen_source(const xorec::Program& p, int threads) {
   if (!p.load_group.empty()) os << kOpaqueXorSrc;
   os << gen_body(p, threads);
   os << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
-     << (p.minb > 0 ? p.minb : env_or("EC_JIT_MINB", std::max(1, 512 / threads)))
+     << (p.minb > 0 ? p.minb : env_or("EC_JIT_MINB", xorec::default_minb(threads, p.n_in)))
      << ") xorec_slp(xk::LaunchParams p, const __grid_constant__ xk::TensorMap tm) {\n"
         "  extern __shared__ __align__(128) xk::u8 smem[];\n"
         "  xk::run_pipeline(p, smem, SlpBody(), &tm);\n"

@@ -20,6 +20,11 @@ std::vector<Bits> bitmatrix_rows(int rows, int cols, const uint8_t* A);
 // into registers: their compiled body reads operands from the shared-memory
 // stage.
 constexpr int kPreloadMaxInputs = 96;
+// Preloaded programs with more input strips than this need more than 128
+// registers per thread (the input words plus the pipeline's own state):
+// ptxas spills 16-68 bytes at a 128-register cap for every code of 11 or 12
+// data blocks, and none at 168, while no code of up to 10 spills at 128.
+constexpr int kPreloadCap128Inputs = 80;
 // Largest program (#_M memory operations) the compiled tier takes, so that
 // NVRTC compiles it in seconds.
 constexpr long kMaxCompiledMemOps = 65536;

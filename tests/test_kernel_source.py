@@ -79,6 +79,20 @@ def test_kernel_compiles_without_spills(k, m, shape, erasures):
         xo.ec_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("k", [4, 8, 10, 11, 12])
+def test_default_shape_never_spills(k):
+    """Every narrow code at the default launch shape, encoder and a decoder:
+    the register cap (128, or 168 from 11 data blocks up, where the preloaded
+    input words and the pipeline's state exceed 128) holds the program."""
+    for m in (1, 4, 8):
+        plan = xo.ec_plan_create(k, m)
+        try:
+            for er in (None, list(range(m))):
+                check_no_spill(xo.ec_plan_kernel_source(plan, er))
+        finally:
+            xo.ec_plan_destroy(plan)
+
+
 @pytest.mark.parametrize("budget", [96, 160, 200])
 def test_explicit_register_budget_sets_the_cap(budget):
     """A plan asking for more than 128 registers per thread gets kernels
