@@ -234,8 +234,12 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
     std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
     ec_plan* plan = to_compile[i].first;
     const int n_in = ps.front()->n_in;
+    // default shapes (no tuned or pinned shape, no EC_BATCH_MINB) may raise
+    // the register cap of a module that spills; a tuned shape is kept
+    const bool default_shape = !(plan->tuned_threads > 0 && plan->tuned_minb > 0) &&
+                               env_int("EC_BATCH_MINB", 0) <= 0;
     mods[i] = jit_compile_module(ps, plan_module_threads(plan, n_in), plan_module_minb(plan, n_in),
-                                 &errs[i]);
+                                 &errs[i], default_shape);
   });
   if (built) *built = static_cast<int>(to_compile.size());
   for (size_t i = 0; i < to_compile.size(); ++i) {

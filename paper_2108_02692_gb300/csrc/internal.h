@@ -148,7 +148,7 @@ void jit_release(Program* p);
 int jit_regs(const Program* p);
 std::string jit_source(const Program& p, int threads);
 void* jit_compile_module(const std::vector<const Program*>& progs, int threads, int minb,
-                         std::string* err);
+                         std::string* err, bool raise_cap_on_spill = false);
 int jit_module_ctas_per_sm(void* mod, size_t smem);
 bool jit_module_launch(void* mod, const xk::BatchParams& bp, int grid, size_t smem,
                        cudaStream_t stream);

@@ -282,8 +282,22 @@ static bool jit_set_smem(JitKernel* jk, size_t smem) {
 }
 
 // NVRTC: source -> cubin for the current device -> loaded kernel `name`.
+// Largest "N bytes spill stores" figure of a ptxas report (0 if none).
+static long spill_stores(const std::string& log) {
+  long most = 0;
+  const std::string key = " bytes spill stores";
+  for (size_t at = log.find(key); at != std::string::npos; at = log.find(key, at + 1)) {
+    size_t b = at;
+    while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
+    if (b < at) most = std::max(most, std::strtol(log.c_str() + b, nullptr, 10));
+  }
+  return most;
+}
+
+// Compile and load; with spill_bytes, ptxas also reports its register use
+// and *spill_bytes receives the bytes it spilled (per thread).
 static JitKernel* compile_and_load(const std::string& src, const char* name, int threads,
-                                   std::string* err) {
+                                   std::string* err, long* spill_bytes = nullptr) {
   xorec::TraceRange trace_("xorec nvrtc compile");
   DeviceInfo di;
   if (!device_info(&di)) {
@@ -304,8 +318,9 @@ static JitKernel* compile_and_load(const std::string& src, const char* name, int
   }
   char arch[64];
   std::snprintf(arch, sizeof(arch), "-arch=sm_%d%da", major, minor);
-  const char* opts[] = {arch, "-std=c++17", "-default-device", "--extra-device-vectorization"};
-  const nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
+  const char* opts[] = {arch, "-std=c++17", "-default-device", "--extra-device-vectorization",
+                        "--ptxas-options=-v"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, spill_bytes ? 5 : 4, opts);
   if (rc != NVRTC_SUCCESS) {
     size_t n = 0;
     nvrtcGetProgramLogSize(prog, &n);
@@ -314,6 +329,13 @@ static JitKernel* compile_and_load(const std::string& src, const char* name, int
     nvrtcDestroyProgram(&prog);
     *err = "NVRTC compile failed: " + log.substr(0, 2000);
     return nullptr;
+  }
+  if (spill_bytes) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    nvrtcGetProgramLog(prog, &log[0]);
+    *spill_bytes = spill_stores(log);
   }
   size_t nbin = 0;
   nvrtcGetCUBINSize(prog, &nbin);
@@ -351,12 +373,24 @@ bool jit_compile(Program* p, int threads, std::string* err) {
 
 // A module of programs sharing n_in (batched launches).
 void* jit_compile_module(const std::vector<const Program*>& progs, int threads, int minb,
-                         std::string* err) {
+                         std::string* err, bool raise_cap_on_spill) {
   if (progs.empty()) {
     *err = "empty module";
     return nullptr;
   }
-  return compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads, err);
+  if (!raise_cap_on_spill)
+    return compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads, err);
+  // The batch pipeline keeps more state than a single launch's, so a module
+  // can spill at the default register cap its programs fit alone; then it is
+  // compiled again with one resident CTA per SM fewer, which raises the cap.
+  for (;;) {
+    long spill = 0;
+    JitKernel* jk =
+        compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads, err, &spill);
+    if (!jk || spill == 0 || minb <= 1) return jk;
+    jit_module_release(jk);
+    --minb;
+  }
 }
 
 int jit_module_ctas_per_sm(void* mod, size_t smem) {
