@@ -112,6 +112,48 @@ def test_explicit_register_budget_sets_the_cap(budget):
         xo.ec_plan_destroy(plan)
 
 
+def live_values_of_emitted_code(src: str) -> int:
+    """Most values a thread holds at once in the emitted straight-line body:
+    a value (an input word loaded from the stage, or a statement's result)
+    lives from the line that defines it to its last use; each statement is
+    counted with its result."""
+    body = src[src.index("struct SlpBody"):]
+    body = body[:body.index("#undef I")]
+    lines = [ln.strip() for ln in body.splitlines()]
+    defs, last_use, stmts = {}, {}, []
+    for i, ln in enumerate(lines):
+        mm = re.match(r"const xk::u32 (\w+) = (.*);$", ln)
+        if mm:
+            name, rhs = mm.groups()
+            defs[name] = i
+            if not rhs.startswith("I("):
+                stmts.append(i)
+                for u in re.findall(r"\b([iv]\d+(?:_\d+)?)\b", rhs):
+                    last_use[u] = i
+            continue
+        mm = re.match(r"O\(\d+, \d+, (\w+)\);$", ln)
+        if mm:
+            last_use[mm.group(1)] = i
+    return max(sum(1 for n, d in defs.items() if d < L and last_use.get(n, -1) >= L) + 1
+               for L in stmts)
+
+
+@pytest.mark.parametrize("k,m", [(13, 4), (16, 4), (24, 8), (32, 4)])
+@pytest.mark.parametrize("temps", [-1, 0], ids=["plain", "per-window"])
+def test_two_level_register_model_matches_emitted_code(k, m, temps):
+    """The planner's live-value count of a two-level program (the group size
+    is chosen by it) equals the count read off the kernel it emits, where
+    each input word is loaded once per group at its first use."""
+    plan = xo.ec_plan_create_ex(k, m, stream_temps=temps)
+    try:
+        src = xo.ec_plan_kernel_source(plan)
+        assert live_values_of_emitted_code(src) == xo.ec_plan_info(plan)["max_live"]
+        info = xo.ec_plan_info(plan)
+        assert len(re.findall(r"= I\(\d+\);", src)) == info["loads"]
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
 def test_kernel_source_buffer_protocol():
     plan = xo.ec_plan_create(4, 2)
     try:
