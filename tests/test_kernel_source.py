@@ -154,6 +154,46 @@ def test_two_level_register_model_matches_emitted_code(k, m, temps):
         xo.ec_plan_destroy(plan)
 
 
+def live_values_preloaded(src: str) -> int:
+    """Same count for a narrow body: every input word is in a register from
+    the start of compute() to its last use."""
+    body = src[src.index("void compute("):]
+    body = body[:body.index("#undef I")]
+    last_in, last_v, stmts = {}, {}, []
+    for i, ln in enumerate(x.strip() for x in body.splitlines()):
+        mm = re.match(r"const xk::u32 v(\d+) = (.*);$", ln) or re.match(r"O\(\d+, \d+, (.*)\)();$", ln)
+        if not mm:
+            continue
+        if ln.startswith("const"):
+            stmts.append((i, int(mm.group(1))))
+            rhs = mm.group(2)
+        else:
+            rhs = mm.group(1)
+        for c in re.findall(r"I\((\d+)\)", rhs):
+            last_in[int(c)] = i
+        for v in re.findall(r"\bv(\d+)\b", rhs):
+            last_v[int(v)] = i
+    defs = {v: i for i, v in stmts}
+    return max(sum(1 for e in last_in.values() if e >= L) +
+               sum(1 for w, d in defs.items() if d < L and last_v.get(w, -1) >= L) + 1
+               for L, _ in stmts)
+
+
+@pytest.mark.parametrize("k,m,er", [(10, 4, None), (10, 4, [0, 3, 7, 11]), (6, 3, None),
+                                    (12, 4, None), (4, 2, [1, 4])])
+def test_preloaded_register_model_matches_emitted_code(k, m, er):
+    """The register-budgeted XorRePair picks its temporaries by the live
+    values of the schedule with every input preloaded; the same count read
+    off the emitted kernel agrees, and stays within the budget (128)."""
+    plan = xo.ec_plan_create(k, m)
+    try:
+        src = xo.ec_plan_kernel_source(plan, er)
+        live = live_values_preloaded(src)
+        assert live == xo.ec_plan_info(plan, er)["max_live"] <= 128
+    finally:
+        xo.ec_plan_destroy(plan)
+
+
 def test_kernel_source_buffer_protocol():
     plan = xo.ec_plan_create(4, 2)
     try:
