@@ -1,14 +1,21 @@
 """Benchmark: RS(10,4) Cauchy encode over 256 stripes x 10 x 1 MiB on one GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload encode|decode] [--executor auto|interp|compiled]
+                [--workload encode|batched|served|codes] [--executor auto|interp|compiled]
 
 One step = one pass of the hot path over one batch: a single
 ec_encode_strided() launch over the 256 stripes (2.5 GiB in, 1 GiB out;
 inputs larger than L2, so no flush is needed between steps).  `value` is
 GB/s (1e9 B) of input data, whole job; `e2e` is the same metric through the
 C ABI with the inputs in pinned host memory and the host<->device copies
-inside the timed region.  Prints one JSON line.
+inside the timed region.  Prints one JSON line.  On one GPU the default run
+adds, as keys of the same line: `decode` (RS(10,4) decode of 256 stripes,
+erasure sets uniform over all 1470 patterns, one batch run, against one
+launch per stripe), `batched` (8192 mixed-code stripes in one batch run
+replayed as a CUDA graph, against one launch per stripe) and `served`
+(Poisson request streams through the continuous-batching server at 20k and
+100k requests/s, p50/p99 latency, against a one-request-at-a-time server);
+each with its bit-exact status against the oracle.
 
 With --impl reference the CPU oracle (test infrastructure, plain C) is
 timed on this host's cores on a bounded sample of the same workload.
@@ -52,6 +59,12 @@ def parse_args():
                     help="coding matrix (default: Cauchy)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-rates", default="",
+                    help="comma-separated arrival rates (req/s) of a served load sweep")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default run: skip the batched (mixed-code) leg")
+    ap.add_argument("--no-served", action="store_true",
+                    help="default run: skip the served leg")
     ap.add_argument("--serve-idle-spin-us", type=int, default=0,
                     help="scheduler polling window before it sleeps (0 = library default "
                          "1000 us, -1 = sleep at once)")
@@ -75,6 +88,9 @@ def parse_args():
                     help="comma-separated block ids erased in every decode stripe (e.g. 2,4,5,6, "
                          "the paper's P_dec)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--decode-launch", default="",
+                    help="THREADS,REG_BUDGET launch shape of the decode plan (default: the "
+                         "plan's default shape)")
     ap.add_argument("--stream-temps", type=int, default=0,
                     help="codes with more than 12 data blocks: XorRePair temporals per input "
                          "window of the two-level program (0 = automatic, -1 = none)")
@@ -357,7 +373,14 @@ def run_ours(args):
             ref = oracle.encode(P, mini)
             got = par[int(s)].view(m, 8, S)[:, :, w0:w0 + 64].cpu().numpy()
             ok &= all(np.array_equal(got[i].reshape(-1), ref[i]) for i in range(m))
-        parity_status = "bit-exact on sampled windows" if ok else "MISMATCH"
+        # and one whole stripe (10 x 1 MiB in, 4 x 1 MiB out)
+        s = int(rng.integers(0, n))
+        full = [synth.block_bytes(ENCODE_WORKLOAD_ID, s, j, B) for j in range(k)]
+        ref = oracle.encode(P, full)
+        got = par[s].cpu().numpy()
+        ok &= all(np.array_equal(got[i], ref[i]) for i in range(m))
+        parity_status = ("bit-exact on sampled windows of 4 stripes and on all of stripe "
+                         f"{s}") if ok else "MISMATCH"
 
     info = xo.ec_plan_info(plan)
     in_bytes = n * k * B
@@ -377,6 +400,13 @@ def run_ours(args):
         del data, par
         torch.cuda.empty_cache()
         decode = run_decode(args, xo, torch, stream, peak)
+    batched = served = None
+    if ws == 1 and n == N_STRIPES and not args.no_batched:
+        torch.cuda.empty_cache()
+        batched = batched_leg(args)
+    if ws == 1 and n == N_STRIPES and not args.no_served:
+        torch.cuda.empty_cache()
+        served = served_leg(args, [args.serve_rate, 100000.0])
     status = xo.ec_device_status()
 
     out = {
@@ -405,6 +435,8 @@ def run_ours(args):
                      "traffic": traffic_from_profiles(kind)},
         "e2e": e2e,
         "decode": decode,
+        "batched": batched,
+        "served": served,
         "gpu_launches": K,
         "clocks": clk,
         "parity": parity_status,
@@ -457,6 +489,9 @@ def run_decode(args, xo, torch, stream, peak):
                              0, sp)
     stream.synchronize()
     plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, args.matrix))
+    if args.decode_launch:
+        th, rb = (int(x) for x in args.decode_launch.split(","))
+        xo.ec_plan_set_launch(plan, th, rb)
     jobs, calls = [], []
     for s, er in enumerate(pats):
         ids = [i for i in range(k + m) if i not in er][:k]
@@ -501,6 +536,20 @@ def run_decode(args, xo, torch, stream, peak):
         ref = oracle.apply(R, mini)
         got = outs[int(s), :len(er)].view(len(er), 8, S)[:, :, w0:w0 + 32].cpu().numpy()
         ok &= all(np.array_equal(got[i].reshape(-1), ref[i]) for i in range(len(er)))
+    # one whole stripe of each erasure count (1..4 blocks lost)
+    whole = []
+    for ne in range(1, m + 1):
+        cand = [s for s, er in enumerate(pats) if len(er) == ne]
+        if not cand:
+            continue
+        s = cand[0]
+        er = list(pats[s])
+        R = oracle.decode_matrix(P, er)
+        full = [synth.block_bytes(DECODE_WORKLOAD_ID, s, j, B) for j in range(k)]
+        ref = oracle.apply(R, full)
+        got = outs[s, :len(er)].cpu().numpy()
+        ok &= all(np.array_equal(got[i], ref[i]) for i in range(len(er)))
+        whole.append(s)
     # plain single-stripe launches (compiled tier, kernels compiled beforehand)
     t0 = time.perf_counter()
     xo.ec_plan_compile(plan, sorted(set(pats)))
@@ -531,7 +580,8 @@ def run_decode(args, xo, torch, stream, peak):
         "distinct_patterns": len(set(pats)),
         "launches_per_step": binfo["launches"],
         "prepare_s": round(prep_s, 2), "plain_compile_s": round(compile_s, 2),
-        "parity": "bit-exact on sampled windows" if ok else "MISMATCH",
+        "parity": (f"bit-exact on sampled windows of 6 stripes and on all of stripes {whole} "
+                   "(one per erasure count)") if ok else "MISMATCH",
     }
 
 
@@ -658,14 +708,16 @@ def percentile(xs, q):
 
 
 def serve_stream(xo, torch, reqs, plans, data_arena, out_arena, max_batch, slots, warm_s,
-                 budget=32 << 30, idle_spin_us=0):
+                 budget=32 << 30, idle_spin_us=0, check=0):
     """Replay a request trace against a server; returns latencies (µs) of the
-    requests that arrived after warm_s, and server stats."""
+    requests that arrived after warm_s, throughput and server stats.  With
+    check > 0 the last `check` requests are verified against the oracle
+    (sampled windows) right after the run."""
     import numpy as np
     rng = np.random.default_rng(13)
     dbase, dsize = data_arena.data_ptr(), data_arena.numel()
     obase, osize = out_arena.data_ptr(), out_arena.numel()
-    jobs, in_bytes = [], []
+    jobs, in_bytes, where = [], [], []
     opos = 0
     for r in reqs:
         k, m, B = r["k"], r["m"], r["B"]
@@ -686,12 +738,19 @@ def serve_stream(xo, torch, reqs, plans, data_arena, out_arena, max_batch, slots
             jobs.append({"plan": plans[(k, m)], "op": xo.EC_OP_ENCODE, "blocks": blocks[:k],
                          "out": outs, "block_bytes": B})
         in_bytes.append(k * B)
+        where.append((blocks, outs))
     arr, keep = xo.make_jobs(jobs)
     server = xo.ec_server_create(hbm_budget=budget, max_batch=max_batch, slots=slots,
                                  idle_spin_us=idle_spin_us)
-    t_ticket = {}
-    lat = {}
+    t_ticket, lat, t_sub, failed = {}, {}, {}, 0
     n = len(reqs)
+
+    def drain():
+        nonlocal failed
+        for tk, us, st in xo.ec_server_poll_ex(server):
+            lat[t_ticket[tk]] = us
+            failed += st != xo.EC_OK
+
     t0 = time.perf_counter()
     next_poll = t0
     i = 0
@@ -702,44 +761,92 @@ def serve_stream(xo, torch, reqs, plans, data_arena, out_arena, max_batch, slots
             tk = xo.ec_server_submit_raw(server, arr[i])
             if tk:
                 t_ticket[tk] = i
+                t_sub[i] = now
                 i += 1
                 continue
         if now >= next_poll or now < target:
-            for tk, us in xo.ec_server_poll(server):
-                lat[t_ticket[tk]] = us
+            drain()
             next_poll = now + 0.001
     while len(lat) < n:
-        for tk, us in xo.ec_server_poll(server):
-            lat[t_ticket[tk]] = us
+        drain()
         time.sleep(0.0005)
     t_end = time.perf_counter()
     stats = xo.ec_server_stats_get(server)
     xo.ec_server_destroy(server)
     measured = [j for j in range(n) if reqs[j]["t"] >= warm_s]
     span = reqs[-1]["t"] - warm_s if n else 0.0
-    return {
+    done_at = [t_sub[j] + lat[j] / 1e6 for j in measured]
+    wall = (max(done_at) - min(t_sub[j] for j in measured)) if measured else 0.0
+    mbytes = sum(in_bytes[j] for j in measured)
+    out = {
         "p50_us": round(percentile([lat[j] for j in measured], 50), 1),
         "p99_us": round(percentile([lat[j] for j in measured], 99), 1),
         "p999_us": round(percentile([lat[j] for j in measured], 99.9), 1),
         "requests": len(measured),
-        "GBps_in": round(sum(in_bytes[j] for j in measured) / span / 1e9, 2) if span > 0 else None,
+        "offered_GBps": round(mbytes / span / 1e9, 2) if span > 0 else None,
+        "GBps_in": round(mbytes / wall / 1e9, 2) if wall > 0 else None,
+        "req_per_s": round(len(measured) / wall, 1) if wall > 0 else None,
         "batches": stats["batches"], "mean_batch": round(stats["completed"] / max(1, stats["batches"]), 2),
         "max_batch_seen": stats["max_batch_seen"], "rejected_retries": stats["rejected"],
-        "wall_s": round(t_end - t0, 2),
+        "failed": failed, "wall_s": round(t_end - t0, 2),
     }
+    if check:
+        out["parity"] = served_parity(xo, torch, reqs, where, data_arena, out_arena,
+                                      range(max(0, n - check), n))
+    return out
 
 
-def run_served(args):
+def served_parity(xo, torch, reqs, where, data_arena, out_arena, idx, L=64):
+    """Bit-exact check of served requests against the oracle on sampled
+    windows: encode outputs against the oracle's encode of the data window,
+    decode outputs against the oracle's decode map applied to the survivor
+    window (the survivors are arbitrary bytes; the map is linear)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(23)
+    dbase, obase = data_arena.data_ptr(), out_arena.data_ptr()
+
+    def window(arena, base, ptr, B, w0, Lw):
+        S = B // 8
+        o = ptr - base
+        return np.concatenate([arena[o + t * S + w0:o + t * S + w0 + Lw].cpu().numpy()
+                               for t in range(8)])
+
+    ok, n = True, 0
+    for j in idx:
+        r = reqs[j]
+        k, m, B = r["k"], r["m"], r["B"]
+        S = B // 8
+        Lw = min(L, S)
+        w0 = int(rng.integers(0, (S - Lw) // 16 + 1)) * 16
+        blocks, outs = where[j]
+        P = oracle.cauchy(k, m)
+        got = [window(out_arena, obase, o, B, w0, Lw) for o in outs]
+        if r["erasures"]:
+            er = list(r["erasures"])
+            surv = [i for i in range(k + m) if i not in er][:k]
+            ref = oracle.apply(oracle.decode_matrix(P, er),
+                               [window(data_arena, dbase, blocks[i], B, w0, Lw) for i in surv])
+        else:
+            ref = oracle.encode(P, [window(data_arena, dbase, blocks[i], B, w0, Lw)
+                                    for i in range(k)])
+        ok &= all(np.array_equal(a, b) for a, b in zip(got, ref))
+        n += 1
+    return ("bit-exact on sampled windows" if ok else "MISMATCH") + f" ({n} requests)"
+
+
+def served_leg(args, rates):
     """Served workload: Poisson arrivals, RS(10,4)/RS(6,3), objects log-uniform
     4 KiB-16 MiB (B = roundup(ceil(L/k), 128)), half of them decodes with
-    1..m random erasures; 32 GiB admission budget."""
+    1..m random erasures; 32 GiB admission budget.  For every arrival rate,
+    the continuous-batching server (512 requests per batch, 4 slots) and the
+    plain form (one request at a time on one slot) replay the same trace."""
     import torch
     import paper_2108_02692_gb300 as xo
     from paper_2108_02692_gb300 import synth
 
     torch.cuda.set_device(0)
     warm_s = 1.0
-    reqs = synth.served_requests(args.serve_seconds + warm_s, args.serve_rate)
     plans = {c: xo.ec_plan_create(*c) for c in ((10, 4), (6, 3))}
     tuned = {}
     if not args.no_tune:
@@ -757,37 +864,60 @@ def run_served(args):
     out_arena = torch.empty(48 << 30, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     spin = args.serve_idle_spin_us
-    served = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 512, 4, warm_s,
-                          idle_spin_us=spin)
-    plain = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 1, 1, warm_s,
-                         idle_spin_us=spin)
+    points = []
+    for rate in rates:
+        # long enough for config 5's rate; ~200k requests at higher rates
+        secs = args.serve_seconds if rate <= args.serve_rate else \
+            max(1.0, min(args.serve_seconds, 2e5 / rate))
+        reqs = synth.served_requests(secs + warm_s, rate)
+        served = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 512, 4, warm_s,
+                              idle_spin_us=spin, check=16)
+        plain = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 1, 1, warm_s,
+                             idle_spin_us=spin, check=16)
+        points.append({"rate": rate, "seconds": secs, "served": served, "plain": plain,
+                       "p99_plain_over_served": round(plain["p99_us"] / served["p99_us"], 2)})
     for p in plans.values():
         xo.ec_plan_destroy(p)
+    del data_arena, out_arena
+    torch.cuda.empty_cache()
+    ok = all(pt[f]["parity"].startswith("bit-exact") and pt[f]["failed"] == 0
+             for pt in points for f in ("served", "plain"))
+    return {
+        "workload": "served: Poisson arrivals, RS(10,4)/RS(6,3), objects log-uniform "
+                    "4 KiB-16 MiB, 50% decodes with 1..m erasures, 32 GiB admission budget; "
+                    "served = continuous batching (512 per batch, 4 slots), plain = one request "
+                    "at a time on one slot",
+        "autotune": tuned or None, "warm_s": round(warm_time, 1),
+        "points": points,
+        "parity": "bit-exact on sampled windows" if ok else "MISMATCH",
+        "device_status": xo.ec_device_status(),
+    }
+
+
+def run_served(args):
+    rates = [float(x) for x in args.serve_rates.split(",")] if args.serve_rates \
+        else [args.serve_rate]
+    leg = served_leg(args, rates)
+    head = leg["points"][0]
     out = {
-        "metric": METRIC, "value": served["GBps_in"], "unit": "GB/s", "n_gpus": 1,
+        "metric": METRIC, "value": head["served"]["GBps_in"], "unit": "GB/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (SplitMix64 bytes generated on the device)",
-        "config": {"workload": f"served: Poisson {args.serve_rate:.0f} req/s for "
-                               f"{args.serve_seconds:.0f} s (+{warm_s:.0f} s warm-up), RS(10,4)/RS(6,3), "
-                               "objects log-uniform 4 KiB-16 MiB, 50% decodes with 1..m erasures, "
-                               "32 GiB admission budget", "autotune": tuned or None},
-        "served": served,
-        "plain": plain,
-        "p99_plain_over_served": round(plain["p99_us"] / served["p99_us"], 2),
-        "warm_s": round(warm_time, 1),
-        "device_status": xo.ec_device_status(),
+        "config": {"workload": f"served: Poisson {head['rate']:.0f} req/s for "
+                               f"{head['seconds']:.0f} s (+1 s warm-up); " + leg["workload"]},
+        "served": leg,
     }
     print(json.dumps(out))
 
 
-def run_batched(args):
+def batched_leg(args):
     """Batched workload: mixed codes RS(6,3)/(8,4)/(10,4)/(12,4), block sizes
     log-uniform 4 KiB-8 MiB, half of the stripes decoded with random
-    erasures, all in one batch run, against one launch per stripe."""
+    erasures, all in one batch run (replayed as a CUDA graph), against one
+    launch per stripe."""
     import numpy as np
     import torch
-    import oracle
     import paper_2108_02692_gb300 as xo
     from paper_2108_02692_gb300 import synth
 
@@ -865,6 +995,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms = g0.elapsed_time(g1) / reps
     del graph
+    batch_status = xo.ec_batch_status(batch)
     # plain: one launch per stripe with the same compiled programs
     singles = [xo.ec_batch_create([j]) for j in jobs]
     for b in singles[:64]:
@@ -881,28 +1012,42 @@ def run_batched(args):
     xo.ec_batch_destroy(batch)
     parity = batched_parity(mix, where, arena, n)
     peak, _ = measured_peaks()
-    print(json.dumps({
-        "metric": METRIC, "value": round(bytes_in / (ms / 1e3) / 1e9, 2), "unit": "GB/s",
-        "n_gpus": 1, "steps": reps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic (SplitMix64 bytes generated on the device)",
-        "config": {"workload": f"batched: {n} stripes, RS(6,3)/(8,4)/(10,4)/(12,4), blocks "
-                               "log-uniform 4 KiB-8 MiB, ~50% decodes with 1..m erasures; one "
-                               "ec_batch_run replayed as a CUDA graph",
-                   "input_bytes": bytes_in, "moved_bytes": moved, "autotune": tuned or None},
+    for p in plans.values():
+        xo.ec_plan_destroy(p)
+    del arena
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"batched: {n} stripes, RS(6,3)/(8,4)/(10,4)/(12,4), blocks log-uniform "
+                    "4 KiB-8 MiB, ~50% decodes with 1..m erasures; one ec_batch_run replayed "
+                    "as a CUDA graph",
+        "value": round(bytes_in / (ms / 1e3) / 1e9, 2), "unit": "GB/s",
+        "ms_per_step": round(ms, 3), "steps": reps,
+        "input_bytes": bytes_in, "moved_bytes": moved, "autotune": tuned or None,
         "eager": {"value": round(bytes_in / (ms_eager / 1e3) / 1e9, 2),
                   "ms_per_step": round(ms_eager, 3)},
         "roofline": {"bound": "hbm", "achieved": round(moved / (ms / 1e3) / 1e9, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(moved / (ms / 1e3) / 1e9 / peak, 4)},
-        "plain": {"value": round(bytes_in / (ms_plain / 1e3) / 1e9, 2), "ms_per_step": round(ms_plain, 2),
-                  "launches_per_step": n},
+                     "unit": "GB/s", "frac": round(moved / (ms / 1e3) / 1e9 / peak, 4),
+                     "bytes_per_step": moved},
+        "plain": {"value": round(bytes_in / (ms_plain / 1e3) / 1e9, 2),
+                  "ms_per_step": round(ms_plain, 2), "launches_per_step": n},
         "batched_over_plain": round(ms_plain / ms, 2),
         "batch": info, "prepare_s": round(prep, 1),
-        "parity": parity,
+        "parity": parity, "batch_status": batch_status,
         "device_status": xo.ec_device_status(),
+    }
+
+
+def run_batched(args):
+    leg = batched_leg(args)
+    print(json.dumps({
+        "metric": METRIC, "value": leg["value"], "unit": "GB/s",
+        "n_gpus": 1, "steps": leg["steps"], "warmup": args.warmup,
+        "ms_per_step": leg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (SplitMix64 bytes generated on the device)",
+        "config": {"workload": leg["workload"]},
+        "batched": leg,
     }))
-    for p in plans.values():
-        xo.ec_plan_destroy(p)
 
 
 def batched_parity(mix, where, arena, n, samples=24, L=64):

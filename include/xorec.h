@@ -23,7 +23,9 @@
  * programs and device state and must outlive the GPU work queued with it.
  * Calls that take a stream are asynchronous with respect to the host;
  * argument errors are returned synchronously.  Errors found by kernels
- * (a bounded wait that timed out) are reported by ec_device_status().
+ * (a bounded wait that timed out) are reported by ec_device_status(); a
+ * batch also records them in its own word (ec_batch_status) and a server
+ * fails the requests of the affected batch (ec_server_poll_ex).
  * ec_last_error() returns a thread-local message for the last failure.
  *
  * Threads.  Encode, decode, batch and serving calls may run from several
@@ -188,6 +190,17 @@ ec_status ec_plan_info(ec_plan *plan, const int *erasures, int n_erasures,
 ec_status ec_plan_kernel_source(ec_plan *plan, const int *erasures, int n_erasures, char *buf,
                                 size_t len, size_t *need);
 
+/* CUDA C++ source of the multi-program module that batched launches compile
+ * for the decoders of the given erasure sets (layout of ec_decode_prepare;
+ * n_sets == 0: the encoder alone), at the plan's module launch shape: the
+ * tile pipeline with its work queue, every program's straight-line
+ * statements and the kernel entry.  The programs must share their input
+ * count.  Copies at most len - 1 characters and a NUL into buf (NULL: none);
+ * *need receives the full length including the NUL.  Host only; for
+ * inspection and for checking the compile without a GPU. */
+ec_status ec_plan_module_source(ec_plan *plan, const int *sets, const int *counts, int n_sets,
+                                char *buf, size_t len, size_t *need);
+
 /* Copy the interpreter instruction stream of the encoder (erasures == NULL)
  * or of a decoder into buf (len 16-bit words); *need receives the length.
  * Stream format, statement by statement: n_args; n_outs | has_slot << 15;
@@ -217,7 +230,9 @@ ec_status ec_encode(ec_plan *plan, const uint8_t *const *data, uint8_t *const *p
  * each call overwrites it, so calls whose GPU work overlaps race.  The
  * first call on each device performs that device's set-up (looks up the
  * array's address, clears its status word) and should come before any
- * stream capture.  Always uses the interpreter executor.  Fails with
+ * stream capture.  Always uses the interpreter executor.  A bounded wait
+ * of its kernel that gives up is recorded in the array's status word, which
+ * ec_device_status reads beside the device's own.  Fails with
  * EC_EINVAL when k + m > EC_NOALLOC_MAX_BLOCKS or the encoding program is
  * longer than EC_NOALLOC_MAX_CODE_WORDS.  Same arguments as ec_encode. */
 ec_status ec_encode_noalloc(ec_plan *plan, const uint8_t *const *data, uint8_t *const *parity,
@@ -344,11 +359,20 @@ typedef struct {
  * while the batch runs. */
 ec_status ec_batch_create(const ec_job *jobs, int n_jobs, int executor, ec_batch **out);
 /* Enqueue the batch on `stream`: one persistent launch per module plus at
- * most one interpreter launch.  Allocates nothing (capturable). */
+ * most one interpreter launch.  Allocates nothing (capturable).  Large
+ * launches split their work items into one contiguous range per SM; the
+ * CTAs of an SM start on its range and then help with the others, so each
+ * SM runs few distinct programs at a time. */
 ec_status ec_batch_run(ec_batch *batch, void *stream);
+/* The batch's own status word: *status = 0 or EC_ETIMEOUT when a bounded
+ * wait of one of its runs gave up since the last reset (that run's outputs
+ * are incomplete).  Synchronises the current device first; reset != 0
+ * clears the word.  The device's word (ec_device_status) is set as well. */
+ec_status ec_batch_status(ec_batch *batch, int *status, int reset);
 ec_status ec_batch_info_get(const ec_batch *batch, ec_batch_info *out);
 void ec_batch_destroy(ec_batch *batch);
-/* create + run + synchronise + destroy. */
+/* create + run + synchronise + destroy; EC_ETIMEOUT when a bounded wait of
+ * the run gave up. */
 ec_status ec_run_batch(const ec_job *jobs, int n_jobs, void *stream);
 
 /* ------------------------------------------------------------------ serving
@@ -380,7 +404,9 @@ typedef struct {
 } ec_server_opts;
 
 typedef struct {
-  long long submitted, completed, rejected, failed;
+  long long submitted, completed, rejected, failed;  /* completed: tickets returned,
+                                      failed ones included; failed: returned with
+                                      a status other than EC_OK                 */
   long long batches, max_batch_seen;
   long long bytes_in, bytes_out;   /* block bytes read / written by completed requests */
   long long admitted_bytes;        /* currently admitted                             */
@@ -401,16 +427,28 @@ ec_status ec_server_submit(ec_server *server, const ec_job *job, uint64_t *ticke
  * the server never issued. */
 ec_status ec_server_cancel(ec_server *server, uint64_t ticket);
 /* Up to max completed tickets (and their latency from submission, in
- * microseconds) since the last call; *n_done receives the count. */
+ * microseconds) since the last call; *n_done receives the count.  The
+ * arrays are filled in every case; the return value is the status of the
+ * first returned request that failed (EC_OK when none did). */
 ec_status ec_server_poll(ec_server *server, uint64_t *tickets, double *latency_us, int max,
                          int *n_done);
+/* Same, with each request's own status in status[i] (NULL: not wanted):
+ * EC_OK; EC_ETIMEOUT when a bounded wait of its batch gave up (each slot has
+ * its own status word, cleared at every dispatch); EC_ENOMEM, EC_ENOTSUP or
+ * EC_ECUDA when its batch could not be launched.  A failed request's
+ * outputs are incomplete; it is returned only after every kernel of its
+ * batch has finished, and its admitted bytes are released.  Returns EC_OK
+ * unless the CUDA context failed. */
+ec_status ec_server_poll_ex(ec_server *server, uint64_t *tickets, double *latency_us, int *status,
+                            int max, int *n_done);
 ec_status ec_server_stats_get(ec_server *server, ec_server_stats *out);
 /* Finish every admitted request, then free the server. */
 void ec_server_destroy(ec_server *server);
 
 /* Device status word written by kernels whose bounded waits gave up:
  * *status = 0 (ok) or EC_ETIMEOUT.  reset != 0 clears it.  Synchronises the
- * current device. */
+ * current device.  Also reads (and with reset clears) the status word that
+ * ec_encode_noalloc's kernels write in its static scratch array. */
 ec_status ec_device_status(int *status, int reset);
 
 /* Diagnostics: launch a one-thread kernel that waits, with the same bounded
@@ -434,6 +472,14 @@ ec_status ec_program_check(const uint16_t *code, size_t len, int n_in, int n_out
  * n = 0 clears it.  No GPU fault is involved.  The paper has no
  * counterpart. */
 ec_status ec_debug_fail_alloc(int n);
+
+/* Fault injection for tests: each of the next n calls of ec_batch_run,
+ * serving dispatches and ec_encode_noalloc first enqueues, on its stream,
+ * the bounded-wait self-test (ec_selftest_wait_timeout) aimed at the status
+ * words that call's kernels use, so it reports EC_ETIMEOUT as if one of its
+ * waits had given up (the real work still runs).  n = 0 clears it.  No GPU
+ * fault is involved.  The paper has no counterpart. */
+ec_status ec_debug_inject_timeout(int n);
 
 /* Thread-local message of the last failure ("" if none). */
 const char *ec_last_error(void);

@@ -155,6 +155,19 @@ def ec_plan_kernel_source(plan: int, erasures=None) -> str:
     return buf.value.decode()
 
 
+def ec_plan_module_source(plan: int, sets=None) -> str:
+    """CUDA source of the batch module compiled for the decoders of `sets`
+    (erasure lists), or for the encoder when `sets` is empty."""
+    sets = sets or []
+    flat = _int_array([int(x) for st in sets for x in st]) if sets else None
+    counts = _int_array([len(st) for st in sets]) if sets else None
+    need = ctypes.c_size_t()
+    _check(lib().ec_plan_module_source(plan, flat, counts, len(sets), None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().ec_plan_module_source(plan, flat, counts, len(sets), buf, need.value, None))
+    return buf.value.decode()
+
+
 def ec_plan_autotune(plan: int, block_bytes: int, n_stripes: int = 16, stream: int = 0) -> dict:
     r = _abi.TuneResult()
     _check(lib().ec_plan_autotune(plan, block_bytes, n_stripes, stream or None, ctypes.byref(r)))
@@ -170,6 +183,10 @@ def ec_program_check(code, n_in: int, n_out: int, n_slots: int) -> None:
 
 def ec_debug_fail_alloc(n: int) -> None:
     _check(lib().ec_debug_fail_alloc(n))
+
+
+def ec_debug_inject_timeout(n: int) -> None:
+    _check(lib().ec_debug_inject_timeout(n))
 
 
 def ec_plan_set_launch(plan: int, threads: int, reg_budget: int) -> None:
@@ -259,6 +276,12 @@ def ec_batch_run(batch: int, stream: int = 0) -> None:
     _check(lib().ec_batch_run(batch, stream or None))
 
 
+def ec_batch_status(batch: int, reset: bool = False) -> int:
+    st = ctypes.c_int()
+    _check(lib().ec_batch_status(batch, ctypes.byref(st), 1 if reset else 0))
+    return st.value
+
+
 def ec_batch_info_get(batch: int) -> dict:
     i = _abi.BatchInfo()
     _check(lib().ec_batch_info_get(batch, ctypes.byref(i)))
@@ -331,6 +354,17 @@ def ec_server_poll(server: int, max_n: int = 4096):
     n = ctypes.c_int()
     _check(lib().ec_server_poll(server, tickets, lat, max_n, ctypes.byref(n)))
     return [(tickets[i], lat[i]) for i in range(n.value)]
+
+
+def ec_server_poll_ex(server: int, max_n: int = 4096):
+    """Completed requests since the last poll: (ticket, latency_us, status)
+    with status EC_OK or the error the request failed with."""
+    tickets = (ctypes.c_uint64 * max_n)()
+    lat = (ctypes.c_double * max_n)()
+    st = (ctypes.c_int * max_n)()
+    n = ctypes.c_int()
+    _check(lib().ec_server_poll_ex(server, tickets, lat, st, max_n, ctypes.byref(n)))
+    return [(tickets[i], lat[i], st[i]) for i in range(n.value)]
 
 
 def ec_server_stats_get(server: int) -> dict:

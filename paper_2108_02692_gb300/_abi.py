@@ -94,6 +94,8 @@ SIGNATURES = {
     "ec_plan_destroy": (None, [c_vp]),
     "ec_plan_matrix": (c_int, [c_vp, u8p]),
     "ec_plan_info": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ProgramInfo)]),
+    "ec_plan_module_source": (c_int, [c_vp, intp, intp, c_int, ctypes.c_char_p, c_size,
+                                      ctypes.POINTER(c_size)]),
     "ec_plan_program": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ctypes.c_uint16), c_size,
                                 ctypes.POINTER(c_size)]),
     "ec_plan_kernel_source": (c_int, [c_vp, intp, c_int, ctypes.c_char_p, c_size,
@@ -111,10 +113,12 @@ SIGNATURES = {
     "ec_plan_set_launch": (c_int, [c_vp, c_int, c_int]),
     "ec_program_check": (c_int, [ctypes.POINTER(ctypes.c_uint16), c_size, c_int, c_int, c_int]),
     "ec_debug_fail_alloc": (c_int, [c_int]),
+    "ec_debug_inject_timeout": (c_int, [c_int]),
     "ec_plan_set_executor": (c_int, [c_vp, c_int]),
     "ec_batch_create": (c_int, [ctypes.POINTER(Job), c_int, c_int, ctypes.POINTER(c_vp)]),
     "ec_batch_run": (c_int, [c_vp, c_vp]),
     "ec_batch_info_get": (c_int, [c_vp, ctypes.POINTER(BatchInfo)]),
+    "ec_batch_status": (c_int, [c_vp, intp, c_int]),
     "ec_batch_destroy": (None, [c_vp]),
     "ec_run_batch": (c_int, [ctypes.POINTER(Job), c_int, c_vp]),
     "ec_server_create": (c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(c_vp)]),
@@ -123,6 +127,8 @@ SIGNATURES = {
     "ec_server_cancel": (c_int, [c_vp, c_u64]),
     "ec_server_poll": (c_int, [c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(ctypes.c_double),
                                c_int, intp]),
+    "ec_server_poll_ex": (c_int, [c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(ctypes.c_double),
+                                  intp, c_int, intp]),
     "ec_server_stats_get": (c_int, [c_vp, ctypes.POINTER(ServerStats)]),
     "ec_server_destroy": (None, [c_vp]),
     "ec_device_status": (c_int, [intp, c_int]),

@@ -56,6 +56,7 @@ struct Launch {
   int max_in = 0, max_slots = 0;
   size_t smem = 0;
   int grid = 0;
+  int n_ranges = 1;                    // per-SM item ranges (work-queue heads)
 };
 
 template <class F>
@@ -86,7 +87,9 @@ struct ec_batch {
   std::vector<cudaEvent_t> done;
   cudaEvent_t fork = nullptr;
   int chunk = 8;
-  xk::u64* d_queues = nullptr;         // one work-queue head per launch
+  int queue_stride = 1;                // work-queue heads per launch (its item ranges)
+  xk::u64* d_queues = nullptr;         // queue_stride heads per launch, then the status word
+  int* d_status = nullptr;             // the batch's own status word (set on a timeout)
   xk::StripeDesc* d_descs = nullptr;
   xk::u64* d_blocks = nullptr;
   xk::TensorMap* d_maps = nullptr;     // per-block tensor maps of the stripes' inputs
@@ -234,12 +237,8 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
     std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
     ec_plan* plan = to_compile[i].first;
     const int n_in = ps.front()->n_in;
-    // default shapes (no tuned or pinned shape, no EC_BATCH_MINB) may raise
-    // the register cap of a module that spills; a tuned shape is kept
-    const bool default_shape = !(plan->tuned_threads > 0 && plan->tuned_minb > 0) &&
-                               env_int("EC_BATCH_MINB", 0) <= 0;
     mods[i] = jit_compile_module(ps, plan_module_threads(plan, n_in), plan_module_minb(plan, n_in),
-                                 &errs[i], default_shape);
+                                 &errs[i], env_int("EC_MODULE_NO_SPILL", 0) != 0);
   });
   if (built) *built = static_cast<int>(to_compile.size());
   for (size_t i = 0; i < to_compile.size(); ++i) {
@@ -275,6 +274,23 @@ bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_
   if (*smem > smem_optin) return false;
   *per_sm = std::max(1, interp_batch_max_ctas_per_sm(threads, *smem));
   return true;
+}
+
+// Item ranges of a batched launch (one work-queue head each, see
+// run_batch_pipeline): one per SM when every SM's range holds at least four
+// chunks per resident CTA, else a single queue.  EC_BATCH_RANGES overrides
+// (1 = a single queue).
+void set_ranges(xk::BatchParams* bp, long long n_items, int n_ranges) {
+  bp->n_ranges = std::max(1, n_ranges);
+  bp->range_len = n_items / bp->n_ranges;
+  bp->range_rem = static_cast<int>(n_items % bp->n_ranges);
+}
+
+int batch_ranges(long long n_items, int sms, int per_sm, int chunk) {
+  const int forced = env_int("EC_BATCH_RANGES", 0);
+  if (forced > 0) return std::min(forced, std::max(1, sms));
+  const long long per_range = 4ll * std::max(1, per_sm) * std::max(1, chunk);
+  return n_items >= per_range * sms ? std::max(1, sms) : 1;
 }
 
 }  // namespace xorec
@@ -343,6 +359,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   b->device = di.device;
   b->status = di.status;
   b->chunk = std::max(1, env_int("EC_BATCH_CHUNK", 2));
+  b->queue_stride = std::max(1, di.sms);
   std::map<void*, int> launch_of;
   for (auto& e : ents) {
     void* mod = compiled ? e.prog->mod : nullptr;
@@ -451,7 +468,9 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   // 6. device copies (owned by the batch)
   if (!ents.empty()) {
     if (xorec::dev_malloc(&b->d_descs, descs.size() * sizeof(xk::StripeDesc)) != cudaSuccess ||
-        xorec::dev_malloc(&b->d_queues, b->launches.size() * sizeof(xk::u64)) != cudaSuccess ||
+        xorec::dev_malloc(&b->d_queues,
+                          (b->launches.size() * b->queue_stride + 1) * sizeof(xk::u64)) !=
+            cudaSuccess ||
         xorec::dev_malloc(&b->d_blocks, std::max<size_t>(1, blocks.size()) * sizeof(xk::u64)) !=
             cudaSuccess) {
       cudaGetLastError();
@@ -463,6 +482,12 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       cudaGetLastError();
       free_batch(b);
       return fail(EC_ENOMEM, "device allocation of the batch tensor maps failed");
+    }
+    b->d_status = reinterpret_cast<int*>(b->d_queues + b->launches.size() * b->queue_stride);
+    if (cudaMemset(b->d_status, 0, sizeof(xk::u64)) != cudaSuccess) {
+      cudaGetLastError();
+      free_batch(b);
+      return fail(EC_ECUDA, "clearing the batch status word failed");
     }
     for (auto& d : descs)
       d.blocks = b->d_blocks + reinterpret_cast<uintptr_t>(d.blocks) / sizeof(xk::u64);
@@ -497,10 +522,11 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     }
     const long long grid = static_cast<long long>(di.sms) * std::max(1, per_sm);
     L.grid = static_cast<int>(std::min<long long>(grid, std::max<long long>(1, L.n_items)));
+    L.n_ranges = xorec::batch_ranges(L.n_items, di.sms, per_sm, b->chunk);
     if (env_int("XOREC_LOG", 0))
-      std::fprintf(stderr, "[xorec] batch launch: %s items=%lld max_in=%d smem=%zu ctas/sm=%d grid=%d regs=%d\n",
+      std::fprintf(stderr, "[xorec] batch launch: %s items=%lld max_in=%d smem=%zu ctas/sm=%d grid=%d regs=%d ranges=%d\n",
                    L.mod ? "module" : "interp", L.n_items, L.max_in, L.smem, per_sm, L.grid,
-                   L.mod ? xorec::jit_module_regs(L.mod) : 0);
+                   L.mod ? xorec::jit_module_regs(L.mod) : 0, L.n_ranges);
   }
   // largest launches first; lanes for concurrent launches
   std::stable_sort(b->launches.begin(), b->launches.end(),
@@ -551,8 +577,12 @@ ec_status ec_batch_run(ec_batch* b, void* stream) {
   if (!b) return fail(EC_EINVAL, "NULL batch");
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
   if (b->launches.empty()) return EC_OK;
-  if (cudaMemsetAsync(b->d_queues, 0, b->launches.size() * sizeof(xk::u64), caller) != cudaSuccess)
+  if (cudaMemsetAsync(b->d_queues, 0, b->launches.size() * b->queue_stride * sizeof(xk::u64),
+                      caller) != cudaSuccess)
     return fail(EC_ECUDA, "resetting the work queues failed");
+  if (xorec::take_injected_timeout() &&
+      !xorec::launch_selftest_wait_to(caller, b->status, b->d_status))
+    return EC_ECUDA;
   const bool fan = !b->lanes.empty();
   if (fan) {
     if (cudaEventRecord(b->fork, caller) != cudaSuccess) return fail(EC_ECUDA, "cudaEventRecord failed");
@@ -568,11 +598,13 @@ ec_status ec_batch_run(ec_batch* b, void* stream) {
     bp.stripes = b->d_descs + L.stripe_begin;
     bp.n_stripes = L.n_stripes;
     bp.chunk = b->chunk;
-    bp.queue = b->d_queues + li;
+    bp.queue = b->d_queues + li * b->queue_stride;
+    xorec::set_ranges(&bp, L.n_items, L.n_ranges);
     bp.n_items = L.n_items;
     bp.T = 4 * L.threads;
     bp.max_in = L.max_in;
     bp.status = b->status;
+    bp.local_status = b->d_status;
     const bool ok = L.mod ? xorec::jit_module_launch(L.mod, bp, L.grid, L.smem, st)
                           : xorec::launch_interp_batch(bp, L.threads, L.grid, L.smem, st);
     if (!ok) return EC_ECUDA;
@@ -584,6 +616,58 @@ ec_status ec_batch_run(ec_batch* b, void* stream) {
         return fail(EC_ECUDA, "joining the batch lanes failed");
     }
   }
+  return EC_OK;
+}
+
+ec_status ec_plan_module_source(ec_plan* plan, const int* sets, const int* counts, int n_sets,
+                                char* buf, size_t len, size_t* need) {
+  if (!plan || (n_sets > 0 && (!sets || !counts)) || n_sets < 0)
+    return fail(EC_EINVAL, "bad argument");
+  std::vector<const Program*> progs;
+  if (n_sets == 0) progs.push_back(plan->enc.get());
+  size_t off = 0;
+  for (int i = 0; i < n_sets; ++i) {
+    std::vector<int> er;
+    ec_status s = canon_erasures(plan, sets + off, counts[i], &er);
+    if (s != EC_OK) return s;
+    off += counts[i];
+    Program* p = nullptr;
+    s = get_decode_program(plan, er, &p);
+    if (s != EC_OK) return s;
+    progs.push_back(p);
+  }
+  const int n_in = progs.front()->n_in;
+  for (const Program* p : progs)
+    if (p->n_in != n_in) return fail(EC_EINVAL, "programs of one module share their input count");
+  const std::string src = xorec::jit_module_source(progs, xorec::plan_module_threads(plan, n_in),
+                                                   xorec::plan_module_minb(plan, n_in));
+  if (need) *need = src.size() + 1;
+  if (buf && len > 0) {
+    const size_t n = std::min(len - 1, src.size());
+    std::memcpy(buf, src.data(), n);
+    buf[n] = '\0';
+  }
+  return EC_OK;
+}
+
+ec_status ec_batch_status(ec_batch* b, int* status, int reset) {
+  if (!b || !status) return fail(EC_EINVAL, "NULL argument");
+  *status = 0;
+  if (!b->d_status) return EC_OK;   // an empty batch launches nothing
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EC_ECUDA, "cudaDeviceSynchronize failed");
+  }
+  int v = 0;
+  if (cudaMemcpy(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EC_ECUDA, "reading the batch status word failed");
+  }
+  if (reset && cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EC_ECUDA, "resetting the batch status word failed");
+  }
+  *status = v == xk::XK_STATUS_TIMEOUT ? EC_ETIMEOUT : 0;
   return EC_OK;
 }
 
@@ -605,6 +689,15 @@ ec_status ec_run_batch(const ec_job* jobs, int n_jobs, void* stream) {
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess && s == EC_OK) {
     cudaGetLastError();
     s = fail(EC_ECUDA, "batch execution failed");
+  }
+  if (s == EC_OK && b->d_status) {
+    int v = 0;
+    if (cudaMemcpy(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      s = fail(EC_ECUDA, "reading the batch status word failed");
+    } else if (v == xk::XK_STATUS_TIMEOUT) {
+      s = fail(EC_ETIMEOUT, "a bounded wait of the batch timed out; its outputs are incomplete");
+    }
   }
   ec_batch_destroy(b);
   return s;

@@ -31,6 +31,15 @@ bool take_injected_alloc_failure() {
   return false;
 }
 
+std::atomic<int> g_inject_timeouts{0};
+
+bool take_injected_timeout() {
+  int v = g_inject_timeouts.load(std::memory_order_relaxed);
+  while (v > 0)
+    if (g_inject_timeouts.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return true;
+  return false;
+}
+
 static std::mutex g_dev_mu;
 static DeviceInfo g_dev[64];
 
@@ -438,6 +447,11 @@ ec_status ec_debug_fail_alloc(int n) {
   return EC_OK;
 }
 
+ec_status ec_debug_inject_timeout(int n) {
+  xorec::g_inject_timeouts.store(std::max(0, n));
+  return EC_OK;
+}
+
 const char* ec_version(void) { return "xorec 0.1 (sm_103a)"; }
 
 ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix,
@@ -781,9 +795,13 @@ ec_status ec_device_status(int* status, int reset) {
   int v = 0;
   if (cudaMemcpy(&v, di.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(EC_ECUDA, "reading the status word failed");
-  *status = v == xk::XK_STATUS_TIMEOUT ? EC_ETIMEOUT : 0;
   if (reset && cudaMemset(di.status, 0, sizeof(int)) != cudaSuccess)
     return fail(EC_ECUDA, "resetting the status word failed");
+  // the allocation-free encoder keeps its own word in its static scratch
+  int w = 0;
+  if (xorec::noalloc_status(di.device, &w, reset != 0) && w == xk::XK_STATUS_TIMEOUT)
+    v = w;
+  *status = v == xk::XK_STATUS_TIMEOUT ? EC_ETIMEOUT : 0;
   return EC_OK;
 }
 

@@ -106,12 +106,17 @@ __global__ void __launch_bounds__(256) interp_batch_kernel(BatchParams p) {
 // mbar_wait, on an mbarrier whose phase nothing completes; the wait gives
 // up after its limit, the kernel records the timeout like the pipelines do
 // and returns.
-__global__ void selftest_wait_kernel(int* status) {
+// `also` (may be null) is a second status word, written the way batched
+// launches write their batch's or slot's own word.
+__global__ void selftest_wait_kernel(int* status, int* also) {
   __shared__ __align__(8) u64 bar;
   if (threadIdx.x != 0) return;
   mbar_init(smem_addr(&bar), 1);
   fence_mbar_init();
-  if (!mbar_wait(smem_addr(&bar), 0)) atomicExch(status, XK_STATUS_TIMEOUT);
+  if (!mbar_wait(smem_addr(&bar), 0)) {
+    if (status) atomicExch(status, XK_STATUS_TIMEOUT);
+    if (also) *reinterpret_cast<volatile int*>(also) = XK_STATUS_TIMEOUT;
+  }
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014) in counter form: byte n of stream
@@ -217,7 +222,11 @@ bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_
 bool launch_selftest_wait(cudaStream_t stream) {
   DeviceInfo di;
   if (!device_info(&di)) return false;
-  selftest_wait_kernel<<<1, 32, 0, stream>>>(di.status);
+  return launch_selftest_wait_to(stream, di.status, nullptr);
+}
+
+bool launch_selftest_wait_to(cudaStream_t stream, int* status, int* also) {
+  selftest_wait_kernel<<<1, 32, 0, stream>>>(status, also);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("self-test launch failed: ") + cudaGetErrorString(e));

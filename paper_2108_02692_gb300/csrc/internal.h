@@ -61,6 +61,12 @@ cudaError_t host_malloc_pinned(T** p, size_t bytes) {
   if (take_injected_alloc_failure()) return cudaErrorMemoryAllocation;
   return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
 }
+// Pinned host memory that kernels address directly (cudaHostGetDevicePointer).
+template <class T>
+cudaError_t host_malloc_mapped(T** p, size_t bytes) {
+  if (take_injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(reinterpret_cast<void**>(p), bytes, cudaHostAllocMapped);
+}
 
 // NVTX range for the duration of a scope (plan, compile, encode, decode,
 // batch and serving steps show up on an nsys or ncu timeline).
@@ -148,7 +154,8 @@ void jit_release(Program* p);
 int jit_regs(const Program* p);
 std::string jit_source(const Program& p, int threads);
 void* jit_compile_module(const std::vector<const Program*>& progs, int threads, int minb,
-                         std::string* err, bool raise_cap_on_spill = false);
+                         std::string* err, bool no_spill);
+std::string jit_module_source(const std::vector<const Program*>& progs, int threads, int minb);
 int jit_module_ctas_per_sm(void* mod, size_t smem);
 bool jit_module_launch(void* mod, const xk::BatchParams& bp, int grid, size_t smem,
                        cudaStream_t stream);
@@ -166,9 +173,24 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
                           int* built);
 bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
                         size_t* smem, int* per_sm);
+int batch_ranges(long long n_items, int sms, int per_sm, int chunk);
+// Split a launch's items into n_ranges contiguous ranges (BatchParams).
+void set_ranges(xk::BatchParams* bp, long long n_items, int n_ranges);
 
-// Bounded-wait self-test (executor.cu).
+// Bounded-wait self-test (executor.cu): a one-thread kernel whose wait
+// gives up after its limit and records the timeout in `status` (the
+// device's word) and, when not null, `also` (a batch's, slot's or the
+// allocation-free encoder's own word).
 bool launch_selftest_wait(cudaStream_t stream);
+bool launch_selftest_wait_to(cudaStream_t stream, int* status, int* also);
+// ec_debug_inject_timeout: true (once per count) when the next batched run,
+// serving dispatch or allocation-free encode should be preceded by the
+// self-test wait on its status words.
+bool take_injected_timeout();
+
+// Status word of the allocation-free encoder on device `dev` (noalloc.cu):
+// false when that device has not run it yet; reset clears the word.
+bool noalloc_status(int dev, int* value, bool reset);
 
 // Synthetic input generator (executor.cu).
 bool launch_synth_fill(uint8_t* dst, size_t n, uint64_t seed, uint64_t offset,

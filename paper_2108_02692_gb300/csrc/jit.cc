@@ -281,7 +281,6 @@ static bool jit_set_smem(JitKernel* jk, size_t smem) {
   return true;
 }
 
-// NVRTC: source -> cubin for the current device -> loaded kernel `name`.
 // Largest "N bytes spill stores" figure of a ptxas report (0 if none).
 static long spill_stores(const std::string& log) {
   long most = 0;
@@ -294,8 +293,9 @@ static long spill_stores(const std::string& log) {
   return most;
 }
 
-// Compile and load; with spill_bytes, ptxas also reports its register use
-// and *spill_bytes receives the bytes it spilled (per thread).
+// NVRTC: source -> cubin for the current device -> loaded kernel `name`.
+// With spill_bytes, ptxas also reports and *spill_bytes receives the bytes
+// it spilled per thread.
 static JitKernel* compile_and_load(const std::string& src, const char* name, int threads,
                                    std::string* err, long* spill_bytes = nullptr) {
   xorec::TraceRange trace_("xorec nvrtc compile");
@@ -371,26 +371,27 @@ bool jit_compile(Program* p, int threads, std::string* err) {
   return true;
 }
 
-// A module of programs sharing n_in (batched launches).
+// A module of programs sharing n_in (batched launches).  With
+// no_spill, a module that ptxas reports spilling is compiled again with one
+// resident CTA per SM fewer (a higher register cap), down to one.
 void* jit_compile_module(const std::vector<const Program*>& progs, int threads, int minb,
-                         std::string* err, bool raise_cap_on_spill) {
+                         std::string* err, bool no_spill) {
   if (progs.empty()) {
     *err = "empty module";
     return nullptr;
   }
-  if (!raise_cap_on_spill)
-    return compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads, err);
-  // The batch pipeline keeps more state than a single launch's, so a module
-  // can spill at the default register cap its programs fit alone; then it is
-  // compiled again with one resident CTA per SM fewer, which raises the cap.
   for (;;) {
     long spill = 0;
-    JitKernel* jk =
-        compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads, err, &spill);
+    JitKernel* jk = compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads,
+                                     err, no_spill ? &spill : nullptr);
     if (!jk || spill == 0 || minb <= 1) return jk;
     jit_module_release(jk);
     --minb;
   }
+}
+
+std::string jit_module_source(const std::vector<const Program*>& progs, int threads, int minb) {
+  return progs.empty() ? std::string() : gen_module_source(progs, threads, minb);
 }
 
 int jit_module_ctas_per_sm(void* mod, size_t smem) {

@@ -15,7 +15,10 @@
 // The first call on a device does the set-up for that device (looks up the
 // array's device address and clears the status word); make that first call
 // before any stream capture.  Uses the interpreter executor, which is part
-// of this library, so no module is loaded either.
+// of this library, so no module is loaded either.  A bounded wait of its
+// kernel that times out is recorded in the array's status word, which
+// ec_device_status reads (and clears on request) beside the device's own
+// word.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -60,6 +63,34 @@ ec_status scratch_for_device(int dev, unsigned char** out) {
   *out = g_scratch_ptr[dev];
   return EC_OK;
 }
+
+}  // namespace
+
+namespace xorec {
+
+// Read (and optionally clear) the status word at the start of the scratch
+// array of device `dev`; the kernels of ec_encode_noalloc write their
+// timeouts there.  Plain copies, no allocation.
+bool noalloc_status(int dev, int* value, bool reset) {
+  unsigned char* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= 64 || !g_scratch_ptr[dev]) return false;
+    p = g_scratch_ptr[dev];
+  }
+  int v = 0;
+  if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (reset && cudaMemset(p, 0, sizeof(int)) != cudaSuccess) cudaGetLastError();
+  *value = v;
+  return true;
+}
+
+}  // namespace xorec
+
+namespace {
 
 ec_status bad(ec_status s, const char* msg) {
   xorec::set_error(msg);
@@ -141,6 +172,9 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
     return bad(EC_EINVAL, "program needs more shared memory than one CTA can hold");
   }
   lp.nstage = nstage;
+  if (xorec::take_injected_timeout() &&
+      !xorec::launch_selftest_wait_to(st, nullptr, lp.status))
+    return EC_ECUDA;
   lp.tiles_per_strip = (lp.io.S + lp.T - 1) / lp.T;
   lp.n_items = lp.tiles_per_strip;
   int per_sm = xorec::interp_max_ctas_per_sm(threads, smem);

@@ -13,6 +13,15 @@
 // event fires, which also timestamps every request in it (latency =
 // submission to observed completion) and frees its admitted bytes.  No
 // device memory is allocated per batch.
+//
+// Every slot has its own status word in host memory that the GPU writes
+// directly (mapped pinned memory), cleared before each dispatch: a bounded
+// wait of the slot's kernels that times out sets it, and the scheduler reads
+// it when the slot's event fires, so every request of that batch completes
+// with EC_ETIMEOUT (its outputs are incomplete) without a copy on the
+// latency path.  A dispatch that fails completes its requests with the
+// failure (after the work it did enqueue has finished) and returns their
+// admitted bytes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,6 +59,10 @@ struct Slot {
   cudaEvent_t done = nullptr;
   bool busy = false;
   std::vector<Req> reqs;
+  int* h_status = nullptr;      // the slot's status word (mapped pinned host memory)
+  int* d_status = nullptr;      // the same word as the kernels address it
+  int fail_status = EC_OK;      // the dispatch failed after enqueuing work: the
+                                // requests complete with this status
   // one device table per slot and its pinned staging copy, laid out per
   // dispatch as [work-queue heads][stripe descriptors][block pointers], so
   // that one copy carries a whole batch's tables
@@ -78,7 +91,12 @@ struct ec_server {
   std::atomic<size_t> n_pending{0};   // pending.size(), readable without the lock
   size_t admitted = 0;
   std::vector<Slot> slots;
-  std::vector<std::pair<uint64_t, double>> done;
+  struct Done {
+    uint64_t ticket;
+    double latency_us;
+    int status;
+  };
+  std::vector<Done> done;
   uint64_t next_ticket = 1;
   std::atomic<bool> stop{false};
   int error = EC_OK;
@@ -102,7 +120,25 @@ void free_slot(Slot& s) {
   if (s.done) cudaEventDestroy(s.done);
   if (s.d_tab) cudaFree(s.d_tab);
   if (s.h_tab) cudaFreeHost(s.h_tab);
+  if (s.h_status) cudaFreeHost(s.h_status);
   s = Slot();
+}
+
+// The slot's status word: pinned host memory mapped into the device's
+// address space, so kernels write it directly and the host reads it.
+bool alloc_status(Slot& s) {
+  if (xorec::host_malloc_mapped(&s.h_status, 64) != cudaSuccess) {
+    cudaGetLastError();
+    s.h_status = nullptr;
+    return false;
+  }
+  *reinterpret_cast<volatile int*>(s.h_status) = 0;
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&s.d_status), s.h_status, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
 }
 
 // Capacity of the slot's table (bytes); contents are rewritten per dispatch.
@@ -125,8 +161,11 @@ bool grow_table(Slot& s, size_t need) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Launch one batch of requests on a free slot.
-bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
+// Launch one batch of requests on a free slot.  On success the requests
+// move into the slot.  On failure *enqueued tells whether some of their
+// work is already on the slot's stream.
+ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueued) {
+  *enqueued = false;
   xorec::TraceRange trace_("xorec serve dispatch");
   // group by launch target: compiled module of this block size, or interpreter
   auto target = [&](const Req& r) -> void* { return r.mod; };
@@ -140,7 +179,7 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
   const size_t desc_off = align_up(n_launches * sizeof(xk::u64), 64);
   const size_t block_off = desc_off + reqs.size() * sizeof(xk::StripeDesc);
   const size_t bytes = block_off + n_blocks * sizeof(xk::u64);
-  if (!grow_table(sl, bytes)) return false;
+  if (!grow_table(sl, bytes)) return fail(EC_ENOMEM, "allocation of a serving slot's table failed");
   std::memset(sl.h_tab, 0, n_launches * sizeof(xk::u64));   // work-queue heads
   auto* h_descs = reinterpret_cast<xk::StripeDesc*>(sl.h_tab + desc_off);
   auto* h_blocks = reinterpret_cast<xk::u64*>(sl.h_tab + block_off);
@@ -174,10 +213,16 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
     l.max_in = std::max(l.max_in, r.prog->n_in);
     if (!mod) l.max_slots = std::max(l.max_slots, r.prog->n_slots);
   }
+  // the slot is free: none of its kernels can write the word now
+  *reinterpret_cast<volatile int*>(sl.h_status) = 0;
   if (cudaMemcpyAsync(sl.d_tab, sl.h_tab, bytes, cudaMemcpyHostToDevice, sl.st) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return fail(EC_ECUDA, "copy of a serving slot's table failed");
   }
+  *enqueued = true;
+  if (xorec::take_injected_timeout() &&
+      !xorec::launch_selftest_wait_to(sl.st, sv->di.status, sl.d_status))
+    return EC_ECUDA;
   for (size_t li = 0; li < launches.size(); ++li) {
     const L& l = launches[li];
     auto key = std::make_tuple(l.mod, l.max_in, l.max_slots);
@@ -187,7 +232,7 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
       int per_sm = 1;
       if (!xorec::batch_launch_shape(l.mod, l.max_in, l.max_slots, l.threads, sv->di.smem_optin,
                                      &smem, &per_sm))
-        return false;
+        return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
       it = sv->shapes.emplace(key, std::make_pair(smem, per_sm)).first;
     }
     xk::BatchParams bp;
@@ -196,20 +241,43 @@ bool dispatch(ec_server* sv, Slot& sl, std::vector<Req>&& reqs) {
     bp.n_stripes = l.n;
     bp.chunk = sv->chunk;
     bp.queue = d_queues + li;
+    xorec::set_ranges(&bp, l.items, 1);
     bp.n_items = l.items;
     bp.T = 4 * l.threads;
     bp.max_in = l.max_in;
     bp.status = sv->di.status;
+    bp.local_status = sl.d_status;
     const long long full = static_cast<long long>(sv->di.sms) * it->second.second;
     const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(full, l.items)));
     const bool ok = l.mod ? xorec::jit_module_launch(l.mod, bp, grid, it->second.first, sl.st)
                           : xorec::launch_interp_batch(bp, l.threads, grid, it->second.first, sl.st);
-    if (!ok) return false;
+    if (!ok) return EC_ECUDA;
   }
-  if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) return false;
+  if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EC_ECUDA, "cudaEventRecord on a serving slot failed");
+  }
   sl.reqs = std::move(reqs);
+  sl.fail_status = EC_OK;
   sl.busy = true;
-  return true;
+  return EC_OK;
+}
+
+// Return requests to their callers with `status` (caller holds sv->mu).
+void complete_locked(ec_server* sv, const std::vector<Req>& reqs, int status,
+                     Clock::time_point now) {
+  for (const Req& r : reqs) {
+    sv->done.push_back({r.ticket, std::chrono::duration<double, std::micro>(now - r.t0).count(),
+                        status});
+    sv->admitted -= r.bytes;
+    sv->stats.completed += 1;
+    if (status == EC_OK) {
+      sv->stats.bytes_in += r.bytes_in;
+      sv->stats.bytes_out += r.bytes_out;
+    } else {
+      sv->stats.failed += 1;
+    }
+  }
 }
 
 void scheduler(ec_server* sv) {
@@ -222,20 +290,19 @@ void scheduler(ec_server* sv) {
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
       const auto now = Clock::now();
-      std::lock_guard<std::mutex> lk(sv->mu);
+      int status = sl.fail_status;
       if (q != cudaSuccess) {
         cudaGetLastError();
-        sv->error = EC_ECUDA;
+        status = EC_ECUDA;
+      } else if (status == EC_OK &&
+                 *reinterpret_cast<volatile int*>(sl.h_status) == xk::XK_STATUS_TIMEOUT) {
+        status = EC_ETIMEOUT;
       }
-      for (const Req& r : sl.reqs) {
-        sv->done.emplace_back(r.ticket,
-                              std::chrono::duration<double, std::micro>(now - r.t0).count());
-        sv->admitted -= r.bytes;
-        sv->stats.completed += 1;
-        sv->stats.bytes_in += r.bytes_in;
-        sv->stats.bytes_out += r.bytes_out;
-      }
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (q != cudaSuccess) sv->error = EC_ECUDA;
+      complete_locked(sv, sl.reqs, status, now);
       sl.reqs.clear();
+      sl.fail_status = EC_OK;
       sl.busy = false;
       worked = true;
     }
@@ -277,14 +344,26 @@ void scheduler(ec_server* sv) {
     }
     if (!take.empty()) {
       const size_t n = take.size();
-      if (!dispatch(sv, *free_slot_p, std::move(take))) {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        sv->error = EC_ECUDA;
-        sv->stats.failed += static_cast<long long>(n);
-      } else {
+      Slot& sl = *free_slot_p;
+      bool enqueued = false;
+      const ec_status ds = dispatch(sv, sl, take, &enqueued);
+      if (ds == EC_OK) {
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stats.batches += 1;
         sv->stats.max_batch_seen = std::max<long long>(sv->stats.max_batch_seen, n);
+      } else if (enqueued && cudaEventRecord(sl.done, sl.st) == cudaSuccess) {
+        // part of the batch is on the GPU: its requests fail once it is done
+        sl.reqs = std::move(take);
+        sl.fail_status = ds;
+        sl.busy = true;
+      } else {
+        if (enqueued) {
+          cudaGetLastError();
+          cudaStreamSynchronize(sl.st);
+          cudaGetLastError();
+        }
+        std::lock_guard<std::mutex> lk(sv->mu);
+        complete_locked(sv, take, ds, Clock::now());
       }
       worked = true;
     }
@@ -345,6 +424,7 @@ ec_status ec_server_create(const ec_server_opts* opts, ec_server** out) {
   for (Slot& sl : sv->slots) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        !alloc_status(sl) ||
         !grow_table(sl, static_cast<size_t>(sv->max_batch) *
                             (sizeof(xk::u64) + sizeof(xk::StripeDesc) + 16 * sizeof(xk::u64)))) {
       cudaGetLastError();
@@ -455,18 +535,31 @@ ec_status ec_server_cancel(ec_server* sv, uint64_t ticket) {
   return EC_EBUSY;   // launched or finished
 }
 
-ec_status ec_server_poll(ec_server* sv, uint64_t* tickets, double* latency_us, int max,
-                         int* n_done) {
+ec_status ec_server_poll_ex(ec_server* sv, uint64_t* tickets, double* latency_us, int* status,
+                            int max, int* n_done) {
   if (!sv || !n_done || max < 0) return fail(EC_EINVAL, "bad argument");
   std::lock_guard<std::mutex> lk(sv->mu);
   const int n = std::min<int>(max, static_cast<int>(sv->done.size()));
   for (int i = 0; i < n; ++i) {
-    if (tickets) tickets[i] = sv->done[i].first;
-    if (latency_us) latency_us[i] = sv->done[i].second;
+    if (tickets) tickets[i] = sv->done[i].ticket;
+    if (latency_us) latency_us[i] = sv->done[i].latency_us;
+    if (status) status[i] = sv->done[i].status;
   }
   sv->done.erase(sv->done.begin(), sv->done.begin() + n);
   *n_done = n;
   return sv->error == EC_OK ? EC_OK : fail(static_cast<ec_status>(sv->error), "a batch failed on the GPU");
+}
+
+ec_status ec_server_poll(ec_server* sv, uint64_t* tickets, double* latency_us, int max,
+                         int* n_done) {
+  if (!sv || !n_done || max < 0) return fail(EC_EINVAL, "bad argument");
+  std::vector<int> st(static_cast<size_t>(max));
+  const ec_status s = ec_server_poll_ex(sv, tickets, latency_us, st.data(), max, n_done);
+  if (s != EC_OK) return s;
+  for (int i = 0; i < *n_done; ++i)
+    if (st[i] != EC_OK)
+      return fail(static_cast<ec_status>(st[i]), "a returned request failed; its outputs are incomplete");
+  return EC_OK;
 }
 
 ec_status ec_server_stats_get(ec_server* sv, ec_server_stats* out) {

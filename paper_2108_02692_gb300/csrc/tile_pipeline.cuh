@@ -14,7 +14,8 @@
 // read from HBM once and every output byte written once.
 //
 // Waits are bounded: an mbarrier wait that exceeds ~2 s of %globaltimer sets
-// the status word to XK_STATUS_TIMEOUT, waits (bounded again) for the CTA's
+// the status word to XK_STATUS_TIMEOUT (batched launches also set their
+// batch's or serving slot's own word), waits (bounded again) for the CTA's
 // copies still in flight and returns.
 #pragma once
 
@@ -86,18 +87,24 @@ struct BatchParams {
   const StripeDesc* stripes;   // the launch's stripes; item_base is increasing
   int n_stripes;
   int chunk;                   // consecutive items a CTA takes from the queue at a time
-  u64* queue;                  // work queue head (chunks handed out), zero at launch
+  u64* queue;                  // n_ranges work-queue heads (chunks handed out), zero at launch
   i64 n_items;
   int T;                   // tile bytes per strip
   int max_in;              // largest n_in (strips) of the launch: stage size
-  int* status;
+  int* status;             // the device's status word
+  int n_ranges;            // items split into this many contiguous ranges, one
+                           // per SM (<= 1: one queue for all items)
+  int range_rem;           // n_items % n_ranges
+  i64 range_len;           // n_items / n_ranges
+  int* local_status;       // the batch's or serving slot's own status word, or null
 };
 
-// Shared-memory header of batched launches: the mbarrier (128 B) and the
-// table of the next item's source addresses (one per strip).
+// Shared-memory header of batched launches: the mbarrier (bytes 0..7), the
+// item ring (64..95), warp 0's work-queue state (128..191) and the table of
+// the next item's source addresses (one per strip, from byte 256).
 constexpr int kMaxPrepared = 128;
-constexpr int kBatchHeader = 128 + 8 * kMaxPrepared;
-constexpr int kRing = 4;   // item ring in the header (bytes 64..95)
+constexpr int kBatchHeader = 256 + 8 * kMaxPrepared;
+constexpr int kRing = 4;
 
 #if defined(__CUDACC__) || defined(__CUDACC_RTC__)
 
@@ -306,11 +313,22 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
 //   kEarlyRelease == false:
 //     void operator()(const StripeDesc&, i64 c0, int len, const u8* stage,
 //                     u8* slots, int T) const
-// Item -> stripe.  A CTA visits its items in increasing order, so each
-// caller keeps a cursor into the stripe list and only moves it forward.
+// Item -> stripe.  A CTA mostly visits consecutive items, so each caller
+// keeps a cursor into the stripe list and moves it to the next stripe, or
+// searches when the CTA has moved to another range of items.
+__device__ __forceinline__ int find_stripe(const BatchParams& p, i64 item);
+
 __device__ __forceinline__ void batch_item_geom(const BatchParams& p, i64 item, int& cursor,
                                                 const StripeDesc*& d, i64& c0, int& len) {
-  while (cursor + 1 < p.n_stripes && p.stripes[cursor + 1].item_base <= item) ++cursor;
+  // the cursor's stripe, else the next one, else a binary search (a CTA
+  // that moves to another range of items jumps)
+  if (p.stripes[cursor].item_base > item) {
+    cursor = find_stripe(p, item);
+  } else if (cursor + 1 < p.n_stripes && p.stripes[cursor + 1].item_base <= item) {
+    ++cursor;
+    if (cursor + 1 < p.n_stripes && p.stripes[cursor + 1].item_base <= item)
+      cursor = find_stripe(p, item);
+  }
   d = &p.stripes[cursor];
   c0 = (item - d->item_base) * p.T;
   const i64 rest = d->S - c0;
@@ -389,11 +407,74 @@ __device__ __forceinline__ void issue_batch_prepared(const BatchParams& p, i64 i
   }
 }
 
+// Warp 0's work-queue state, kept in shared memory between items so that
+// none of it occupies registers while the XOR program runs.
+struct QueueState {
+  i64 q_pos, q_end;   // current chunk [q_pos, q_end)
+  int cur_r;          // range popped from, -1 when every range is empty
+  int home;           // range of the SM the CTA runs on
+  int prep_cur;       // stripe cursor of the prepared item
+  int pad_;
+  NextCopy nc;        // the prepared copy
+};
+
+// Items are split into n_ranges contiguous ranges: the first range_rem
+// ranges hold range_len + 1 items, the others range_len.
+__device__ __forceinline__ i64 range_lo(const BatchParams& p, int r) {
+  return p.range_len * r + (r < p.range_rem ? r : p.range_rem);
+}
+
+// Warp 0 (all lanes): the nearest range, from `home` on, whose queue head
+// still has items; -1 when none has.  Heads only grow, so a range seen
+// empty stays empty; a range seen non-empty may empty before the pop, which
+// then fails and the scan runs again.
+__device__ __forceinline__ int next_range(const BatchParams& p, int home, int R, i64 C) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < R; base += 32) {
+    bool left = false;
+    if (base + lane < R) {
+      int r = home + base + lane;
+      if (r >= R) r -= R;
+      const u64 h = *reinterpret_cast<volatile const u64*>(p.queue + r);
+      left = range_lo(p, r) + static_cast<i64>(h) * C < range_lo(p, r + 1);
+    }
+    const u32 b = __ballot_sync(0xffffffffu, left);
+    if (b) {
+      const int r = home + base + __ffs(b) - 1;
+      return r >= R ? r - R : r;
+    }
+  }
+  return -1;
+}
+
+// Warp 0 (all lanes): next item of this CTA, -1 at the end.
+__device__ __forceinline__ i64 batch_pop(const BatchParams& p, QueueState& q) {
+  const int R = p.n_ranges > 1 ? p.n_ranges : 1;
+  const i64 C = p.chunk > 0 ? p.chunk : 1;
+  while (q.q_pos >= q.q_end) {
+    if (q.cur_r < 0) return -1;
+    u64 c = 0;
+    if ((threadIdx.x & 31) == 0) c = atomicAdd(p.queue + q.cur_r, 1ull);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    const i64 lo = range_lo(p, q.cur_r) + static_cast<i64>(c) * C;
+    const i64 hi = range_lo(p, q.cur_r + 1);
+    if (lo < hi) {
+      q.q_pos = lo;
+      q.q_end = lo + C < hi ? lo + C : hi;
+      break;
+    }
+    q.cur_r = next_range(p, q.home, R, C);
+  }
+  return q.q_pos++;
+}
+
 template <class Body>
 __device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* smem, const Body& body,
                                                    u8* slots) {
   u64* bar = reinterpret_cast<u64*>(smem);
-  const u8** src = reinterpret_cast<const u8**>(smem + 128);
+  volatile i64* ring = reinterpret_cast<volatile i64*>(smem + 64);
+  QueueState* qs = reinterpret_cast<QueueState*>(smem + 128);
+  const u8** src = reinterpret_cast<const u8**>(smem + 256);
   u8* stage = smem + kBatchHeader;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -401,47 +482,52 @@ __device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* sme
     fence_mbar_init();
   }
   __syncthreads();
-  // Work queue: warp 0 pops chunks of `chunk` consecutive items from the
-  // launch's queue head (consecutive items mostly share a stripe, whose
-  // descriptor stays in L1, and each CTA streams long runs of every strip;
-  // popping on demand balances stripes of different cost).  Warp 0 works
+  // Work queue: warp 0 pops chunks of `chunk` consecutive items (consecutive
+  // items mostly share a stripe, whose descriptor stays in L1, and each CTA
+  // streams long runs of every strip; popping on demand balances stripes of
+  // different cost).  The items are split into n_ranges contiguous ranges,
+  // one per SM, each with its own queue head: a CTA pops from the range of
+  // the SM it runs on, so the CTAs of one SM work on the same stripe, hence
+  // the same program, and an SM runs only the few programs of its range
+  // (straight-line programs of many decode patterns otherwise compete for
+  // the SM's instruction cache).  When its range is empty, a CTA takes
+  // chunks from the nearest range that still has items (a warp-wide scan of
+  // the heads); it returns only when every range is empty, so every item is
+  // processed exactly once whichever SMs the CTAs land on.  Warp 0 works
   // two items ahead: it publishes item indices in a ring in shared memory
   // and keeps the source table of the next copy prepared, so that neither
   // the queue nor the descriptors delay the barrier.
-  volatile i64* ring = reinterpret_cast<volatile i64*>(smem + 64);
-  const i64 n = p.n_items;
-  const i64 C = p.chunk > 0 ? p.chunk : 1;
-  i64 q_pos = 0, q_end = 0;   // warp 0: current chunk
-  auto pop = [&]() -> i64 {   // warp 0 (all lanes): next item of this CTA, -1 at the end
-    if (q_pos >= q_end) {
-      u64 c = 0;
-      if ((threadIdx.x & 31) == 0) c = atomicAdd(p.queue, 1ull);
-      c = __shfl_sync(0xffffffffu, c, 0);
-      q_pos = static_cast<i64>(c) * C;
-      q_end = q_pos + C < n ? q_pos + C : n;
-      if (q_pos >= n) { q_end = q_pos; return -1; }
-    }
-    return q_pos++;
-  };
-  NextCopy nc;
-  int cur = 0, prep_cur = 0;   // stripe cursors of this item and of the prepared one
   if (tid < 32) {
-    const i64 a = pop();
-    const i64 b2 = a >= 0 ? pop() : -1;
+    QueueState q;
+    q.q_pos = q.q_end = 0;
+    q.home = 0;
+    if (p.n_ranges > 1) {
+      u32 sm;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+      q.home = static_cast<int>(sm % static_cast<u32>(p.n_ranges));
+    }
+    q.cur_r = q.home;
+    q.prep_cur = 0;
+    q.pad_ = 0;
+    const i64 a = batch_pop(p, q);
+    const i64 b2 = a >= 0 ? batch_pop(p, q) : -1;
     if (tid == 0) {
       ring[0] = a;
       ring[1] = b2;
     }
     if (a >= 0) {
-      prep_cur = find_stripe(p, a);
-      prepare_batch_item(p, a, prep_cur, nc, src);
+      q.prep_cur = find_stripe(p, a);
+      prepare_batch_item(p, a, q.prep_cur, q.nc, src);
       __syncwarp();
-      issue_batch_prepared(p, a, prep_cur, nc, src, stage, smem_addr(bar));
+      issue_batch_prepared(p, a, q.prep_cur, q.nc, src, stage, smem_addr(bar));
       __syncwarp();
-      if (b2 >= 0) prepare_batch_item(p, b2, prep_cur, nc, src);
+      if (b2 >= 0) prepare_batch_item(p, b2, q.prep_cur, q.nc, src);
     }
+    __syncwarp();
+    if (tid == 0) *qs = q;
   }
   __syncthreads();
+  int cur;   // stripe cursor of the current item
   {
     const i64 a = ring[0];
     cur = a >= 0 ? find_stripe(p, a) : 0;
@@ -458,35 +544,47 @@ __device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* sme
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicExch(p.status, XK_STATUS_TIMEOUT);
+        if (p.local_status) *reinterpret_cast<volatile int*>(p.local_status) = XK_STATUS_TIMEOUT;
         mbar_wait(smem_addr(bar), static_cast<u32>(i & 1));
       }
       return;
     }
-    // warp 0, after the stage is free: issue the next copy, pop the item
-    // after it and prepare its sources
-    auto refill = [&]() {
+    // warp 0, once the stage is free: issue the copy of the next item
+    // (prepared one item earlier) ...
+    auto issue_next = [&]() {
+      if (tid < 32 && nxt >= 0) {
+        if (tid == 0) fence_proxy_async();
+        __syncwarp();
+        issue_batch_prepared(p, nxt, qs->prep_cur, qs->nc, src, stage, smem_addr(bar));
+        __syncwarp();
+      }
+    };
+    // ... and, after its own share of the work (no input words are held in
+    // registers then), pop the item after it and prepare its sources.  The
+    // ring entry it writes is read by the other warps only after the next
+    // iteration's barrier.
+    auto prepare_after = [&]() {
       if (tid < 32) {
-        if (nxt >= 0) {
-          if (tid == 0) fence_proxy_async();
-          __syncwarp();
-          issue_batch_prepared(p, nxt, prep_cur, nc, src, stage, smem_addr(bar));
-          __syncwarp();
-        }
-        const i64 after = nxt >= 0 ? pop() : -1;
+        QueueState q = *qs;
+        const i64 after = nxt >= 0 ? batch_pop(p, q) : -1;
         if (tid == 0) ring[(i + 2) % kRing] = after;
-        if (after >= 0) prepare_batch_item(p, after, prep_cur, nc, src);
+        if (after >= 0) prepare_batch_item(p, after, q.prep_cur, q.nc, src);
+        __syncwarp();
+        if (tid == 0) *qs = q;
       }
     };
     if constexpr (Body::kEarlyRelease) {
       typename Body::Regs r;
       body.load(*d, len, stage, r);
       __syncthreads();
-      refill();
+      issue_next();
       body.compute(*d, c0, len, r);
+      prepare_after();
     } else {
       body(*d, c0, len, stage, slots, p.T);
       __syncthreads();
-      refill();
+      issue_next();
+      prepare_after();
     }
   }
 }

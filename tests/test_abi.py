@@ -46,3 +46,30 @@ def test_exported_dynamic_symbols_cover_header():
 def test_version_and_error_string():
     assert "xorec" in xo.ec_version()
     assert isinstance(xo.ec_last_error(), str)
+
+
+def test_noalloc_limits_are_checked_before_any_device_call():
+    """ec_encode_noalloc rejects programs longer than its static array holds
+    (EC_EINVAL) before it touches a device, and rejects bad block sizes the
+    same way.  k + m above its block limit cannot reach it: plans already
+    refuse k + m > 256 = EC_NOALLOC_MAX_BLOCKS."""
+    import pytest
+    plan = xo.ec_plan_create_ex(100, 4, opt_level=xo.EC_OPT_RAW)
+    try:
+        assert xo.ec_plan_info(plan)["code_words"] > 32768
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_encode_noalloc(plan, [16] * 100, [16] * 4, 128, 0)
+        assert e.value.status == xo.EC_EINVAL
+        assert "32768" in xo.ec_last_error()
+    finally:
+        xo.ec_plan_destroy(plan)
+    plan = xo.ec_plan_create(4, 2)
+    try:
+        with pytest.raises(xo.XorecError) as e:
+            xo.ec_encode_noalloc(plan, [16] * 4, [16] * 2, 100, 0)
+        assert e.value.status == xo.EC_EINVAL
+    finally:
+        xo.ec_plan_destroy(plan)
+    with pytest.raises(xo.XorecError) as e:
+        xo.ec_plan_create(200, 57)
+    assert e.value.status == xo.EC_EINVAL

@@ -79,6 +79,32 @@ def test_mixed_batch_matches_oracle(plans, executor):
         xo.ec_batch_destroy(b)
 
 
+@pytest.mark.parametrize("ranges", [2, 7, 152, 4096])
+@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED],
+                         ids=["interp", "compiled"])
+def test_batch_item_ranges_match_oracle(plans, executor, ranges, monkeypatch):
+    """Items split into per-SM ranges (forced here; a batch only chooses them
+    when it has enough items): CTAs start on their SM's range and move to the
+    others, so every item of a mixed batch is still computed exactly once,
+    whatever the number of ranges (more ranges than SMs are capped)."""
+    monkeypatch.setenv("EC_BATCH_RANGES", str(ranges))
+    jobs, keep, expect = make_jobs(plans, 40, seed=50 + ranges + executor,
+                                   sizes=(128, 4096, 8 * 1552, 64 * 1024, 8 * 32784))
+    b = xo.ec_batch_create(jobs, executor)
+    try:
+        st = torch.cuda.current_stream().cuda_stream
+        for _ in range(2):   # the queue heads are reset at every run
+            for o, _ in expect:
+                for t in o:
+                    t.fill_(0xEE)
+            xo.ec_batch_run(b, st)
+            torch.cuda.synchronize()
+            check(expect)
+    finally:
+        xo.ec_batch_destroy(b)
+    assert xo.ec_device_status() == 0
+
+
 def test_alone_and_in_mix_give_identical_bytes(plans):
     jobs, keep, expect = make_jobs(plans, 30, seed=7)
     st = torch.cuda.current_stream().cuda_stream
