@@ -277,6 +277,33 @@ def test_cauchy_min_has_fewer_ones_and_locally_best_rows(k, m):
             assert sum(_ones_clmul(clmul_mod(x, di)) for x in row) >= here
 
 
+@pytest.mark.parametrize("k,m", [(4, 2), (6, 3), (8, 4), (10, 4), (12, 4), (20, 8), (16, 16)])
+def test_cauchy_min_rows_equal_the_bruteforce_choice(k, m):
+    """Reading R14 fixes every entry: with R[i][j] = C[i][j] / C[0][j] (the
+    columns divided by their row-0 entries), row i >= 1 is R[i] divided by
+    the entry d of R[i] that leaves the fewest bitmatrix ones, and among
+    divisors leaving equally few, the smallest value of d.  Derived here by
+    trying every divisor with carry-less products, independently of the
+    oracle's log tables, so a wrong tie-break or a wrong pivot row fails."""
+    C = oracle.cauchy(k, m)
+    Q = oracle.cauchy_min(k, m)
+    R = [[clmul_mod(int(C[i, j]), _inv_clmul(int(C[0, j]))) for j in range(k)] for i in range(m)]
+    assert [int(x) for x in Q[0]] == R[0] == [1] * k
+    tied_rows = 0
+    for i in range(1, m):
+        cand = []
+        for d in sorted(set(R[i])):
+            di = _inv_clmul(d)
+            row = [clmul_mod(x, di) for x in R[i]]
+            cand.append((sum(_ones_clmul(x) for x in row), d, row))
+        fewest = min(c[0] for c in cand)
+        best = [c for c in cand if c[0] == fewest]
+        tied_rows += len(best) > 1
+        assert [int(x) for x in Q[i]] == best[0][2], (i, best[0][1])
+    if (k, m) == (16, 16):
+        assert tied_rows > 0     # this code exercises the tie-break
+
+
 def _rank_gf(M, T, inv):
     M = [list(map(int, r)) for r in M]
     n, c = len(M), len(M[0])
