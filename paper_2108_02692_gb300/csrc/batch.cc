@@ -204,12 +204,17 @@ int plan_module_minb(const ec_plan* p, int n_in) {
 int launch_threads(void* mod) { return mod ? jit_module_threads(mod) : batch_threads(); }
 
 // Compile every program of `want` that has no module of its plan's launch
-// shape into modules of at most EC_BATCH_MODULE_SIZE programs (per plan and
-// input width, NVRTC, in parallel host threads).  Modules belong to their
-// plan.
+// shape into multi-program modules (per plan and input width, NVRTC, in
+// parallel host threads).  Modules belong to their plan.  Each group is cut
+// into as few modules as keep every module within EC_BATCH_MODULE_SIZE
+// programs (default 128) and about 128 K memory operations of straight-line
+// code, programs spread evenly over them: a batch then runs few long
+// launches (every launch starts each SM on a program whose code is not yet
+// in its instruction cache), at the price of fewer, longer compiles.
 ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, bool must,
                           int* built) {
-  const int module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 32));
+  const long module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 128));
+  const long module_mem = 131072;
   DeviceInfo di;
   if (!device_info(&di)) return EC_ECUDA;
   std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
@@ -225,12 +230,18 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
     pending[{w.first, w.second->n_in}].push_back(w.second);
   }
   std::vector<std::pair<ec_plan*, std::vector<Program*>>> to_compile;
-  for (auto& kv : pending)
-    for (size_t i = 0; i < kv.second.size(); i += module_size)
-      to_compile.emplace_back(
-          kv.first.first,
-          std::vector<Program*>(kv.second.begin() + i,
-                                kv.second.begin() + std::min(kv.second.size(), i + module_size)));
+  for (auto& kv : pending) {
+    const std::vector<Program*>& ps = kv.second;
+    long mem = 0;
+    for (const Program* p : ps) mem += p->stats.fused.mem;
+    const long n = static_cast<long>(ps.size());
+    const long n_mod = std::max({1L, (n + module_size - 1) / module_size,
+                                 std::min(n, (mem + module_mem - 1) / module_mem)});
+    for (long m = 0; m < n_mod; ++m)
+      to_compile.emplace_back(kv.first.first,
+                              std::vector<Program*>(ps.begin() + n * m / n_mod,
+                                                    ps.begin() + n * (m + 1) / n_mod));
+  }
   std::vector<std::string> errs(to_compile.size());
   std::vector<void*> mods(to_compile.size(), nullptr);
   parallel_for(to_compile.size(), [&](size_t i) {

@@ -285,21 +285,27 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   }
   if (!compiled) {
     if (!ensure_device_code(p)) return false;
-    threads = env_int("EC_INTERP_THREADS", 128);
-    nstage = env_int("EC_INTERP_NSTAGE", 2);
+    // one stage (more resident CTAs hide more latency than a second stage
+    // of the same CTA) and 8 bytes per thread and strip, halving per byte
+    // the work of fetching and addressing each operand; the tile shrinks
+    // (words, then threads) while it does not fit
+    int words = env_int("EC_INTERP_WORDS", 2) == 1 ? 1 : 2;
+    threads = env_int("EC_INTERP_THREADS", words == 2 ? 64 : 128);
+    nstage = env_int("EC_INTERP_NSTAGE", 1);
     for (;;) {
-      lp.T = 4 * threads;
+      lp.T = 4 * words * threads;
       smem = interp_smem_bytes(p->n_in, p->n_slots, lp.T, nstage);
       if (smem <= di.smem_optin) break;
       if (nstage > 1) { --nstage; continue; }
-      if (threads > 32) { threads /= 2; nstage = env_int("EC_INTERP_NSTAGE", 2); continue; }
+      if (words > 1) { words = 1; continue; }
+      if (threads > 32) { threads /= 2; continue; }
       set_error("program needs more shared memory than one CTA can hold");
       return false;
     }
     lp.code = p->d_code;
     lp.code_len = static_cast<int>(p->code.size());
     lp.n_slots = p->n_slots;
-    per_sm = interp_max_ctas_per_sm(threads, smem);
+    per_sm = interp_max_ctas_per_sm(threads, smem, lp.T);
   }
   lp.nstage = nstage;
   lp.tiles_per_strip = (io.S + lp.T - 1) / lp.T;

@@ -21,15 +21,61 @@ namespace {
 
 using namespace xk;
 
-// Runs an instruction stream for one thread's 4-byte column of a tile.
-// in_col: the column in strip 0 of the stage; slots: base of the slot area;
-// out(r): address of output strip r at this column.
-template <class OutAddr>
-__device__ __forceinline__ void interpret(const u16* __restrict__ code, int code_len, int n_in, int T,
-                                          int col, const u8* in_col, u8* slots,
-                                          const OutAddr& out) {
-  // operand id -> address: inputs live in the stage, slots after it
-  u8* slot_col = slots + col - static_cast<i64>(n_in) * T;
+// Shared-memory accesses by 32-bit shared-window address.  Volatile so
+// that a statement's reads of a slot stay after the earlier statement's
+// write of it (the same thread, the same address).
+template <int W> struct Words { u32 v[W]; };
+
+template <int W>
+__device__ __forceinline__ Words<W> lds(u32 a) {
+  Words<W> r;
+  if constexpr (W == 1) {
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r.v[0]) : "r"(a));
+  } else {
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.v[0]), "=r"(r.v[1]) : "r"(a));
+  }
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ void sts(u32 a, const Words<W>& x) {
+  if constexpr (W == 1) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(x.v[0]) : "memory");
+  } else {
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(x.v[0]), "r"(x.v[1]) : "memory");
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void stg(u8* p, const Words<W>& x) {
+  if constexpr (W == 1) {
+    *reinterpret_cast<u32*>(p) = x.v[0];
+  } else {
+    *reinterpret_cast<uint2*>(p) = make_uint2(x.v[0], x.v[1]);
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void xor_in(Words<W>& acc, const Words<W>& x) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc.v[w] ^= x.v[w];
+}
+
+// Runs an instruction stream for one thread's column of a tile: W 4-byte
+// words of every strip (bytes [col, col + 4W) of the tile).  in_col: shared
+// address of the column in input strip 0 of the stage (strip c at
+// in_col + c*T); slot_col: shared address of the column in slot 0 (slot s
+// at slot_col + s*T); out(r): global address of output strip r at this
+// column.  Operand ids below n_in are input strips, the others slots.
+template <int W, class OutAddr>
+__device__ __forceinline__ void interpret(const u16* __restrict__ code, int code_len, int n_in,
+                                          u32 T, u32 in_col, u32 slot_col, const OutAddr& out) {
+  // operand o at in_col + o*T, plus `gap` for slots when they do not
+  // directly follow the input strips
+  const u32 gap = slot_col - (in_col + static_cast<u32>(n_in) * T);
+  auto addr = [&](int o) -> u32 {
+    return in_col + static_cast<u32>(o) * T + (o >= n_in ? gap : 0u);
+  };
   int pc = 0;
   while (pc < code_len) {
     const int na = __ldg(code + pc);
@@ -40,37 +86,39 @@ __device__ __forceinline__ void interpret(const u16* __restrict__ code, int code
     if (w1 & 0x8000) slot = __ldg(code + pc++);
     const int ob = pc;
     pc += no;
-    u32 acc = 0;
+    Words<W> acc;
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc.v[w] = 0;
     int a = 0;
-    for (; a + 4 <= na; a += 4) {
-      const int o0 = __ldg(code + pc + a), o1 = __ldg(code + pc + a + 1);
-      const int o2 = __ldg(code + pc + a + 2), o3 = __ldg(code + pc + a + 3);
-      const u32 x0 = *reinterpret_cast<const u32*>((o0 < n_in ? in_col : slot_col) + static_cast<i64>(o0) * T);
-      const u32 x1 = *reinterpret_cast<const u32*>((o1 < n_in ? in_col : slot_col) + static_cast<i64>(o1) * T);
-      const u32 x2 = *reinterpret_cast<const u32*>((o2 < n_in ? in_col : slot_col) + static_cast<i64>(o2) * T);
-      const u32 x3 = *reinterpret_cast<const u32*>((o3 < n_in ? in_col : slot_col) + static_cast<i64>(o3) * T);
-      acc ^= x0 ^ x1 ^ x2 ^ x3;
+    for (; a + 8 <= na; a += 8) {
+      int o[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) o[q] = __ldg(code + pc + a + q);
+      Words<W> x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = lds<W>(addr(o[q]));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xor_in(acc, x[q]);
     }
-    for (; a < na; ++a) {
-      const int o = __ldg(code + pc + a);
-      acc ^= *reinterpret_cast<const u32*>((o < n_in ? in_col : slot_col) + static_cast<i64>(o) * T);
-    }
+    for (; a < na; ++a) xor_in(acc, lds<W>(addr(__ldg(code + pc + a))));
     pc += na;
-    if (slot >= 0) *reinterpret_cast<u32*>(slots + static_cast<i64>(slot) * T + col) = acc;
-    for (int o = 0; o < no; ++o) *reinterpret_cast<u32*>(out(__ldg(code + ob + o))) = acc;
+    if (slot >= 0) sts<W>(slot_col + static_cast<u32>(slot) * T, acc);
+    for (int q = 0; q < no; ++q) stg<W>(out(__ldg(code + ob + q)), acc);
   }
 }
 
+template <int W>
 struct InterpBody {
   static constexpr bool kEarlyRelease = false;
   __device__ __forceinline__ void operator()(const LaunchParams& p, i64 s, i64 c0, int len,
-                                             const u8* stg, u8* slots) const {
-    const int col = threadIdx.x * 4;
+                                             const u8* stg_base, u8* slots) const {
+    const int col = threadIdx.x * 4 * W;
     if (col >= len) return;
     auto out = [&](int r) {
       return out_block(p.io, s, r >> 3) + static_cast<i64>(r & 7) * p.io.S + c0 + col;
     };
-    interpret(p.code, p.code_len, p.n_in, p.T, col, stg + col, slots, out);
+    interpret<W>(p.code, p.code_len, p.n_in, static_cast<u32>(p.T), smem_addr(stg_base + col),
+                 smem_addr(slots + col), out);
   }
 };
 
@@ -84,19 +132,25 @@ struct InterpBatchBody {
     auto out = [&](int r) {
       return reinterpret_cast<u8*>(outs[r >> 3]) + static_cast<i64>(r & 7) * d.S + c0 + col;
     };
-    interpret(d.code, d.code_len, 8 * d.n_inblk, T, col, stg + col, slots, out);
+    interpret<1>(d.code, d.code_len, 8 * d.n_inblk, static_cast<u32>(T), smem_addr(stg + col),
+                 smem_addr(slots + col), out);
   }
 };
 
-__global__ void __launch_bounds__(256)
+// Single-launch interpreter: each thread owns W 4-byte words per strip
+// (tile T = 4 * W * threads bytes).
+// Shared memory, not registers, bounds its resident CTAs (the stage and the
+// slots of a program take tens of KB), so the register cap is left loose.
+template <int W>
+__global__ void __launch_bounds__(256, 1)
     interp_kernel(LaunchParams p, const __grid_constant__ TensorMap tm) {
   extern __shared__ __align__(128) u8 smem[];
-  run_pipeline(p, smem, InterpBody(), &tm);
+  run_pipeline(p, smem, InterpBody<W>(), &tm);
 }
 
 // Batched interpreter: shared memory = [header][stage: max_in * T]
 // [slots: the largest slot count of the launch * T].
-__global__ void __launch_bounds__(256) interp_batch_kernel(BatchParams p) {
+__global__ void __launch_bounds__(256, 1) interp_batch_kernel(BatchParams p) {
   extern __shared__ __align__(128) u8 smem[];
   u8* slots = smem + kBatchHeader + static_cast<i64>(p.max_in) * p.T;
   run_batch_pipeline(p, smem, InterpBatchBody(), slots);
@@ -158,20 +212,31 @@ size_t interp_smem_bytes(int n_in, int n_slots, int T, int nstage) {
   return 128 + static_cast<size_t>(nstage) * n_in * T + static_cast<size_t>(n_slots) * T;
 }
 
-int interp_max_ctas_per_sm(int threads, size_t smem) {
-  if (cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+// The kernel instance for a tile of T bytes per strip at `threads` threads:
+// 4 bytes per thread (W = 1) or 8 (W = 2).
+static const void* interp_kernel_for(int threads, int T) {
+  return T == 8 * threads ? reinterpret_cast<const void*>(&interp_kernel<2>)
+                          : reinterpret_cast<const void*>(&interp_kernel<1>);
+}
+
+int interp_max_ctas_per_sm(int threads, size_t smem, int T) {
+  const void* k = interp_kernel_for(threads, T);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, interp_kernel, threads, smem) !=
-      cudaSuccess)
-    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) return 0;
   return n;
 }
 
 bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads, int grid,
                    size_t smem, cudaStream_t stream) {
-  if (cudaFuncSetAttribute(interp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (lp.T != 4 * threads && lp.T != 8 * threads) {
+    set_error("interpreter tile must be 4 or 8 bytes per thread");
+    return false;
+  }
+  const void* k = interp_kernel_for(threads, lp.T);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     set_error("cudaFuncSetAttribute(interp) failed");
     return false;
@@ -179,7 +244,10 @@ bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int thre
   xk::TensorMap map;
   if (tm) map = *tm;
   else std::memset(&map, 0, sizeof(map));
-  interp_kernel<<<grid, threads, smem, stream>>>(lp, map);
+  if (lp.T == 8 * threads)
+    interp_kernel<2><<<grid, threads, smem, stream>>>(lp, map);
+  else
+    interp_kernel<1><<<grid, threads, smem, stream>>>(lp, map);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("interpreter launch failed: ") + cudaGetErrorString(e));

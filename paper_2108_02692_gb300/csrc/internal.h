@@ -110,7 +110,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
 bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads, int grid,
                    size_t smem, cudaStream_t stream);
 size_t interp_smem_bytes(int n_in, int n_slots, int T, int nstage);
-int interp_max_ctas_per_sm(int threads, size_t smem);
+int interp_max_ctas_per_sm(int threads, size_t smem, int T);
 
 // Batched interpreter (executor.cu).
 size_t interp_batch_smem_bytes(int max_in, int max_slots, int T);

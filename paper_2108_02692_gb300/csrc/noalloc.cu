@@ -177,7 +177,7 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
     return EC_ECUDA;
   lp.tiles_per_strip = (lp.io.S + lp.T - 1) / lp.T;
   lp.n_items = lp.tiles_per_strip;
-  int per_sm = xorec::interp_max_ctas_per_sm(threads, smem);
+  int per_sm = xorec::interp_max_ctas_per_sm(threads, smem, lp.T);
   if (per_sm < 1) per_sm = 1;
   long long grid = static_cast<long long>(sms) * per_sm;
   if (grid > lp.n_items) grid = lp.n_items;
