@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-rates", default="",
                     help="comma-separated arrival rates (req/s) of a served load sweep")
+    ap.add_argument("--serve-obj", default="4096,16777216",
+                    help="MIN,MAX object bytes of the served requests (log-uniform)")
     ap.add_argument("--no-batched", action="store_true",
                     help="default run: skip the batched (mixed-code) leg")
     ap.add_argument("--no-served", action="store_true",
@@ -869,7 +871,8 @@ def served_leg(args, rates):
         # long enough for config 5's rate; ~200k requests at higher rates
         secs = args.serve_seconds if rate <= args.serve_rate else \
             max(1.0, min(args.serve_seconds, 2e5 / rate))
-        reqs = synth.served_requests(secs + warm_s, rate)
+        lo, hi = (int(x) for x in args.serve_obj.split(","))
+        reqs = synth.served_requests(secs + warm_s, rate, min_obj=lo, max_obj=hi)
         served = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 512, 4, warm_s,
                               idle_spin_us=spin, check=16)
         plain = serve_stream(xo, torch, reqs, plans, data_arena, out_arena, 1, 1, warm_s,
@@ -882,9 +885,10 @@ def served_leg(args, rates):
     torch.cuda.empty_cache()
     ok = all(pt[f]["parity"].startswith("bit-exact") and pt[f]["failed"] == 0
              for pt in points for f in ("served", "plain"))
+    lo, hi = (int(x) for x in args.serve_obj.split(","))
     return {
         "workload": "served: Poisson arrivals, RS(10,4)/RS(6,3), objects log-uniform "
-                    "4 KiB-16 MiB, 50% decodes with 1..m erasures, 32 GiB admission budget; "
+                    f"{lo} B-{hi} B, 50% decodes with 1..m erasures, 32 GiB admission budget; "
                     "served = continuous batching (512 per batch, 4 slots), plain = one request "
                     "at a time on one slot",
         "autotune": tuned or None, "warm_s": round(warm_time, 1),

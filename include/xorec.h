@@ -218,7 +218,9 @@ ec_status ec_encode(ec_plan *plan, const uint8_t *const *data, uint8_t *const *p
 
 /* Limits of ec_encode_noalloc. */
 #define EC_NOALLOC_MAX_BLOCKS 256        /* k + m                            */
-#define EC_NOALLOC_MAX_CODE_WORDS 32768  /* 16-bit words of the program      */
+#define EC_NOALLOC_MAX_CODE_WORDS 32768  /* 16-bit words of the program as the
+                                            interpreter reads it on the device
+                                            (its stream in 16-byte chunks)   */
 
 /* Encode one stripe like ec_encode, without allocating any memory.  The
  * paper has no counterpart: this is for callers that are not allowed to

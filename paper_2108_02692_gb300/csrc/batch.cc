@@ -195,8 +195,15 @@ int plan_module_threads(const ec_plan* p, int n_in) {
   return p->tuned_threads > 0 ? p->tuned_threads : batch_threads_for(n_in);
 }
 
+// A tuned shape keeps its occupancy in batch modules down to a 128-register
+// cap: a tighter cap leaves the batched pipeline no registers of its own
+// beside the program's values (the autotuned RS(6,3) shape, register budget
+// 96 at 5 CTAs/SM, spilled 40 B in a module at its 96-register cap).
 int plan_module_minb(const ec_plan* p, int n_in) {
-  return p->tuned_threads > 0 && p->tuned_minb > 0 ? p->tuned_minb : batch_minb_for(n_in);
+  if (!(p->tuned_threads > 0 && p->tuned_minb > 0)) return batch_minb_for(n_in);
+  const int floor_cap = env_int("EC_MODULE_MIN_CAP", 128);
+  if (floor_cap <= 0) return p->tuned_minb;
+  return std::max(1, std::min(p->tuned_minb, 65536 / (p->tuned_threads * floor_cap)));
 }
 
 // Threads per CTA of the launch that runs `prog`: its module's, or the
@@ -428,7 +435,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     d.n_outblk = e.prog->n_out / 8;
     d.prog = e.prog->mod_index;
     d.code = e.prog->d_code;
-    d.code_len = static_cast<int>(e.prog->code.size());
+    d.code_len = static_cast<int>(e.prog->chunks.size() / 8);
     d.n_slots = e.prog->n_slots;
     for (uint64_t p : e.ptrs) blocks.push_back(p);
     {

@@ -78,16 +78,16 @@ bool device_info(DeviceInfo* out) {
 
 bool ensure_device_code(Program* p) {
   if (p->d_code) return true;
-  const size_t bytes = std::max<size_t>(1, p->code.size()) * sizeof(uint16_t);
+  const size_t bytes = std::max<size_t>(8, p->chunks.size()) * sizeof(uint16_t);
   uint16_t* d = nullptr;
   if (dev_malloc(&d, bytes) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc of the program failed");
     return false;
   }
-  if (!p->code.empty() &&
-      cudaMemcpy(d, p->code.data(), p->code.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
+  if (!p->chunks.empty() &&
+      cudaMemcpy(d, p->chunks.data(), p->chunks.size() * sizeof(uint16_t),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(d);
     set_error("upload of the program failed");
@@ -303,7 +303,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
       return false;
     }
     lp.code = p->d_code;
-    lp.code_len = static_cast<int>(p->code.size());
+    lp.code_len = static_cast<int>(p->chunks.size() / 8);
     lp.n_slots = p->n_slots;
     per_sm = interp_max_ctas_per_sm(threads, smem, lp.T);
   }
@@ -396,9 +396,21 @@ ec_status get_decode_program(ec_plan* plan, const std::vector<int>& er, Program*
   std::vector<uint8_t> R;
   if (!xorec::decode_matrix(k, m, plan->P.data(), er, S, &R))
     return fail(EC_ESINGULAR, "survivor submatrix is singular for this erasure set");
+  // Decoders run mostly inside batch modules, whose pipeline keeps about
+  // eight registers of its own beside the program's values: their budget
+  // stays that far below the register cap of the plan's module shape, so
+  // that modules compile without spills.
+  xorec::PlanOptions o = plan->opts;
+  const int margin = xorec::env_int("EC_DECODE_REG_MARGIN", 8);
+  if (8 * k <= xorec::kPreloadMaxInputs && margin > 0) {
+    const int th = xorec::plan_module_threads(plan, 8 * k);
+    const int minb = xorec::plan_module_minb(plan, 8 * k);
+    const int cap = std::min(255, 65536 / (th * minb)) & ~7;
+    o.reg_budget = std::max(32, std::min(o.reg_budget, cap - margin));
+  }
   auto prog = std::make_unique<Program>();
   std::string err;
-  if (!xorec::build_program(static_cast<int>(er.size()), k, R.data(), plan->opts, prog.get(), &err))
+  if (!xorec::build_program(static_cast<int>(er.size()), k, R.data(), o, prog.get(), &err))
     return fail(EC_EINVAL, err);
   prog->threads = plan->tuned_threads;
   prog->minb = plan->tuned_minb;

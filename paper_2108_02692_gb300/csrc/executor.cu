@@ -61,49 +61,70 @@ __device__ __forceinline__ void xor_in(Words<W>& acc, const Words<W>& x) {
   for (int w = 0; w < W; ++w) acc.v[w] ^= x.v[w];
 }
 
-// Runs an instruction stream for one thread's column of a tile: W 4-byte
-// words of every strip (bytes [col, col + 4W) of the tile).  in_col: shared
+// Runs a program for one thread's column of a tile: W 4-byte words of
+// every strip (bytes [col, col + 4W) of the tile).  code: the program's
+// device stream of n_chunks 16-byte chunks (Program::chunks: per statement a
+// header chunk, ceil(a/8) chunks of operand ids, then chunks of the outputs
+// beyond five), read warp-uniformly one chunk ahead of its use, so a chunk's
+// eight operand loads wait only for the shared memory.  in_col: shared
 // address of the column in input strip 0 of the stage (strip c at
 // in_col + c*T); slot_col: shared address of the column in slot 0 (slot s
 // at slot_col + s*T); out(r): global address of output strip r at this
 // column.  Operand ids below n_in are input strips, the others slots.
 template <int W, class OutAddr>
-__device__ __forceinline__ void interpret(const u16* __restrict__ code, int code_len, int n_in,
+__device__ __forceinline__ void interpret(const u16* __restrict__ code, int n_chunks, int n_in,
                                           u32 T, u32 in_col, u32 slot_col, const OutAddr& out) {
   // operand o at in_col + o*T, plus `gap` for slots when they do not
   // directly follow the input strips
   const u32 gap = slot_col - (in_col + static_cast<u32>(n_in) * T);
-  auto addr = [&](int o) -> u32 {
-    return in_col + static_cast<u32>(o) * T + (o >= n_in ? gap : 0u);
+  auto addr = [&](u32 o) -> u32 {
+    return in_col + o * T + (o >= static_cast<u32>(n_in) ? gap : 0u);
   };
-  int pc = 0;
-  while (pc < code_len) {
-    const int na = __ldg(code + pc);
-    const int w1 = __ldg(code + pc + 1);
-    pc += 2;
-    const int no = w1 & 0x7fff;
-    int slot = -1;
-    if (w1 & 0x8000) slot = __ldg(code + pc++);
-    const int ob = pc;
-    pc += no;
+  const uint4* chunk = reinterpret_cast<const uint4*>(code);
+  int at = 0;
+  uint4 ahead = n_chunks > 0 ? __ldg(chunk) : make_uint4(0, 0, 0, 0);
+  auto take = [&]() -> uint4 {   // the next chunk; starts the load of the one after
+    const uint4 c = ahead;
+    if (++at < n_chunks) ahead = __ldg(chunk + at);
+    return c;
+  };
+  while (at < n_chunks) {
+    const uint4 h = take();
+    const int na = static_cast<int>(h.x & 0xffffu);
+    const int no = static_cast<int>(h.x >> 16);
+    const u32 slot = h.y & 0xffffu;
     Words<W> acc;
 #pragma unroll
     for (int w = 0; w < W; ++w) acc.v[w] = 0;
-    int a = 0;
-    for (; a + 8 <= na; a += 8) {
-      int o[8];
+    for (int left = na; left > 0; left -= 8) {
+      const uint4 c = take();
+      const u32 id[8] = {c.x & 0xffffu, c.x >> 16, c.y & 0xffffu, c.y >> 16,
+                         c.z & 0xffffu, c.z >> 16, c.w & 0xffffu, c.w >> 16};
+      if (left >= 8) {
+        Words<W> x[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) o[q] = __ldg(code + pc + a + q);
-      Words<W> x[8];
+        for (int q = 0; q < 8; ++q) x[q] = lds<W>(addr(id[q]));
 #pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = lds<W>(addr(o[q]));
+        for (int q = 0; q < 8; ++q) xor_in(acc, x[q]);
+      } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) xor_in(acc, x[q]);
+        for (int q = 0; q < 7; ++q)
+          if (q < left) xor_in(acc, lds<W>(addr(id[q])));
+      }
     }
-    for (; a < na; ++a) xor_in(acc, lds<W>(addr(__ldg(code + pc + a))));
-    pc += na;
-    if (slot >= 0) sts<W>(slot_col + static_cast<u32>(slot) * T, acc);
-    for (int q = 0; q < no; ++q) stg<W>(out(__ldg(code + ob + q)), acc);
+    if (slot != 0xffffu) sts<W>(slot_col + slot * T, acc);
+    const u32 first[5] = {h.y >> 16, h.z & 0xffffu, h.z >> 16, h.w & 0xffffu, h.w >> 16};
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      if (q < no) stg<W>(out(static_cast<int>(first[q])), acc);
+    for (int left = no - 5; left > 0; left -= 8) {
+      const uint4 c = take();
+      const u32 id[8] = {c.x & 0xffffu, c.x >> 16, c.y & 0xffffu, c.y >> 16,
+                         c.z & 0xffffu, c.z >> 16, c.w & 0xffffu, c.w >> 16};
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < left) stg<W>(out(static_cast<int>(id[q])), acc);
+    }
   }
 }
 

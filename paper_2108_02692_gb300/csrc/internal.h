@@ -169,6 +169,10 @@ void host_io_release(xorec_host_io* h);
 ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
                       std::vector<uint64_t>* ptrs);
 int launch_threads(void* mod);
+// Launch shape of a plan's batch modules for programs of n_in input strips:
+// the autotuner's (or ec_plan_set_launch's) shape, else the defaults.
+int plan_module_threads(const ec_plan* p, int n_in);
+int plan_module_minb(const ec_plan* p, int n_in);
 ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, bool must,
                           int* built);
 bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,

@@ -109,7 +109,7 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
   const int nblk = plan->k + plan->m;
   if (nblk > EC_NOALLOC_MAX_BLOCKS)
     return bad(EC_EINVAL, "k + m exceeds the no-allocation block limit");
-  if (p->code.size() > static_cast<size_t>(EC_NOALLOC_MAX_CODE_WORDS))
+  if (p->chunks.size() > static_cast<size_t>(EC_NOALLOC_MAX_CODE_WORDS))
     return bad(EC_EINVAL, "encoding program exceeds the no-allocation limit of 32768 words");
   uint64_t tab[EC_NOALLOC_MAX_BLOCKS];
   for (int j = 0; j < plan->k; ++j) {
@@ -142,8 +142,8 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
   uint16_t* d_code = reinterpret_cast<uint16_t*>(scratch + kStatusBytes + kTableBytes);
   if (cudaMemcpyAsync(d_tab, tab, nblk * sizeof(uint64_t), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
-      (!p->code.empty() &&
-       cudaMemcpyAsync(d_code, p->code.data(), p->code.size() * sizeof(uint16_t),
+      (!p->chunks.empty() &&
+       cudaMemcpyAsync(d_code, p->chunks.data(), p->chunks.size() * sizeof(uint16_t),
                        cudaMemcpyHostToDevice, st) != cudaSuccess)) {
     cudaGetLastError();
     return bad(EC_ECUDA, "copy into the scratch array failed");
@@ -158,7 +158,7 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
   lp.n_in = p->n_in;
   lp.n_out = p->n_out;
   lp.code = d_code;
-  lp.code_len = static_cast<int>(p->code.size());
+  lp.code_len = static_cast<int>(p->chunks.size() / 8);
   lp.n_slots = p->n_slots;
   lp.status = reinterpret_cast<int*>(scratch);
   int threads = 128, nstage = 2;

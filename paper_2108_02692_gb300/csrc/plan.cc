@@ -87,6 +87,32 @@ bool lower(const Slp& q, const Schedule& s, int n_in, int n_out, Program* p,
 
 }  // namespace
 
+std::vector<uint16_t> chunk_stream(const std::vector<uint16_t>& code) {
+  std::vector<uint16_t> out;
+  auto pad = [&]() {
+    while (out.size() % 8) out.push_back(0xffff);
+  };
+  size_t pc = 0;
+  while (pc < code.size()) {
+    const uint16_t na = code[pc];
+    const uint16_t w1 = code[pc + 1];
+    pc += 2;
+    const uint16_t no = w1 & 0x7fff;
+    const uint16_t slot = (w1 & 0x8000) ? code[pc++] : 0xffff;
+    const size_t outs = pc, args = pc + no;
+    pc = args + na;
+    out.push_back(na);
+    out.push_back(no);
+    out.push_back(slot);
+    for (int q = 0; q < 5; ++q) out.push_back(q < no ? code[outs + q] : 0xffff);
+    for (size_t a = 0; a < na; ++a) out.push_back(code[args + a]);
+    pad();
+    for (size_t q = 5; q < no; ++q) out.push_back(code[outs + q]);
+    pad();
+  }
+  return out;
+}
+
 bool check_program_stream(const uint16_t* code, size_t len, int n_in, int n_out, int n_slots,
                           std::string* err) {
   std::vector<char> written(static_cast<size_t>(std::max(0, n_slots)), 0);
@@ -268,6 +294,7 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   if (!lower(fused, gpu, n_in, n_out, &p, err)) return false;
   if (!check_program_stream(p.code.data(), p.code.size(), n_in, n_out, p.n_slots, err))
     return false;
+  p.chunks = chunk_stream(p.code);
   p.fused = fused;
   p.sched = gpu;
   *out = std::move(p);

@@ -53,9 +53,17 @@ struct PipelineStats {
 //   out_0 .. out_{o-1}   output strip indices
 //   arg_0 .. arg_{a-1}   operand ids: < n_in input strip, else slot + n_in
 // `sched` keeps the scheduled fused program for code generation.
+//
+// `chunks` is the same stream as the interpreter reads it on the device:
+// 16-byte chunks of eight 16-bit words, so that one 128-bit load brings
+// eight operand ids.  Per statement: a header chunk (a, o, slot or 0xffff,
+// the first five output strips, unused ones 0xffff), ceil(a/8) chunks of
+// operand ids (the last padded with 0xffff), then, when o > 5, chunks of
+// the remaining output strips (padded with 0xffff).
 struct Program {
   int n_in = 0, n_out = 0, n_slots = 0, n_stmts = 0;
   std::vector<uint16_t> code;
+  std::vector<uint16_t> chunks;
   PipelineStats stats;
   Slp fused;                 // single-assignment fused program
   Schedule sched;            // GPU schedule of `fused`
@@ -94,6 +102,9 @@ struct PlanOptions {
   // -1 = none, > 0 = explicit).
   int stream_temps = 0;
 };
+
+// The device form of an interpreter stream (Program::chunks).
+std::vector<uint16_t> chunk_stream(const std::vector<uint16_t>& code);
 
 // Build the program for the linear map A (rows x cols over GF(2^8)).
 bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,

@@ -204,7 +204,7 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     d.n_outblk = r.prog->n_out / 8;
     d.prog = r.prog->mod_index;
     d.code = r.prog->d_code;
-    d.code_len = static_cast<int>(r.prog->code.size());
+    d.code_len = static_cast<int>(r.prog->chunks.size() / 8);
     d.n_slots = r.prog->n_slots;
     std::memcpy(h_blocks + off, r.ptrs.data(), r.ptrs.size() * sizeof(xk::u64));
     off += r.ptrs.size();
