@@ -71,14 +71,15 @@ __device__ __forceinline__ void xor_in(Words<W>& acc, const Words<W>& x) {
 // in_col + c*T); slot_col: shared address of the column in slot 0 (slot s
 // at slot_col + s*T); out(r): global address of output strip r at this
 // column.  Operand ids below n_in are input strips, the others slots.
-template <int W, class OutAddr>
-__device__ __forceinline__ void interpret(const u16* __restrict__ code, int n_chunks, int n_in,
-                                          u32 T, u32 in_col, u32 slot_col, const OutAddr& out) {
+template <int W, bool kGap, class OutAddr>
+__device__ __forceinline__ void interpret_run(const u16* __restrict__ code, int n_chunks, int n_in,
+                                              u32 T, u32 in_col, u32 slot_col, const OutAddr& out) {
   // operand o at in_col + o*T, plus `gap` for slots when they do not
-  // directly follow the input strips
+  // directly follow the input strips (kGap)
   const u32 gap = slot_col - (in_col + static_cast<u32>(n_in) * T);
   auto addr = [&](u32 o) -> u32 {
-    return in_col + o * T + (o >= static_cast<u32>(n_in) ? gap : 0u);
+    if constexpr (kGap) return in_col + o * T + (o >= static_cast<u32>(n_in) ? gap : 0u);
+    return in_col + o * T;
   };
   const uint4* chunk = reinterpret_cast<const uint4*>(code);
   int at = 0;
@@ -126,6 +127,16 @@ __device__ __forceinline__ void interpret(const u16* __restrict__ code, int n_ch
         if (q < left) stg<W>(out(static_cast<int>(id[q])), acc);
     }
   }
+}
+
+template <int W, class OutAddr>
+__device__ __forceinline__ void interpret(const u16* __restrict__ code, int n_chunks, int n_in,
+                                          u32 T, u32 in_col, u32 slot_col, const OutAddr& out) {
+  // single launches with one stage keep the slots right after the inputs
+  if (slot_col == in_col + static_cast<u32>(n_in) * T)
+    interpret_run<W, false>(code, n_chunks, n_in, T, in_col, slot_col, out);
+  else
+    interpret_run<W, true>(code, n_chunks, n_in, T, in_col, slot_col, out);
 }
 
 template <int W>

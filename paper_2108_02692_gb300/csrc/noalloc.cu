@@ -161,14 +161,17 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
   lp.code_len = static_cast<int>(p->chunks.size() / 8);
   lp.n_slots = p->n_slots;
   lp.status = reinterpret_cast<int*>(scratch);
-  int threads = 128, nstage = 2;
+  // the interpreter's shape for single launches: one stage, 8 bytes per
+  // thread and strip at 64 threads; the tile shrinks while it does not fit
+  int threads = 64, words = 2;
+  const int nstage = 1;
   size_t smem = 0;
   for (;;) {
-    lp.T = 4 * threads;
+    lp.T = 4 * words * threads;
     smem = xorec::interp_smem_bytes(p->n_in, p->n_slots, lp.T, nstage);
     if (smem <= static_cast<size_t>(optin)) break;
-    if (nstage > 1) { --nstage; continue; }
-    if (threads > 32) { threads /= 2; nstage = 2; continue; }
+    if (words > 1) { words = 1; continue; }
+    if (threads > 32) { threads /= 2; continue; }
     return bad(EC_EINVAL, "program needs more shared memory than one CTA can hold");
   }
   lp.nstage = nstage;
