@@ -153,9 +153,9 @@ typedef struct {
 
 typedef struct {
   int n_in, n_out;      /* input / output strips                              */
-  int slots;            /* pebbles held in shared memory by the interpreter   */
+  int slots;            /* pebbles (slots) of the program's stream            */
   int stmts;            /* statements of the lowered program                  */
-  int code_words;       /* 16-bit words of the instruction stream             */
+  int code_words;       /* 16-bit words of the program's instruction stream   */
   int sched_nvar;       /* pebbles of the paper's game (goals hold)           */
   ec_slp_stats raw;     /* unoptimised binary-chain program (Sec. 7.5)        */
   ec_slp_stats compressed;  /* after (Xor)RePair                              */
@@ -201,11 +201,16 @@ ec_status ec_plan_kernel_source(ec_plan *plan, const int *erasures, int n_erasur
 ec_status ec_plan_module_source(ec_plan *plan, const int *sets, const int *counts, int n_sets,
                                 char *buf, size_t len, size_t *need);
 
-/* Copy the interpreter instruction stream of the encoder (erasures == NULL)
- * or of a decoder into buf (len 16-bit words); *need receives the length.
- * Stream format, statement by statement: n_args; n_outs | has_slot << 15;
- * [slot]; output strip ids; operand ids (< n_in: input strip, else slot +
- * n_in).  For inspection and host-side checks. */
+/* Copy the instruction stream of the encoder's program (erasures == NULL)
+ * or of a decoder's into buf (len 16-bit words); *need receives the length.
+ * This is the optimised, scheduled program that the compiled tier runs, in
+ * stream form.  Stream format, statement by statement: n_args; n_outs |
+ * has_slot << 15; [slot]; output strip ids; operand ids (< n_in: input
+ * strip, else slot + n_in).  The interpreter tier runs the same program,
+ * except for codes of up to 96 input strips, where it runs the unoptimised
+ * fused program (one statement per output strip, no slots): its tile of
+ * inputs and slots lives in shared memory, and without slots twice as many
+ * warps fit an SM.  For inspection and host-side checks. */
 ec_status ec_plan_program(ec_plan *plan, const int *erasures, int n_erasures, uint16_t *buf,
                           size_t len, size_t *need);
 

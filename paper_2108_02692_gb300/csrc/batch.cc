@@ -294,19 +294,26 @@ bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_
   return true;
 }
 
-// Item ranges of a batched launch (one work-queue head each, see
-// run_batch_pipeline): one per SM when every SM's range holds at least four
-// chunks per resident CTA, else a single queue.  EC_BATCH_RANGES overrides
-// (1 = a single queue).
+// A launch's items split into n_ranges contiguous ranges (BatchParams).
 void set_ranges(xk::BatchParams* bp, long long n_items, int n_ranges) {
   bp->n_ranges = std::max(1, n_ranges);
   bp->range_len = n_items / bp->n_ranges;
   bp->range_rem = static_cast<int>(n_items % bp->n_ranges);
 }
 
-int batch_ranges(long long n_items, int sms, int per_sm, int chunk) {
+// Item ranges of a batched launch (one work-queue head each, see
+// run_batch_pipeline): one per SM when every SM's range holds at least four
+// chunks per resident CTA and the programs preload their inputs, else a
+// single queue.  Programs with more input strips are far larger than an SM's
+// instruction cache, so ranges gain nothing there, and their tiles are short
+// (256 B of each of hundreds of strips): with a single queue all CTAs read
+// neighbouring tiles, which keeps DRAM rows open (RS(100,4) decode: 0.39 of
+// the copy bandwidth with one queue, 0.20 with per-SM ranges).
+// EC_BATCH_RANGES overrides (1 = a single queue).
+int batch_ranges(long long n_items, int sms, int per_sm, int chunk, int max_in) {
   const int forced = env_int("EC_BATCH_RANGES", 0);
   if (forced > 0) return std::min(forced, std::max(1, sms));
+  if (max_in > kPreloadMaxInputs) return 1;
   const long long per_range = 4ll * std::max(1, per_sm) * std::max(1, chunk);
   return n_items >= per_range * sms ? std::max(1, sms) : 1;
 }
@@ -393,7 +400,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     Launch& L = b->launches[e.launch];
     e.tiles = (e.S + 4 * L.threads - 1) / (4 * L.threads);
     L.max_in = std::max(L.max_in, e.prog->n_in);
-    if (!mod) L.max_slots = std::max(L.max_slots, e.prog->n_slots);
+    if (!mod) L.max_slots = std::max(L.max_slots, e.prog->interp_slots);
   }
   // interpreter programs need their streams on the device
   for (auto& e : ents)
@@ -436,7 +443,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     d.prog = e.prog->mod_index;
     d.code = e.prog->d_code;
     d.code_len = static_cast<int>(e.prog->chunks.size() / 8);
-    d.n_slots = e.prog->n_slots;
+    d.n_slots = e.prog->interp_slots;
     for (uint64_t p : e.ptrs) blocks.push_back(p);
     {
       bool ok = true;
@@ -540,7 +547,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     }
     const long long grid = static_cast<long long>(di.sms) * std::max(1, per_sm);
     L.grid = static_cast<int>(std::min<long long>(grid, std::max<long long>(1, L.n_items)));
-    L.n_ranges = xorec::batch_ranges(L.n_items, di.sms, per_sm, b->chunk);
+    L.n_ranges = xorec::batch_ranges(L.n_items, di.sms, per_sm, b->chunk, L.max_in);
     if (env_int("XOREC_LOG", 0))
       std::fprintf(stderr, "[xorec] batch launch: %s items=%lld max_in=%d smem=%zu ctas/sm=%d grid=%d regs=%d ranges=%d\n",
                    L.mod ? "module" : "interp", L.n_items, L.max_in, L.smem, per_sm, L.grid,

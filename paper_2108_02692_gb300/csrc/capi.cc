@@ -294,7 +294,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     nstage = env_int("EC_INTERP_NSTAGE", 1);
     for (;;) {
       lp.T = 4 * words * threads;
-      smem = interp_smem_bytes(p->n_in, p->n_slots, lp.T, nstage);
+      smem = interp_smem_bytes(p->n_in, p->interp_slots, lp.T, nstage);
       if (smem <= di.smem_optin) break;
       if (nstage > 1) { --nstage; continue; }
       if (words > 1) { words = 1; continue; }
@@ -304,7 +304,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     }
     lp.code = p->d_code;
     lp.code_len = static_cast<int>(p->chunks.size() / 8);
-    lp.n_slots = p->n_slots;
+    lp.n_slots = p->interp_slots;
     per_sm = interp_max_ctas_per_sm(threads, smem, lp.T);
   }
   lp.nstage = nstage;

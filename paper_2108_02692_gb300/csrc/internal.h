@@ -177,7 +177,7 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
                           int* built);
 bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
                         size_t* smem, int* per_sm);
-int batch_ranges(long long n_items, int sms, int per_sm, int chunk);
+int batch_ranges(long long n_items, int sms, int per_sm, int chunk, int max_in);
 // Split a launch's items into n_ranges contiguous ranges (BatchParams).
 void set_ranges(xk::BatchParams* bp, long long n_items, int n_ranges);
 

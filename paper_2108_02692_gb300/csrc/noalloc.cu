@@ -159,7 +159,7 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
   lp.n_out = p->n_out;
   lp.code = d_code;
   lp.code_len = static_cast<int>(p->chunks.size() / 8);
-  lp.n_slots = p->n_slots;
+  lp.n_slots = p->interp_slots;
   lp.status = reinterpret_cast<int*>(scratch);
   // the interpreter's shape for single launches: one stage, 8 bytes per
   // thread and strip at 64 threads; the tile shrinks while it does not fit
@@ -168,7 +168,7 @@ extern "C" ec_status ec_encode_noalloc(ec_plan* plan, const uint8_t* const* data
   size_t smem = 0;
   for (;;) {
     lp.T = 4 * words * threads;
-    smem = xorec::interp_smem_bytes(p->n_in, p->n_slots, lp.T, nstage);
+    smem = xorec::interp_smem_bytes(p->n_in, p->interp_slots, lp.T, nstage);
     if (smem <= static_cast<size_t>(optin)) break;
     if (words > 1) { words = 1; continue; }
     if (threads > 32) { threads /= 2; continue; }

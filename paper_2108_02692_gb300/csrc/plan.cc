@@ -295,6 +295,20 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   if (!check_program_stream(p.code.data(), p.code.size(), n_in, n_out, p.n_slots, err))
     return false;
   p.chunks = chunk_stream(p.code);
+  p.interp_slots = p.n_slots;
+  if (!two_level && n_in <= kPreloadMaxInputs && p.n_slots > 0) {
+    // The interpreter keeps every input strip and every slot of its tile in
+    // shared memory, so slots cost it resident warps: it runs the
+    // unoptimised fused program instead (one statement per output strip, no
+    // slots), the paper's P^{+F}; more XORs, twice the resident warps.
+    Slp plain = slp_rows_fused(n_in, R, order);
+    Program ip;
+    if (!lower(plain, schedule_dfs(plain, false), n_in, n_out, &ip, err)) return false;
+    if (!check_program_stream(ip.code.data(), ip.code.size(), n_in, n_out, ip.n_slots, err))
+      return false;
+    p.chunks = chunk_stream(ip.code);
+    p.interp_slots = ip.n_slots;
+  }
   p.fused = fused;
   p.sched = gpu;
   *out = std::move(p);

@@ -54,16 +54,20 @@ struct PipelineStats {
 //   arg_0 .. arg_{a-1}   operand ids: < n_in input strip, else slot + n_in
 // `sched` keeps the scheduled fused program for code generation.
 //
-// `chunks` is the same stream as the interpreter reads it on the device:
-// 16-byte chunks of eight 16-bit words, so that one 128-bit load brings
-// eight operand ids.  Per statement: a header chunk (a, o, slot or 0xffff,
-// the first five output strips, unused ones 0xffff), ceil(a/8) chunks of
+// `chunks` is the stream the interpreter runs on the device, in 16-byte
+// chunks of eight 16-bit words, so that one 128-bit load brings eight
+// operand ids.  Per statement: a header chunk (a, o, slot or 0xffff, the
+// first five output strips, unused ones 0xffff), ceil(a/8) chunks of
 // operand ids (the last padded with 0xffff), then, when o > 5, chunks of
-// the remaining output strips (padded with 0xffff).
+// the remaining output strips (padded with 0xffff).  For programs of up to
+// kPreloadMaxInputs inputs it is the unoptimised fused program's stream (no
+// slots: the interpreter's occupancy is bounded by the shared memory its
+// slots take), with interp_slots = 0; otherwise the program's own.
 struct Program {
   int n_in = 0, n_out = 0, n_slots = 0, n_stmts = 0;
   std::vector<uint16_t> code;
   std::vector<uint16_t> chunks;
+  int interp_slots = 0;      // slots of the stream in `chunks`
   PipelineStats stats;
   Slp fused;                 // single-assignment fused program
   Schedule sched;            // GPU schedule of `fused`

@@ -205,13 +205,13 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     d.prog = r.prog->mod_index;
     d.code = r.prog->d_code;
     d.code_len = static_cast<int>(r.prog->chunks.size() / 8);
-    d.n_slots = r.prog->n_slots;
+    d.n_slots = r.prog->interp_slots;
     std::memcpy(h_blocks + off, r.ptrs.data(), r.ptrs.size() * sizeof(xk::u64));
     off += r.ptrs.size();
     l.n += 1;
     l.items += r.tiles;
     l.max_in = std::max(l.max_in, r.prog->n_in);
-    if (!mod) l.max_slots = std::max(l.max_slots, r.prog->n_slots);
+    if (!mod) l.max_slots = std::max(l.max_slots, r.prog->interp_slots);
   }
   // the slot is free: none of its kernels can write the word now
   *reinterpret_cast<volatile int*>(sl.h_status) = 0;
