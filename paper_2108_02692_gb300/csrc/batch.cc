@@ -398,9 +398,18 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     }
     e.launch = it->second;
     Launch& L = b->launches[e.launch];
-    e.tiles = (e.S + 4 * L.threads - 1) / (4 * L.threads);
     L.max_in = std::max(L.max_in, e.prog->n_in);
     if (!mod) L.max_slots = std::max(L.max_slots, e.prog->interp_slots);
+  }
+  // the interpreter's tile shrinks (down to 32 threads, 128 bytes per strip)
+  // until its stage of every input strip and its slots fit one CTA
+  for (auto& L : b->launches)
+    while (!L.mod && L.threads > 32 &&
+           xorec::interp_batch_smem_bytes(L.max_in, L.max_slots, 4 * L.threads) > di.smem_optin)
+      L.threads /= 2;
+  for (auto& e : ents) {
+    const Launch& L = b->launches[e.launch];
+    e.tiles = (e.S + 4 * L.threads - 1) / (4 * L.threads);
   }
   // interpreter programs need their streams on the device
   for (auto& e : ents)

@@ -127,12 +127,27 @@ int default_minb(int threads, int n_in) {
 int program_threads(const Program* p) {
   if (p->threads > 0) return p->threads;
   const int th = env_int("EC_JIT_THREADS", 0);
-  return th > 0 ? th : tile_threads_for_inputs(p->n_in, 128);
+  if (th > 0) return th;
+  // windowed programs keep a ring of a few windows, not a tile of every strip
+  return windowed(*p) ? 128 : tile_threads_for_inputs(p->n_in, 128);
 }
 
 bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin) {
   const size_t smem = 128 + static_cast<size_t>(p->n_in) * 4 * threads + xk::kBatchHeader;
   return smem <= smem_optin && p->stats.fused.mem <= kMaxCompiledMemOps;
+}
+
+// Shared memory of a windowed program's single launch: barriers and the
+// ring of kWinRing windows.
+static size_t window_smem_bytes(const Program* p, int threads) {
+  return 128 + static_cast<size_t>(xk::kWinRing) * p->stats.window * 4 * threads;
+}
+
+bool single_launch_fits(const Program* p, int threads, size_t smem_optin) {
+  if (windowed(*p))
+    return window_smem_bytes(p, threads) <= smem_optin &&
+           p->stats.fused.mem <= kMaxCompiledMemOps;
+  return compiled_tier_fits(p, threads, smem_optin);
 }
 
 // Compile p's straight-line kernel once.  The compile itself runs without
@@ -153,6 +168,7 @@ bool jit_ensure(Program* p, int threads, std::string* err) {
   tmp.n_in = p->n_in;
   tmp.n_out = p->n_out;
   tmp.minb = p->minb;
+  tmp.stats = p->stats;
   if (!jit_compile(&tmp, threads, err)) return false;
   std::lock_guard<std::mutex> lk(g_jit_mu);
   if (p->jit) {
@@ -187,7 +203,7 @@ EncodeTiledFn tensor_map_encoder() {
 
 }  // namespace
 
-int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out) {
+int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out, int box_rows) {
   static_assert(sizeof(xk::TensorMap) == sizeof(CUtensorMap), "tensor map size");
   if (env_int("EC_TMA_TENSOR", 1) == 0) return 0;
   if (io.tab || !io.in_base || io.n_stripes < 1) return 0;
@@ -204,13 +220,18 @@ int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out) 
   const EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return 0;
   // box rows: the largest multiple of 8 strips that divides n_in and fits
-  // a box dimension (256), so that the boxes tile the stage exactly
+  // a box dimension (256), so that the boxes tile the stage exactly; or the
+  // window of a windowed program (rows past n_in are zero-filled)
   int rows = 8;
   for (int r = 256; r >= 8; r -= 8)
     if (n_in % r == 0) {
       rows = r;
       break;
     }
+  if (box_rows > 0) {
+    if (box_rows % 8 != 0 || box_rows > 256) return 0;
+    rows = box_rows;
+  }
   const cuuint64_t dim[3] = {static_cast<cuuint64_t>(S / 4), static_cast<cuuint64_t>(n_in),
                              static_cast<cuuint64_t>(io.n_stripes)};
   const cuuint64_t stride[2] = {static_cast<cuuint64_t>(S), static_cast<cuuint64_t>(sstride)};
@@ -257,7 +278,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     threads = program_threads(p);
     nstage = env_int("EC_JIT_NSTAGE", 1);
     std::string err = "program too large for the compiled tier";
-    compiled = compiled_tier_fits(p, threads, di.smem_optin) && jit_ensure(p, threads, &err);
+    compiled = single_launch_fits(p, threads, di.smem_optin) && jit_ensure(p, threads, &err);
     if (!compiled && executor == EC_EXEC_COMPILED) {
       set_error("compiled tier unavailable: " + err);
       return false;
@@ -271,7 +292,17 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   lp.status = di.status;
   size_t smem = 0;
   int per_sm = 0;
-  if (compiled) {
+  const bool win = compiled && jit_is_windowed(p);
+  if (compiled && win) {
+    int w = 0, n_win = 0, n_phases = 0;
+    window_layout(*p, &w, &n_win, &n_phases, nullptr);
+    lp.T = 4 * threads;
+    lp.win = w;
+    lp.n_win = n_win;
+    lp.n_phases = n_phases;
+    smem = window_smem_bytes(p, threads);
+    per_sm = jit_max_ctas_per_sm(p, threads, smem);
+  } else if (compiled) {
     lp.T = 4 * threads;
     for (;; --nstage) {
       smem = interp_smem_bytes(p->n_in, 0, lp.T, nstage);
@@ -317,12 +348,12 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   if (grid > lp.n_items) grid = lp.n_items;
   if (compiled) {
     xk::TensorMap tm;
-    lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm);
+    lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, win ? lp.win : 0);
     return jit_launch(p, lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem,
                       stream);
   }
   xk::TensorMap tm;
-  lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm);
+  lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, 0);
   return launch_interp(lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem, stream);
 }
 
@@ -774,7 +805,7 @@ ec_status ec_plan_compile(ec_plan* plan, const int* sets, const int* counts, int
   if (!xorec::device_info(&di)) return EC_ECUDA;
   progs.erase(std::remove_if(progs.begin(), progs.end(),
                              [&](Program* p) {
-                               return !xorec::compiled_tier_fits(p, xorec::program_threads(p),
+                               return !xorec::single_launch_fits(p, xorec::program_threads(p),
                                                                  di.smem_optin);
                              }),
               progs.end());

@@ -122,6 +122,9 @@ bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_
 bool jit_available();
 bool jit_ensure(Program* p, int threads, std::string* err);
 bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin);
+// A single launch of `p` fits the compiled tier: its shared memory (the
+// windowed ring, or a stage of every input strip) and its code size.
+bool single_launch_fits(const Program* p, int threads, size_t smem_optin);
 // Threads per CTA of a launch whose tile holds n_in input strips when no
 // shape was chosen: `threads`, halved (not below 64) while two CTAs' tiles
 // do not fit one CTA's shared memory, so that an SM keeps at least two CTAs
@@ -138,13 +141,23 @@ int minb_for(int threads, int reg_budget);
 // kPreloadCap128Inputs input strips.
 int default_minb(int threads, int n_in);
 bool jit_compile(Program* p, int threads, std::string* err);
+// Two-level programs that stream their inputs window by window through a
+// small ring (run_window_pipeline): the layout of their phases (jit.cc).
+bool window_layout(const Program& p, int* win, int* n_win, int* n_phases,
+                   std::vector<int>* phase);
+// The compiled tier runs `p` with the windowed pipeline (EC_WINDOWED=0
+// turns it off).
+bool windowed(const Program& p);
+// The compiled kernel of `p` exists and is the windowed form (its launch
+// follows the kernel, whatever EC_WINDOWED says later).
+bool jit_is_windowed(const Program* p);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
                 int grid, size_t smem, cudaStream_t stream);
 // Tensor map of a strided launch's inputs as [stripe][input strip][4-byte
 // word] with a box of one tile of up to 256 input strips; returns the strips
 // per box (a multiple of 8 that divides n_in), or 0 (no map) when the layout
 // or the driver does not allow one.
-int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out);
+int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out, int box_rows);
 // Tensor map of one block as [strip][4-byte word] (8 strips S bytes apart)
 // with a box of one tile of its 8 strips; false when not allowed.
 bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out);

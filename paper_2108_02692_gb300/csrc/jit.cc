@@ -45,7 +45,8 @@ __device__ __forceinline__ xk::u32 xk_x2(xk::u32 a, xk::u32 b) {
 struct JitKernel {
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kern = nullptr;
-  int threads = 0;
+  int threads = 0;          // threads that own a column of the tile
+  int block = 0;            // threads per CTA (a producer warp more for windowed programs)
   int regs = 0;
   size_t smem_set = 0;
   int device = -1;
@@ -101,6 +102,82 @@ void emit_statements(std::ostringstream& os, const xorec::Program& p) {
     if (t < 0) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", 0u);\n";
     else if (t < nc) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", I(" << t << "));\n";
   }
+}
+
+// Windowed form of a two-level program (run_window_pipeline): the
+// statements in phases of (group of rows, window of inputs), each phase
+// reading its operands from the ring slot it waits for and releasing the
+// slot when it ends.  I(c) is redefined at every phase start.
+std::string gen_window_body(const xorec::Program& p, int threads) {
+  int win = 0, n_win = 0, n_phases = 0;
+  std::vector<int> phase;
+  xorec::window_layout(p, &win, &n_win, &n_phases, &phase);
+  const xorec::Slp& q = p.fused;
+  const int nc = q.n_const;
+  const int T = 4 * threads;
+  std::ostringstream os;
+  os << "struct SlpBody {\n"
+        "  __device__ __forceinline__ bool compute(const xk::LaunchParams& p, const xk::WindowView& v,\n"
+        "      xk::i64 q0, xk::i64 s, xk::i64 c0, int len, int col) const {\n"
+        "    const bool keep = col < len;\n"
+        "    const xk::i64 S = p.io.S;\n";
+  for (int b = 0; b < p.n_out / 8; ++b)
+    os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
+  os << "#define O(b, t, v) if (keep) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
+  std::vector<int> loaded(nc, -1);
+  std::vector<std::vector<int>> outs_of(q.n_var);
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
+    if (q.ret[r] >= nc) outs_of[q.ret[r] - nc].push_back(r);
+  int open = -1;   // phase whose slot is held
+  auto enter = [&](int ph) {
+    while (open < ph) {
+      if (open >= 0) os << "    v.end(q0 + " << open << ");\n";
+      ++open;
+      const int c0w = (open % n_win) * win;
+      os << "    const xk::u8* in" << open << " = v.begin(q0 + " << open << ");\n"
+         << "    if (!in" << open << ") return false;\n"
+         << "    in" << open << " += col;\n"
+         << "#undef I\n#define I(c) (*reinterpret_cast<const xk::u32*>(in" << open << " + ((c) - "
+         << c0w << ") * " << T << "))\n";
+    }
+  };
+  for (size_t k = 0; k < p.sched.steps.size(); ++k) {
+    const auto& st = p.sched.steps[k];
+    const int g = p.load_group[k];
+    enter(phase[k]);
+    for (int a : st.args)
+      if (a < nc && loaded[a] != g) {
+        os << "    const xk::u32 i" << a << "_" << g << " = I(" << a << ");\n";
+        loaded[a] = g;
+      }
+    os << "    const xk::u32 v" << st.node << " = ";
+    if (st.args.size() >= 2 && st.args.size() <= 3) {
+      os << (st.args.size() == 3 ? "xk_x3(" : "xk_x2(");
+      for (size_t i = 0; i < st.args.size(); ++i) {
+        const int a = st.args[i];
+        if (i) os << ", ";
+        if (a < nc) os << "i" << a << "_" << g;
+        else os << "v" << (a - nc);
+      }
+      os << ");\n";
+    } else {
+      if (st.args.empty()) os << "0u";
+      for (size_t i = 0; i < st.args.size(); ++i) {
+        const int a = st.args[i];
+        if (i) os << " ^ ";
+        if (a < nc) os << "i" << a << "_" << g;
+        else os << "v" << (a - nc);
+      }
+      os << ";\n";
+    }
+    for (int r : outs_of[st.node]) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", v" << st.node << ");\n";
+  }
+  enter(n_phases - 1);   // phases without statements still take and free their slot
+  os << "    v.end(q0 + " << (n_phases - 1) << ");\n";
+  for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
+    if (q.ret[r] < 0) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", 0u);\n";
+  os << "#undef I\n#undef O\n    return true;\n  }\n};\n";
+  return os.str();
 }
 
 // Single-program body.  Narrow programs (n_in <= kPreloadMaxInputs):
@@ -247,10 +324,22 @@ int env_or(const char* name, int dflt) {
   return v && *v ? std::atoi(v) : dflt;
 }
 
-std::string gen_source(const xorec::Program& p, int threads) {
+// minb > 0 overrides the resident CTAs per SM the kernel is built for.
+std::string gen_source(const xorec::Program& p, int threads, int minb = 0) {
   std::ostringstream os;
   os << kPipelineSrc << "\n";
   if (!p.load_group.empty()) os << kOpaqueXorSrc;
+  if (xorec::windowed(p)) {
+    const int block = threads + 32;
+    os << gen_window_body(p, threads);
+    os << "extern \"C\" __global__ void __launch_bounds__(" << block << ", "
+       << (minb > 0 ? minb : p.minb > 0 ? p.minb : xorec::minb_for(block, 128))
+       << ") xorec_slp(xk::LaunchParams p, const __grid_constant__ xk::TensorMap tm) {\n"
+          "  extern __shared__ __align__(128) xk::u8 smem[];\n"
+          "  xk::run_window_pipeline(p, smem, SlpBody(), &tm);\n"
+          "}\n";
+    return os.str();
+  }
   os << gen_body(p, threads);
   os << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", "
      << (p.minb > 0 ? p.minb : env_or("EC_JIT_MINB", xorec::default_minb(threads, p.n_in)))
@@ -264,6 +353,60 @@ std::string gen_source(const xorec::Program& p, int threads) {
 }  // namespace
 
 namespace xorec {
+
+// Phases of a two-level program read window by window: window `win` (the
+// program's input window, a multiple of 8 strips), n_win windows per group,
+// one phase per (group, window) in that order; phase[k] is the phase of
+// schedule step k (a step with input operands belongs to their window, one
+// without to the phase before it).  False when the program does not have
+// that form (not two-level, or an output that is an input strip itself).
+bool window_layout(const Program& p, int* win, int* n_win, int* n_phases, std::vector<int>* phase) {
+  if (p.load_group.empty() || p.stats.window <= 0 || p.stats.window % 8 != 0) return false;
+  const int nc = p.fused.n_const;
+  if (p.load_group.size() != p.sched.steps.size() || p.sched.steps.empty()) return false;
+  for (int t : p.fused.ret)
+    if (t >= 0 && t < nc) return false;
+  const int w = p.stats.window;
+  const int nw = (p.n_in + w - 1) / w;
+  int groups = 0;
+  for (int g : p.load_group) groups = std::max(groups, g + 1);
+  std::vector<int> ph(p.sched.steps.size(), 0);
+  int cur = 0;
+  for (size_t k = 0; k < p.sched.steps.size(); ++k) {
+    int x = -1;
+    for (int a : p.sched.steps[k].args)
+      if (a < nc) {
+        const int y = p.load_group[k] * nw + a / w;
+        if (x >= 0 && y != x) return false;   // operands from two windows
+        x = y;
+      }
+    if (x < 0) x = cur;
+    if (x < cur) return false;                // phases must not go back
+    ph[k] = cur = x;
+  }
+  *win = w;
+  *n_win = nw;
+  *n_phases = groups * nw;
+  if (phase) *phase = std::move(ph);
+  return true;
+}
+
+// Measured on GB300 (encode, 128 stripes x 1 MiB, fraction of the copy
+// bandwidth, full-stage kernel -> windowed): RS(100,4) 0.45 -> 0.93,
+// RS(48,4) 0.75 -> 0.98, RS(32,4) 0.93 -> 0.98 (scaled Cauchy matrix 1.03 ->
+// 0.99), RS(16,4) 1.02 -> 0.98, RS(24,8) (two groups) 0.78 -> 0.68.  The
+// full-stage kernel keeps several CTAs per SM up to 256 input strips, and a
+// second group of rows reads every window again, so the windowed pipeline is
+// taken for single-group programs of more than 256 input strips.
+// EC_WINDOWED=1 takes it for every program of the form, 0 for none.
+bool windowed(const Program& p) {
+  const char* e = std::getenv("EC_WINDOWED");
+  const int force = e && *e ? std::atoi(e) : -1;
+  if (force == 0) return false;
+  int win, n_win, n_phases;
+  if (!window_layout(p, &win, &n_win, &n_phases, nullptr)) return false;
+  return force == 1 || (n_phases == n_win && p.n_in > 256);
+}
 
 bool jit_available() {
   int major = 0, minor = 0;
@@ -297,7 +440,7 @@ static long spill_stores(const std::string& log) {
 // With spill_bytes, ptxas also reports and *spill_bytes receives the bytes
 // it spilled per thread.
 static JitKernel* compile_and_load(const std::string& src, const char* name, int threads,
-                                   std::string* err, long* spill_bytes = nullptr) {
+                                   std::string* err, long* spill_bytes = nullptr, int block = 0) {
   xorec::TraceRange trace_("xorec nvrtc compile");
   DeviceInfo di;
   if (!device_info(&di)) {
@@ -352,6 +495,7 @@ static JitKernel* compile_and_load(const std::string& src, const char* name, int
     return nullptr;
   }
   jk->threads = threads;
+  jk->block = block > 0 ? block : threads;
   jk->device = di.device;
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(jk->kern)) == cudaSuccess)
@@ -361,11 +505,35 @@ static JitKernel* compile_and_load(const std::string& src, const char* name, int
   return jk;
 }
 
+static void jit_release_kernel(JitKernel* jk) {
+  cudaLibraryUnload(jk->lib);
+  delete jk;
+}
+
 // Compile `p` for the current device's architecture.  Stores a JitKernel in
 // p->jit on success.
 bool jit_compile(Program* p, int threads, std::string* err) {
   if (p->jit) return true;
-  JitKernel* jk = compile_and_load(gen_source(*p, threads), "xorec_slp", threads, err);
+  if (windowed(*p) && p->minb <= 0) {
+    // the register cap of three resident CTAs is too tight for the partial
+    // sums and window inputs of the widest programs: ptxas spills there, and
+    // the kernel is compiled again for two CTAs per SM
+    int minb = minb_for(threads + 32, 128);
+    for (;;) {
+      long spill = 0;
+      JitKernel* jk = compile_and_load(gen_source(*p, threads, minb), "xorec_slp", threads, err,
+                                       &spill, threads + 32);
+      if (!jk) return false;
+      if (spill == 0 || minb <= 2) {
+        p->jit = jk;
+        return true;
+      }
+      jit_release_kernel(jk);
+      --minb;
+    }
+  }
+  JitKernel* jk = compile_and_load(gen_source(*p, threads), "xorec_slp", threads, err, nullptr,
+                                   windowed(*p) ? threads + 32 : threads);
   if (!jk) return false;
   p->jit = jk;
   return true;
@@ -444,9 +612,10 @@ int jit_module_regs(void* mod) {
 int jit_max_ctas_per_sm(Program* p, int threads, size_t smem) {
   auto* jk = static_cast<JitKernel*>(p->jit);
   if (!jk || !jit_set_smem(jk, smem)) return 0;
+  (void)threads;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, reinterpret_cast<const void*>(jk->kern),
-                                                    threads, smem) != cudaSuccess) {
+                                                    jk->block, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -470,7 +639,7 @@ bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm,
   else std::memset(&map, 0, sizeof(map));
   void* args[] = {&copy, &map};
   const cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(jk->kern), dim3(grid),
-                                         dim3(threads), args, smem, stream);
+                                         dim3(jk->block), args, smem, stream);
   if (e != cudaSuccess) {
     set_error(std::string("compiled kernel launch failed: ") + cudaGetErrorString(e));
     return false;
@@ -487,6 +656,11 @@ void jit_release(Program* p) {
   cudaLibraryUnload(jk->lib);
   delete jk;
   p->jit = nullptr;
+}
+
+bool jit_is_windowed(const Program* p) {
+  const auto* jk = static_cast<const JitKernel*>(p ? p->jit : nullptr);
+  return jk && jk->block != jk->threads;
 }
 
 int jit_regs(const Program* p) {

@@ -64,7 +64,13 @@ struct LaunchParams {
   int code_len;
   int n_slots;
   int* status;
+  // windowed programs (run_window_pipeline): input strips per window, windows
+  // per group of rows, phases per item (groups x windows); 0 otherwise
+  int win, n_win, n_phases, pad_;
 };
+
+// Window slots in the shared-memory ring of windowed programs.
+constexpr int kWinRing = 4;
 
 // Batched launches: every stripe has its own program, strip length and
 // blocks.  Work items are (stripe, tile) pairs listed in `items`.
@@ -300,6 +306,136 @@ __device__ __forceinline__ void run_pipeline(const LaunchParams& p, u8* smem, co
         __syncwarp();
         issue_item(p, tm, nxt, stages + st * stage_bytes, smem_addr(&bars[st]));
       }
+    }
+  }
+}
+
+// Windowed pipeline, for two-level programs whose inputs stream through in
+// windows (the multilevel pebble game: registers hold the partial sums of a
+// group of rows, shared memory one window of input strips at a time).  The
+// program reads the windows in a fixed order of phases: for every group of
+// rows, every window of `win` input strips in turn.  Instead of a stage
+// holding a tile of all n_in strips, shared memory holds a ring of kWinRing
+// window slots (win x T bytes each), so several CTAs fit an SM even for codes
+// of hundreds of strips.  Warp 0 produces: for each of the CTA's items and
+// each phase it waits until the phase's slot is free, then copies the
+// phase's window into it (one tiled tensor copy of `win` strips when the
+// launch has a tensor map, else one 1-D bulk copy per strip).  The other
+// warps consume: the program waits for each phase's slot, reads its operands
+// from it, and releases it (one arrival per consumer thread).  A group of
+// rows after the first reads the windows again; they come from L2.
+//
+// Shared memory: [full barriers][empty barriers] (128 B), then the ring.
+// Consumer-side view of the ring.  Phase q of the CTA's running phase count
+// uses slot q % kWinRing, in round q / kWinRing.
+struct WindowView {
+  u8* ring;
+  u32 full0, empty0;     // shared addresses of the barrier arrays
+  i64 slot_bytes;
+  // Wait for phase q's window; the slot's address, or null after a wait
+  // that timed out.
+  __device__ __forceinline__ const u8* begin(i64 q) const {
+    const int slot = static_cast<int>(q % kWinRing);
+    if (!mbar_wait(full0 + 8u * slot, static_cast<u32>((q / kWinRing) & 1))) return nullptr;
+    return ring + slot * slot_bytes;
+  }
+  // This thread is done with phase q's window.
+  __device__ __forceinline__ void end(i64 q) const {
+    const int slot = static_cast<int>(q % kWinRing);
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }"
+                 ::"r"(empty0 + 8u * slot) : "memory");
+  }
+};
+
+// Warp 0: copy window w of `item` into `dst`; completion on `bar`.
+__device__ __forceinline__ void issue_window(const LaunchParams& p, const TensorMap* tm, i64 item,
+                                             int w, u8* dst, u32 bar) {
+  const i64 s = item / p.tiles_per_strip;
+  const i64 c0 = (item % p.tiles_per_strip) * p.T;
+  const int lane = threadIdx.x & 31;
+  const int y0 = w * p.win;
+  if (p.tmap > 0) {
+    // one box of `win` strips; rows past n_in are zero-filled and counted
+    if (lane == 0) {
+      mbar_arrive_expect_tx(bar, static_cast<u32>(p.win) * static_cast<u32>(p.T));
+      tma_load_3d(smem_addr(dst), tm, static_cast<int>(c0 >> 2), y0, static_cast<int>(s), bar);
+    }
+    return;
+  }
+  const i64 rest = p.io.S - c0;
+  const int len = rest < p.T ? static_cast<int>(rest) : p.T;
+  const int n = p.n_in - y0 < p.win ? p.n_in - y0 : p.win;
+  if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(n) * static_cast<u32>(len));
+  __syncwarp();
+  for (int c = lane; c < n; c += 32) {
+    const int strip = y0 + c;
+    const u8* src = in_block(p.io, s, strip >> 3) + static_cast<i64>(strip & 7) * p.io.S + c0;
+    tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), src, static_cast<u32>(len), bar);
+  }
+}
+
+// Body (windowed programs):
+//   bool compute(const LaunchParams&, const WindowView&, i64 q0, i64 stripe,
+//                i64 c0, int len, int col) const
+// runs the program on column `col` of the item whose first phase is the
+// CTA's phase q0 (col may lie past len: its results are not stored, but it
+// takes part in every phase); false when a wait timed out.
+template <class Body>
+__device__ __forceinline__ void run_window_pipeline(const LaunchParams& p, u8* smem,
+                                                    const Body& body, const TensorMap* tm) {
+  u64* full = reinterpret_cast<u64*>(smem);
+  u64* empty = reinterpret_cast<u64*>(smem + 64);
+  const int tid = threadIdx.x;
+  const int n_cons = static_cast<int>(blockDim.x) - 32;
+  WindowView v;
+  v.ring = smem + 128;
+  v.full0 = smem_addr(full);
+  v.empty0 = smem_addr(empty);
+  v.slot_bytes = static_cast<i64>(p.win) * p.T;
+  if (tid == 0) {
+    for (int r = 0; r < kWinRing; ++r) {
+      mbar_init(smem_addr(&full[r]), 1);
+      mbar_init(smem_addr(&empty[r]), static_cast<u32>(n_cons));
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const i64 first = blockIdx.x, step = gridDim.x;
+  if (tid < 32) {
+    // producer: a fresh empty barrier counts its phase before phase 0 as
+    // complete, so the first round of slots needs no release
+    i64 q = 0;
+    bool ok = true;
+    for (i64 item = first; ok && item < p.n_items; item += step)
+      for (int ph = 0; ph < p.n_phases; ++ph, ++q) {
+        const int slot = static_cast<int>(q % kWinRing);
+        if (tid == 0) ok = mbar_wait(smem_addr(&empty[slot]), static_cast<u32>(((q / kWinRing) & 1) ^ 1));
+        ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+        if (!ok) break;
+        if (tid == 0) fence_proxy_async();
+        __syncwarp();
+        issue_window(p, tm, item, ph % p.n_win, v.ring + slot * v.slot_bytes,
+                     smem_addr(&full[slot]));
+      }
+    if (!ok && tid == 0) {
+      // a release never came: record it and let the copies in flight land
+      // (bounded) before the CTA ends
+      atomicExch(p.status, XK_STATUS_TIMEOUT);
+      for (i64 d = q - kWinRing; d < q; ++d)
+        if (d >= 0) mbar_wait(smem_addr(&full[d % kWinRing]), static_cast<u32>((d / kWinRing) & 1));
+    }
+    return;
+  }
+  const int col = (tid - 32) * 4;
+  i64 q0 = 0;
+  for (i64 item = first; item < p.n_items; item += step, q0 += p.n_phases) {
+    const i64 s = item / p.tiles_per_strip;
+    const i64 c0 = (item % p.tiles_per_strip) * p.T;
+    const i64 rest = p.io.S - c0;
+    const int len = rest < p.T ? static_cast<int>(rest) : p.T;
+    if (!body.compute(p, v, q0, s, c0, len, col)) {
+      atomicExch(p.status, XK_STATUS_TIMEOUT);
+      return;
     }
   }
 }

@@ -130,7 +130,7 @@ extern "C" ec_status ec_plan_autotune(ec_plan* plan, size_t block_bytes, int n_s
     }
     prog->threads = cands[c].threads;
     prog->minb = xorec::minb_for(cands[c].threads, cands[c].reg_budget);
-    if (!xorec::compiled_tier_fits(prog.get(), prog->threads, di.smem_optin)) continue;
+    if (!xorec::single_launch_fits(prog.get(), prog->threads, di.smem_optin)) continue;
     if (!xorec::launch_program(prog.get(), io, EC_EXEC_COMPILED, st)) {   // compiles
       xorec::jit_release(prog.get());
       continue;

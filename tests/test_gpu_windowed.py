@@ -1,0 +1,146 @@
+"""The windowed pipeline of two-level programs (multilevel pebble game,
+Sec. 8, with inputs streamed window by window through a ring of shared
+memory): a producer warp copies one window of 32 input strips per phase,
+the program consumes the windows in phase order.  Checked against the
+oracle with the pipeline forced on (EC_WINDOWED=1) for codes it would not
+take by default, and at its default for the widest ones: tensor copies with
+a partial last window (RS(13,4): 104 strips), two groups of rows (RS(24,8)),
+per-strip copies from block pointer tables, ragged strip tails, decoders,
+and a code whose kernel is recompiled for two CTAs per SM (RS(100,4))."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2108_02692_gb300 as xo
+from paper_2108_02692_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _windowed_source(plan, erasures=None):
+    return "xk::run_window_pipeline(p, smem, SlpBody()" in xo.ec_plan_kernel_source(plan, erasures)
+
+
+@pytest.mark.parametrize("k,m,force", [(13, 4, True), (16, 4, True), (24, 8, True),
+                                       (48, 4, False), (100, 4, False)])
+def test_windowed_strided_encode(k, m, force, monkeypatch):
+    """ec_encode_strided: one tiled tensor copy per window (a box of 32
+    strips; past the last strip the box is zero-filled); strips of 1552 B
+    end in a ragged 16-byte tile."""
+    if force:
+        monkeypatch.setenv("EC_WINDOWED", "1")
+    torch.cuda.set_device(0)
+    B, n = 8 * 1552, 3
+    data = np.stack([np.stack([synth.block_bytes(97, s, j, B) for j in range(k)])
+                     for s in range(n)])
+    d = torch.from_numpy(data).cuda()
+    plan = xo.ec_plan_create_ex(k, m, executor=xo.EC_EXEC_COMPILED)
+    try:
+        assert _windowed_source(plan)
+        par = torch.full((n, m, B), 0x5A, dtype=torch.uint8, device="cuda")
+        xo.ec_encode_strided(plan, d.data_ptr(), k * B, B, par.data_ptr(), m * B, B, n, B, stream())
+        torch.cuda.synchronize()
+        got = par.cpu().numpy()
+        P = oracle.cauchy(k, m)
+        for s in range(n):
+            ref = oracle.encode(P, list(data[s]))
+            for i in range(m):
+                assert np.array_equal(got[s, i], ref[i]), (s, i)
+    finally:
+        xo.ec_plan_destroy(plan)
+    assert xo.ec_device_status() == 0
+
+
+@pytest.mark.parametrize("k,m", [(13, 4), (24, 8), (48, 4)])
+def test_windowed_table_encode_and_decode(k, m, monkeypatch):
+    """ec_encode and ec_decode (block pointer tables: one 1-D bulk copy per
+    strip of the window) through the windowed pipeline."""
+    monkeypatch.setenv("EC_WINDOWED", "1")
+    torch.cuda.set_device(0)
+    B = 8 * 2064                                    # 4 tiles of 512 B and a 16-byte tail
+    plan = xo.ec_plan_create_ex(k, m, executor=xo.EC_EXEC_COMPILED)
+    try:
+        P = oracle.cauchy(k, m)
+        data = [synth.block_bytes(98, k, j, B) for j in range(k)]
+        blocks = data + oracle.encode(P, data)
+        d = [torch.from_numpy(x).cuda() for x in blocks]
+        par = [torch.full((B,), 0x3C, dtype=torch.uint8, device="cuda") for _ in range(m)]
+        xo.ec_encode(plan, [t.data_ptr() for t in d[:k]], [t.data_ptr() for t in par], B, stream())
+        torch.cuda.synchronize()
+        for i in range(m):
+            assert np.array_equal(par[i].cpu().numpy(), blocks[k + i]), i
+        for er in ([0, 5, k + 1], [1, 2, 3, k + m - 1], [k - 1]):
+            assert _windowed_source(plan, er)
+            out = [torch.full((B,), 0x3C, dtype=torch.uint8, device="cuda") for _ in er]
+            xo.ec_decode(plan, er, [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                         [t.data_ptr() for t in out], B, stream())
+            torch.cuda.synchronize()
+            for t, e in zip(out, er):
+                assert np.array_equal(t.cpu().numpy(), blocks[e]), (er, e)
+    finally:
+        xo.ec_plan_destroy(plan)
+    assert xo.ec_device_status() == 0
+
+
+def test_windowed_and_full_stage_kernels_agree():
+    """RS(32,4) (256 strips: the full-stage kernel by default) encoded by both
+    forms on arbitrary bytes gives identical parity."""
+    torch.cuda.set_device(0)
+    k, m, B, n = 32, 4, 8 * 4096, 4
+    d = torch.empty((n, k, B), dtype=torch.uint8, device="cuda")
+    for s in range(n):
+        for j in range(k):
+            xo.ec_synth_fill(d[s, j].data_ptr(), B, synth.block_seed(99, s, j), 0, stream())
+    outs = []
+    for force in ("0", "1"):
+        import os
+        os.environ["EC_WINDOWED"] = force
+        try:
+            plan = xo.ec_plan_create_ex(k, m, executor=xo.EC_EXEC_COMPILED)
+            try:
+                assert _windowed_source(plan) == (force == "1")
+                par = torch.zeros((n, m, B), dtype=torch.uint8, device="cuda")
+                xo.ec_encode_strided(plan, d.data_ptr(), k * B, B, par.data_ptr(), m * B, B, n, B,
+                                     stream())
+                torch.cuda.synchronize()
+                outs.append(par.cpu().numpy())
+            finally:
+                xo.ec_plan_destroy(plan)
+        finally:
+            del os.environ["EC_WINDOWED"]
+    assert np.array_equal(outs[0], outs[1])
+    assert xo.ec_device_status() == 0
+
+
+def test_batch_of_a_very_wide_code():
+    """RS(128,4) decodes in a batch: 1024 input strips do not fit a stage of
+    512-byte tiles in one CTA, so the batch's interpreter launch takes
+    smaller tiles; bit-exact against the codeword."""
+    torch.cuda.set_device(0)
+    k, m, B = 128, 4, 8 * 1040
+    plan = xo.ec_plan_create(k, m)
+    try:
+        P = oracle.cauchy(k, m)
+        data = [synth.block_bytes(100, 0, j, B) for j in range(k)]
+        blocks = data + oracle.encode(P, data)
+        d = [torch.from_numpy(x).cuda() for x in blocks]
+        jobs, outs, want = [], [], []
+        for er in ([0, 1, 2, 3], [5, k + 2], [k + 3]):
+            o = [torch.full((B,), 0x77, dtype=torch.uint8, device="cuda") for _ in er]
+            jobs.append({"plan": plan, "op": xo.EC_OP_DECODE, "erasures": er,
+                         "blocks": [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                         "out": [t.data_ptr() for t in o], "block_bytes": B})
+            outs += o
+            want += [blocks[e] for e in er]
+        xo.ec_run_batch(jobs, stream())
+        for t, w in zip(outs, want):
+            assert np.array_equal(t.cpu().numpy(), w)
+    finally:
+        xo.ec_plan_destroy(plan)
+    assert xo.ec_device_status() == 0
