@@ -21,6 +21,7 @@
 #include <cstring>
 #include <map>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -210,6 +211,30 @@ int plan_module_minb(const ec_plan* p, int n_in) {
 // interpreter's default.
 int launch_threads(void* mod) { return mod ? jit_module_threads(mod) : batch_threads(); }
 
+// A program of one group of rows that the windowed pipeline runs (its
+// modules hold a ring of windows, not a stage of every input strip).
+static bool window_program(const Program* p) {
+  int w, nw, np;
+  return windowed(*p) && window_layout(*p, &w, &nw, &np, nullptr) && np == nw;
+}
+
+// Threads that own a column in the module that runs `prog`: the plan's
+// tuned shape, else 128 for windowed programs and the default module shape
+// otherwise.
+int module_threads(const ec_plan* plan, const Program* prog) {
+  if (plan->tuned_threads > 0) return plan->tuned_threads;
+  return window_program(prog) ? 128 : plan_module_threads(plan, prog->n_in);
+}
+
+// Such a module fits one CTA: a ring of windows (windowed programs) or a
+// stage of every input strip, and code small enough to compile quickly.
+static bool module_fits(const Program* prog, int threads, size_t smem_optin) {
+  if (window_program(prog))
+    return 128 + static_cast<size_t>(xk::kWinRing) * prog->stats.window * 4 * threads <= smem_optin &&
+           prog->stats.fused.mem <= kMaxCompiledMemOps;
+  return compiled_tier_fits(prog, threads, smem_optin);
+}
+
 // Compile every program of `want` that has no module of its plan's launch
 // shape into multi-program modules (per plan and input width, NVRTC, in
 // parallel host threads).  Modules belong to their plan.  Each group is cut
@@ -224,17 +249,18 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
   const long module_mem = 131072;
   DeviceInfo di;
   if (!device_info(&di)) return EC_ECUDA;
-  std::map<std::pair<ec_plan*, int>, std::vector<Program*>> pending;
+  // modules per plan, input width and pipeline (windowed or not)
+  std::map<std::tuple<ec_plan*, int, bool>, std::vector<Program*>> pending;
   std::vector<Program*> seen;
   for (const auto& w : want) {
-    const int threads = plan_module_threads(w.first, w.second->n_in);
-    if (!compiled_tier_fits(w.second, threads, di.smem_optin)) continue;   // interpreter
+    const int threads = module_threads(w.first, w.second);
+    if (!module_fits(w.second, threads, di.smem_optin)) continue;   // interpreter
     std::lock_guard<std::mutex> lk(w.first->mu);
     if ((w.second->mod && jit_module_threads(w.second->mod) == threads) ||
         std::find(seen.begin(), seen.end(), w.second) != seen.end())
       continue;
     seen.push_back(w.second);
-    pending[{w.first, w.second->n_in}].push_back(w.second);
+    pending[{w.first, w.second->n_in, window_program(w.second)}].push_back(w.second);
   }
   std::vector<std::pair<ec_plan*, std::vector<Program*>>> to_compile;
   for (auto& kv : pending) {
@@ -245,7 +271,7 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
     const long n_mod = std::max({1L, (n + module_size - 1) / module_size,
                                  std::min(n, (mem + module_mem - 1) / module_mem)});
     for (long m = 0; m < n_mod; ++m)
-      to_compile.emplace_back(kv.first.first,
+      to_compile.emplace_back(std::get<0>(kv.first),
                               std::vector<Program*>(ps.begin() + n * m / n_mod,
                                                     ps.begin() + n * (m + 1) / n_mod));
   }
@@ -255,7 +281,7 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
     std::vector<const Program*> ps(to_compile[i].second.begin(), to_compile[i].second.end());
     ec_plan* plan = to_compile[i].first;
     const int n_in = ps.front()->n_in;
-    mods[i] = jit_compile_module(ps, plan_module_threads(plan, n_in), plan_module_minb(plan, n_in),
+    mods[i] = jit_compile_module(ps, module_threads(plan, ps.front()), plan_module_minb(plan, n_in),
                                  &errs[i], env_int("EC_MODULE_NO_SPILL", 0) != 0);
   });
   if (built) *built = static_cast<int>(to_compile.size());
@@ -283,6 +309,12 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
 bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
                         size_t* smem, int* per_sm) {
   const int T = 4 * threads;
+  int win = 0, n_win = 0;
+  if (mod && jit_module_window(mod, &win, &n_win)) {
+    *smem = 128 + static_cast<size_t>(xk::kWinRing) * win * T;
+    *per_sm = std::max(1, jit_module_ctas_per_sm(mod, *smem));
+    return true;
+  }
   if (mod) {
     *smem = xk::kBatchHeader + static_cast<size_t>(max_in) * T;
     *per_sm = std::max(1, jit_module_ctas_per_sm(mod, *smem));
@@ -673,7 +705,7 @@ ec_status ec_plan_module_source(ec_plan* plan, const int* sets, const int* count
   const int n_in = progs.front()->n_in;
   for (const Program* p : progs)
     if (p->n_in != n_in) return fail(EC_EINVAL, "programs of one module share their input count");
-  const std::string src = xorec::jit_module_source(progs, xorec::plan_module_threads(plan, n_in),
+  const std::string src = xorec::jit_module_source(progs, xorec::module_threads(plan, progs.front()),
                                                    xorec::plan_module_minb(plan, n_in));
   if (need) *need = src.size() + 1;
   if (buf && len > 0) {

@@ -151,6 +151,11 @@ bool windowed(const Program& p);
 // The compiled kernel of `p` exists and is the windowed form (its launch
 // follows the kernel, whatever EC_WINDOWED says later).
 bool jit_is_windowed(const Program* p);
+// A module of `progs` takes the batched windowed pipeline (jit.cc): its
+// window and windows per item.
+bool window_module(const std::vector<const Program*>& progs, int* win, int* n_win);
+// The module is windowed: its window and windows per item.
+bool jit_module_window(void* mod, int* win, int* n_win);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
                 int grid, size_t smem, cudaStream_t stream);
 // Tensor map of a strided launch's inputs as [stripe][input strip][4-byte

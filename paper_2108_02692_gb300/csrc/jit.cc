@@ -47,6 +47,7 @@ struct JitKernel {
   cudaKernel_t kern = nullptr;
   int threads = 0;          // threads that own a column of the tile
   int block = 0;            // threads per CTA (a producer warp more for windowed programs)
+  int win = 0, n_win = 0;   // windowed modules: strips per window, windows per item
   int regs = 0;
   size_t smem_set = 0;
   int device = -1;
@@ -104,25 +105,18 @@ void emit_statements(std::ostringstream& os, const xorec::Program& p) {
   }
 }
 
-// Windowed form of a two-level program (run_window_pipeline): the
-// statements in phases of (group of rows, window of inputs), each phase
-// reading its operands from the ring slot it waits for and releasing the
-// slot when it ends.  I(c) is redefined at every phase start.
-std::string gen_window_body(const xorec::Program& p, int threads) {
+// The statements of a windowed program in phases of (group of rows, window
+// of inputs), after the output pointers ob<b>, `keep`, `S`, `v`, `q0` and
+// `col` are in scope: each phase waits for its ring slot, redefines I(c) to
+// read from it and releases it at its end; outputs that are zero are written
+// after the last phase.
+void emit_window_statements(std::ostringstream& os, const xorec::Program& p, int threads) {
   int win = 0, n_win = 0, n_phases = 0;
   std::vector<int> phase;
   xorec::window_layout(p, &win, &n_win, &n_phases, &phase);
   const xorec::Slp& q = p.fused;
   const int nc = q.n_const;
   const int T = 4 * threads;
-  std::ostringstream os;
-  os << "struct SlpBody {\n"
-        "  __device__ __forceinline__ bool compute(const xk::LaunchParams& p, const xk::WindowView& v,\n"
-        "      xk::i64 q0, xk::i64 s, xk::i64 c0, int len, int col) const {\n"
-        "    const bool keep = col < len;\n"
-        "    const xk::i64 S = p.io.S;\n";
-  for (int b = 0; b < p.n_out / 8; ++b)
-    os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
   os << "#define O(b, t, v) if (keep) *reinterpret_cast<xk::u32*>(ob##b + (t) * S) = (v)\n";
   std::vector<int> loaded(nc, -1);
   std::vector<std::vector<int>> outs_of(q.n_var);
@@ -176,7 +170,57 @@ std::string gen_window_body(const xorec::Program& p, int threads) {
   os << "    v.end(q0 + " << (n_phases - 1) << ");\n";
   for (int r = 0; r < static_cast<int>(q.ret.size()); ++r)
     if (q.ret[r] < 0) os << "    O(" << (r >> 3) << ", " << (r & 7) << ", 0u);\n";
-  os << "#undef I\n#undef O\n    return true;\n  }\n};\n";
+  os << "#undef I\n#undef O\n";
+}
+
+// Windowed single-launch body (run_window_pipeline).
+std::string gen_window_body(const xorec::Program& p, int threads) {
+  std::ostringstream os;
+  os << "struct SlpBody {\n"
+        "  __device__ __forceinline__ bool compute(const xk::LaunchParams& p, const xk::WindowView& v,\n"
+        "      xk::i64 q0, xk::i64 s, xk::i64 c0, int len, int col) const {\n"
+        "    const bool keep = col < len;\n"
+        "    const xk::i64 S = p.io.S;\n";
+  for (int b = 0; b < p.n_out / 8; ++b)
+    os << "    xk::u8* ob" << b << " = xk::out_block(p.io, s, " << b << ") + c0 + col;\n";
+  emit_window_statements(os, p, threads);
+  os << "    return true;\n  }\n};\n";
+  return os.str();
+}
+
+// Windowed multi-program module (run_batch_window_pipeline): every program
+// has one group of rows and the same windows.
+std::string gen_window_module_source(const std::vector<const xorec::Program*>& progs, int threads,
+                                     int minb) {
+  std::ostringstream os;
+  os << kPipelineSrc << "\n" << kOpaqueXorSrc;
+  for (size_t i = 0; i < progs.size(); ++i) {
+    os << "__device__ __forceinline__ bool prog_" << i
+       << "(const xk::StripeDesc& d, const xk::WindowView& v, xk::i64 q0, xk::i64 c0, int col,\n"
+          "    bool keep) {\n"
+          "    const xk::i64 S = d.S;\n";
+    for (int b = 0; b < progs[i]->n_out / 8; ++b)
+      os << "    xk::u8* ob" << b << " = reinterpret_cast<xk::u8*>(d.blocks[d.n_inblk + " << b
+         << "]) + c0 + col;\n";
+    emit_window_statements(os, *progs[i], threads);
+    os << "    return true;\n}\n";
+  }
+  os << "struct ModBody {\n"
+        "  __device__ __forceinline__ bool compute(const xk::StripeDesc& d, const xk::WindowView& v,\n"
+        "      xk::i64 q0, xk::i64 c0, int len, int col) const {\n"
+        "    const bool keep = col < len;\n"
+        "    switch (d.prog) {\n";
+  for (size_t i = 0; i < progs.size(); ++i)
+    os << "      case " << i << ": return prog_" << i << "(d, v, q0, c0, col, keep);\n";
+  os << "      default: return false;\n"
+        "    }\n"
+        "  }\n"
+        "};\n";
+  os << "extern \"C\" __global__ void __launch_bounds__(" << threads + 32 << ", " << minb
+     << ") xorec_mod(xk::BatchParams p) {\n"
+        "  extern __shared__ __align__(128) xk::u8 smem[];\n"
+        "  xk::run_batch_window_pipeline(p, smem, ModBody());\n"
+        "}\n";
   return os.str();
 }
 
@@ -408,6 +452,32 @@ bool windowed(const Program& p) {
   return force == 1 || (n_phases == n_win && p.n_in > 256);
 }
 
+// A module of these programs takes the batched windowed pipeline: every
+// program is windowed, with one group of rows (one phase per window), and
+// all have the same windows.
+bool window_module(const std::vector<const Program*>& progs, int* win, int* n_win) {
+  int w0 = -1, nw0 = -1;
+  for (const Program* p : progs) {
+    int w, nw, np;
+    if (!windowed(*p) || !window_layout(*p, &w, &nw, &np, nullptr) || np != nw) return false;
+    if (w0 >= 0 && (w != w0 || nw != nw0)) return false;
+    w0 = w;
+    nw0 = nw;
+  }
+  if (w0 < 0) return false;
+  *win = w0;
+  *n_win = nw0;
+  return true;
+}
+
+bool jit_module_window(void* mod, int* win, int* n_win) {
+  auto* jk = static_cast<JitKernel*>(mod);
+  if (!jk || jk->win <= 0) return false;
+  *win = jk->win;
+  *n_win = jk->n_win;
+  return true;
+}
+
 bool jit_available() {
   int major = 0, minor = 0;
   return nvrtcVersion(&major, &minor) == NVRTC_SUCCESS;
@@ -548,6 +618,21 @@ void* jit_compile_module(const std::vector<const Program*>& progs, int threads, 
     *err = "empty module";
     return nullptr;
   }
+  // modules of windowed programs take the batched windowed pipeline, built
+  // for three CTAs per SM, or two when ptxas spills at three
+  int win = 0, n_win = 0;
+  if (window_module(progs, &win, &n_win)) {
+    for (int mb = minb_for(threads + 32, 128);; --mb) {
+      long spill = 0;
+      JitKernel* jk = compile_and_load(gen_window_module_source(progs, threads, mb), "xorec_mod",
+                                       threads, err, &spill, threads + 32);
+      if (!jk) return nullptr;
+      jk->win = win;
+      jk->n_win = n_win;
+      if (spill == 0 || mb <= 2) return jk;
+      jit_release_kernel(jk);
+    }
+  }
   for (;;) {
     long spill = 0;
     JitKernel* jk = compile_and_load(gen_module_source(progs, threads, minb), "xorec_mod", threads,
@@ -559,7 +644,11 @@ void* jit_compile_module(const std::vector<const Program*>& progs, int threads, 
 }
 
 std::string jit_module_source(const std::vector<const Program*>& progs, int threads, int minb) {
-  return progs.empty() ? std::string() : gen_module_source(progs, threads, minb);
+  if (progs.empty()) return std::string();
+  int win = 0, n_win = 0;
+  if (window_module(progs, &win, &n_win))
+    return gen_window_module_source(progs, threads, minb_for(threads + 32, 128));
+  return gen_module_source(progs, threads, minb);
 }
 
 int jit_module_ctas_per_sm(void* mod, size_t smem) {
@@ -567,7 +656,7 @@ int jit_module_ctas_per_sm(void* mod, size_t smem) {
   if (!jk || !jit_set_smem(jk, smem)) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, reinterpret_cast<const void*>(jk->kern),
-                                                    jk->threads, smem) != cudaSuccess) {
+                                                    jk->block, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -582,9 +671,11 @@ bool jit_module_launch(void* mod, const xk::BatchParams& bp, int grid, size_t sm
     return false;
   }
   xk::BatchParams copy = bp;
+  copy.win = jk->win;
+  copy.n_win = jk->n_win;
   void* args[] = {&copy};
   const cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(jk->kern), dim3(grid),
-                                         dim3(jk->threads), args, smem, stream);
+                                         dim3(jk->block), args, smem, stream);
   if (e != cudaSuccess) {
     set_error(std::string("compiled module launch failed: ") + cudaGetErrorString(e));
     return false;

@@ -103,6 +103,10 @@ struct BatchParams {
   int range_rem;           // n_items % n_ranges
   i64 range_len;           // n_items / n_ranges
   int* local_status;       // the batch's or serving slot's own status word, or null
+  // windowed modules (run_batch_window_pipeline): input strips per window,
+  // windows per item (= phases: the programs have one group of rows); 0
+  // otherwise
+  int win, n_win;
 };
 
 // Shared-memory header of batched launches: the mbarrier (bytes 0..7), the
@@ -722,6 +726,140 @@ __device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* sme
       issue_next();
       prepare_after();
     }
+  }
+}
+
+// Batched form of the windowed pipeline, for modules of single-group
+// windowed programs (one phase per window).  Warp 0 pops items from the work
+// queue (chunks of consecutive items; one queue) and, per item and window,
+// waits for a free slot, copies the window (one 2-D tensor copy per input
+// block of the window, or one 1-D copy per strip) and, in the item's first
+// slot, leaves the item's index for the consumers; a last slot holding -1
+// ends the launch.  The consumers take the item from its first slot and run
+// its program window by window.
+// Shared memory: [full barriers (0)][empty barriers (64)][slot items (96)],
+// then the ring from byte 128.
+// Body (windowed modules):
+//   bool compute(const StripeDesc&, const WindowView&, i64 q0, i64 c0, int len,
+//                int col) const
+__device__ __forceinline__ void issue_batch_window(const BatchParams& p, const StripeDesc* d,
+                                                   i64 c0, int len, int w, u8* dst, u32 bar) {
+  const int lane = threadIdx.x & 31;
+  const int n_in = 8 * d->n_inblk;
+  const int y0 = w * p.win;
+  const int n = n_in - y0 < p.win ? n_in - y0 : p.win;
+  if (d->maps) {
+    // one box of a block's 8 strips per block; past the end of the strips it
+    // is zero-filled and counts in full
+    const int b0 = y0 >> 3, nb = n >> 3;
+    if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(n) * static_cast<u32>(p.T));
+    __syncwarp();
+    for (int j = lane; j < nb; j += 32)
+      tma_load_2d(smem_addr(dst + static_cast<i64>(8 * j) * p.T), d->maps + b0 + j,
+                  static_cast<int>(c0 >> 2), 0, bar);
+    return;
+  }
+  if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(n) * static_cast<u32>(len));
+  __syncwarp();
+  for (int c = lane; c < n; c += 32) {
+    const int strip = y0 + c;
+    const u8* src = reinterpret_cast<const u8*>(d->blocks[strip >> 3]) +
+                    static_cast<i64>(strip & 7) * d->S + c0;
+    tma_load_1d(smem_addr(dst + static_cast<i64>(c) * p.T), src, static_cast<u32>(len), bar);
+  }
+}
+
+template <class Body>
+__device__ __forceinline__ void run_batch_window_pipeline(const BatchParams& p, u8* smem,
+                                                          const Body& body) {
+  u64* full = reinterpret_cast<u64*>(smem);
+  u64* empty = reinterpret_cast<u64*>(smem + 64);
+  volatile i64* slot_item = reinterpret_cast<volatile i64*>(smem + 96);
+  const int tid = threadIdx.x;
+  const int n_cons = static_cast<int>(blockDim.x) - 32;
+  WindowView v;
+  v.ring = smem + 128;
+  v.full0 = smem_addr(full);
+  v.empty0 = smem_addr(empty);
+  v.slot_bytes = static_cast<i64>(p.win) * p.T;
+  if (tid == 0) {
+    for (int r = 0; r < kWinRing; ++r) {
+      mbar_init(smem_addr(&full[r]), 1);
+      mbar_init(smem_addr(&empty[r]), static_cast<u32>(n_cons));
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid < 32) {
+    // producer: a fresh empty barrier counts its phase before phase 0 as
+    // complete, so the first round of slots needs no release
+    QueueState qs;
+    qs.q_pos = qs.q_end = 0;
+    qs.cur_r = 0;
+    qs.home = 0;
+    qs.prep_cur = 0;
+    qs.pad_ = 0;
+    int cursor = 0;
+    i64 q = 0;
+    bool ok = true;
+    for (bool done = false; ok && !done;) {
+      const i64 item = batch_pop(p, qs);
+      const StripeDesc* d = nullptr;
+      i64 c0 = 0;
+      int len = 0;
+      if (item >= 0) batch_item_geom(p, item, cursor, d, c0, len);
+      const int phases = item >= 0 ? p.n_win : 1;
+      for (int ph = 0; ph < phases; ++ph, ++q) {
+        const int slot = static_cast<int>(q % kWinRing);
+        if (tid == 0)
+          ok = mbar_wait(smem_addr(&empty[slot]), static_cast<u32>(((q / kWinRing) & 1) ^ 1));
+        ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+        if (!ok) break;
+        if (ph == 0 && tid == 0) slot_item[slot] = item;
+        if (item < 0) {
+          // the end: an arrival without copies completes the slot's phase
+          if (tid == 0)
+            asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }"
+                         ::"r"(smem_addr(&full[slot])) : "memory");
+          done = true;
+          break;
+        }
+        if (tid == 0) fence_proxy_async();
+        __syncwarp();
+        issue_batch_window(p, d, c0, len, ph, v.ring + slot * v.slot_bytes, smem_addr(&full[slot]));
+      }
+    }
+    if (!ok && tid == 0) {
+      // a release never came: record it and let the copies in flight land
+      // (bounded) before the CTA ends
+      atomicExch(p.status, XK_STATUS_TIMEOUT);
+      if (p.local_status) *reinterpret_cast<volatile int*>(p.local_status) = XK_STATUS_TIMEOUT;
+      for (i64 x = q - kWinRing; x < q; ++x)
+        if (x >= 0) mbar_wait(smem_addr(&full[x % kWinRing]), static_cast<u32>((x / kWinRing) & 1));
+    }
+    return;
+  }
+  const int col = (tid - 32) * 4;
+  int cursor = 0;
+  for (i64 q0 = 0;;) {
+    const int slot = static_cast<int>(q0 % kWinRing);
+    if (!mbar_wait(v.full0 + 8u * slot, static_cast<u32>((q0 / kWinRing) & 1))) {
+      atomicExch(p.status, XK_STATUS_TIMEOUT);
+      if (p.local_status) *reinterpret_cast<volatile int*>(p.local_status) = XK_STATUS_TIMEOUT;
+      return;
+    }
+    const i64 item = slot_item[slot];
+    if (item < 0) return;
+    const StripeDesc* d;
+    i64 c0;
+    int len;
+    batch_item_geom(p, item, cursor, d, c0, len);
+    if (!body.compute(*d, v, q0, c0, len, col)) {
+      atomicExch(p.status, XK_STATUS_TIMEOUT);
+      if (p.local_status) *reinterpret_cast<volatile int*>(p.local_status) = XK_STATUS_TIMEOUT;
+      return;
+    }
+    q0 += p.n_win;
   }
 }
 

@@ -144,3 +144,54 @@ def test_batch_of_a_very_wide_code():
     finally:
         xo.ec_plan_destroy(plan)
     assert xo.ec_device_status() == 0
+
+
+@pytest.mark.parametrize("tensor_copies", ["1", "0"], ids=["tensor-copies", "strip-copies"])
+def test_windowed_batch_decodes(tensor_copies, monkeypatch):
+    """Batches of wide decoders run as windowed modules (a producer warp pops
+    items and streams their windows; the first slot of an item carries its
+    index; a last slot ends the launch), beside a narrow code in the same
+    batch; one 2-D tensor copy per input block of a window, or one 1-D copy
+    per strip.  Bit-exact against the codewords, including a ragged tile."""
+    monkeypatch.setenv("EC_WINDOWED", "1")
+    monkeypatch.setenv("EC_TMA_TENSOR", tensor_copies)
+    torch.cuda.set_device(0)
+    codes = [(13, 4), (48, 4), (10, 4)]
+    plans = {c: xo.ec_plan_create(*c) for c in codes}
+    try:
+        rng = np.random.default_rng(101)
+        jobs, outs, want, keep = [], [], [], []
+        for s in range(12):
+            k, m = codes[s % 3]
+            B = int(rng.choice([8 * 528, 8 * 2064, 4096]))
+            P = oracle.cauchy(k, m)
+            data = [synth.block_bytes(102, s, j, B) for j in range(k)]
+            blocks = data + oracle.encode(P, data)
+            d = [torch.from_numpy(x).cuda() for x in blocks]
+            keep += d
+            ne = int(rng.integers(1, m + 1))
+            er = [int(x) for x in rng.choice(k + m, size=ne, replace=False)]
+            o = [torch.full((B,), 0x66, dtype=torch.uint8, device="cuda") for _ in er]
+            jobs.append({"plan": plans[(k, m)], "op": xo.EC_OP_DECODE, "erasures": er,
+                         "blocks": [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                         "out": [t.data_ptr() for t in o], "block_bytes": B})
+            outs += o
+            want += [blocks[e] for e in er]
+        b = xo.ec_batch_create(jobs, xo.EC_EXEC_COMPILED)
+        try:
+            src = xo.ec_plan_module_source(plans[(48, 4)], [[0, 1]])
+            assert "xk::run_batch_window_pipeline(p, smem, ModBody())" in src
+            for _ in range(2):
+                for t in outs:
+                    t.fill_(0x66)
+                xo.ec_batch_run(b, stream())
+                torch.cuda.synchronize()
+                for t, w in zip(outs, want):
+                    assert np.array_equal(t.cpu().numpy(), w)
+            assert xo.ec_batch_status(b) == 0
+        finally:
+            xo.ec_batch_destroy(b)
+    finally:
+        for h in plans.values():
+            xo.ec_plan_destroy(h)
+    assert xo.ec_device_status() == 0

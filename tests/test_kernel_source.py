@@ -246,3 +246,23 @@ def test_batch_module_compiles_without_spills(k, m, shape):
         check_no_spill(xo.ec_plan_module_source(plan))   # the encoder alone
     finally:
         xo.ec_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("k,m", [(48, 4), (100, 4)])
+def test_windowed_module_compiles_without_spills(k, m):
+    """A batch module of wide single-group decoders (more than 256 input
+    strips) takes the batched windowed pipeline: a producer warp beside the
+    128 threads that own a column, a ring of windows instead of a stage of
+    every strip; it compiles for sm_103a without spills."""
+    import itertools
+    import random
+    plan = xo.ec_plan_create(k, m)
+    try:
+        pats = [c for e in range(1, m + 1) for c in itertools.combinations(range(k + m), e)]
+        sets = [list(c) for c in random.Random(k).sample(pats, 8)]
+        src = xo.ec_plan_module_source(plan, sets)
+        assert "xk::run_batch_window_pipeline(p, smem, ModBody())" in src
+        assert "__launch_bounds__(160, 3)" in src
+        check_no_spill(src)
+    finally:
+        xo.ec_plan_destroy(plan)
