@@ -6,7 +6,8 @@ oracle with the pipeline forced on (EC_WINDOWED=1) for codes it would not
 take by default, and at its default for the widest ones: tensor copies with
 a partial last window (RS(13,4): 104 strips), two groups of rows (RS(24,8)),
 per-strip copies from block pointer tables, ragged strip tails, decoders,
-and a code whose kernel is recompiled for two CTAs per SM (RS(100,4))."""
+the widest code of the benchmark (RS(100,4)), batched decodes as windowed
+modules, and the serving loop running those modules."""
 import numpy as np
 import pytest
 
@@ -194,4 +195,50 @@ def test_windowed_batch_decodes(tensor_copies, monkeypatch):
     finally:
         for h in plans.values():
             xo.ec_plan_destroy(h)
+    assert xo.ec_device_status() == 0
+
+
+def test_server_runs_windowed_modules():
+    """Requests of a wide code through the serving loop: after ec_server_warm
+    its programs run as windowed modules (the server's batches use the same
+    batched windowed pipeline); every request bit-exact and successful."""
+    import time
+    torch.cuda.set_device(0)
+    k, m, B = 48, 4, 8 * 2064
+    plan = xo.ec_plan_create(k, m)
+    sv = xo.ec_server_create(slots=2, max_batch=8, background_compile=False)
+    try:
+        xo.ec_server_warm(sv, plan, 2)
+        assert "xk::run_batch_window_pipeline(p, smem, ModBody())" in \
+            xo.ec_plan_module_source(plan, [[3, 50]])
+        P = oracle.cauchy(k, m)
+        data = [synth.block_bytes(103, 0, j, B) for j in range(k)]
+        blocks = data + oracle.encode(P, data)
+        d = [torch.from_numpy(x).cuda() for x in blocks]
+        reqs = []
+        for er in (None, [3, 50], [0], [k, k + 1]):
+            if er is None:
+                o = [torch.zeros(B, dtype=torch.uint8, device="cuda") for _ in range(m)]
+                job = {"plan": plan, "op": xo.EC_OP_ENCODE, "blocks": [t.data_ptr() for t in d[:k]],
+                       "out": [t.data_ptr() for t in o], "block_bytes": B}
+                want = blocks[k:]
+            else:
+                o = [torch.zeros(B, dtype=torch.uint8, device="cuda") for _ in er]
+                job = {"plan": plan, "op": xo.EC_OP_DECODE, "erasures": er,
+                       "blocks": [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                       "out": [t.data_ptr() for t in o], "block_bytes": B}
+                want = [blocks[e] for e in er]
+            reqs.append((xo.ec_server_submit(sv, job), o, want))
+        got, t0 = {}, time.time()
+        while len(got) < len(reqs) and time.time() - t0 < 30:
+            for tk, _, st in xo.ec_server_poll_ex(sv):
+                got[tk] = st
+            time.sleep(0.001)
+        for tk, o, want in reqs:
+            assert got.get(tk) == xo.EC_OK, tk
+            for t, w in zip(o, want):
+                assert np.array_equal(t.cpu().numpy(), w)
+    finally:
+        xo.ec_server_destroy(sv)
+        xo.ec_plan_destroy(plan)
     assert xo.ec_device_status() == 0
