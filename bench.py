@@ -1,7 +1,7 @@
 """Benchmark: RS(10,4) Cauchy encode over 256 stripes x 10 x 1 MiB on one GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload encode|batched|served|codes] [--executor auto|interp|compiled]
+                [--workload encode|batched|served|codes] [--executor auto|interp|compiled|dense]
 
 One step = one pass of the hot path over one batch: a single
 ec_encode_strided() launch over the 256 stripes (2.5 GiB in, 1 GiB out;
@@ -71,7 +71,7 @@ def parse_args():
                     help="scheduler polling window before it sleeps (0 = library default "
                          "1000 us, -1 = sleep at once)")
     ap.add_argument("--batched-stripes", type=int, default=8192)
-    ap.add_argument("--executor", default="auto", choices=["auto", "interp", "compiled"])
+    ap.add_argument("--executor", default="auto", choices=["auto", "interp", "compiled", "dense"])
     ap.add_argument("--opt", default="xorrepair", choices=["raw", "repair", "xorrepair", "triple"],
                     help="optimiser level of the encoding program")
     ap.add_argument("--max-temps", type=int, default=-2,
@@ -256,6 +256,7 @@ def cpu_baseline_obj():
 KERNEL_SOURCES = {
     "compiled": ("tile_pipeline.cuh", "jit.cc", "slp.cc", "plan.cc"),
     "interp": ("tile_pipeline.cuh", "executor.cu", "slp.cc", "plan.cc"),
+    "dense": ("tile_pipeline.cuh", "executor.cu", "plan.cc"),
 }
 
 
@@ -310,7 +311,7 @@ def run_ours(args):
             dist.barrier()
 
     executor = {"auto": xo.EC_EXEC_AUTO, "interp": xo.EC_EXEC_INTERP,
-                "compiled": xo.EC_EXEC_COMPILED}[args.executor]
+                "compiled": xo.EC_EXEC_COMPILED, "dense": xo.EC_EXEC_DENSE}[args.executor]
     k, m, B, n = K_DATA, M_PAR, BLOCK, args.stripes
     S = B // 8
     stream = torch.cuda.Stream()
@@ -326,7 +327,7 @@ def run_ours(args):
             xo.ec_synth_fill(data[s, j].data_ptr(), B, synth.block_seed(ENCODE_WORKLOAD_ID, s, j), 0, sp)
     stream.synchronize()
     tune = None
-    if not args.no_tune and executor != xo.EC_EXEC_INTERP and args.max_temps == -2 and args.opt == "xorrepair":
+    if not args.no_tune and executor in (xo.EC_EXEC_AUTO, xo.EC_EXEC_COMPILED) and args.max_temps == -2 and args.opt == "xorrepair":
         tune = xo.ec_plan_autotune(plan, B, 32, sp)
 
     def step(st):
@@ -391,7 +392,10 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     mean_launch_ms = statistics.mean(launch_ms)
     achieved = moved / (mean_launch_ms / 1e3) / 1e9
-    kind = "compiled" if info["compiled"] else "interp"
+    if args.executor in ("interp", "dense"):
+        kind = args.executor
+    else:
+        kind = "compiled" if info["compiled"] else "dense"
 
     e2e = None
     if not args.no_e2e and n == N_STRIPES:

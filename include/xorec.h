@@ -88,11 +88,16 @@ enum {
 /* Pebble-game scheduler (Sec. 6.6). */
 enum { EC_SCHED_DFS = 0, EC_SCHED_GREEDY = 1 };
 
-/* Executor tier. */
+/* Executor tier.  Without a compiled kernel (none yet, no run-time
+ * compiler, or a program too large for one) EC_EXEC_AUTO runs the dense
+ * bitmatrix executor: output strip r = XOR of the input strips c whose bit
+ * (r, c) of the program's bitmatrix is set (Sec. 1, property (ii)), built
+ * into the library. */
 enum {
-  EC_EXEC_AUTO = 0,     /* compiled straight-line kernel when available       */
-  EC_EXEC_INTERP = 1,   /* instruction-stream interpreter                     */
-  EC_EXEC_COMPILED = 2  /* compiled straight-line kernel (NVRTC)              */
+  EC_EXEC_AUTO = 0,     /* compiled straight-line kernel, else dense          */
+  EC_EXEC_INTERP = 1,   /* instruction-stream interpreter of the SLP          */
+  EC_EXEC_COMPILED = 2, /* compiled straight-line kernel (NVRTC)              */
+  EC_EXEC_DENSE = 3     /* dense bitmatrix executor                           */
 };
 
 typedef struct {

@@ -37,6 +37,7 @@ EC_SCHED_GREEDY = _abi.EC_SCHED_GREEDY
 EC_EXEC_AUTO = _abi.EC_EXEC_AUTO
 EC_EXEC_INTERP = _abi.EC_EXEC_INTERP
 EC_EXEC_COMPILED = _abi.EC_EXEC_COMPILED
+EC_EXEC_DENSE = _abi.EC_EXEC_DENSE
 
 
 class XorecError(RuntimeError):

@@ -32,7 +32,7 @@ EC_ENOTSUP = -8
 EC_MATRIX_CAUCHY, EC_MATRIX_POWER, EC_MATRIX_USER, EC_MATRIX_CAUCHY_MIN = 0, 1, 2, 3
 EC_OPT_RAW, EC_OPT_REPAIR, EC_OPT_XORREPAIR, EC_OPT_TRIPLE = 0, 1, 2, 3
 EC_SCHED_DFS, EC_SCHED_GREEDY = 0, 1
-EC_EXEC_AUTO, EC_EXEC_INTERP, EC_EXEC_COMPILED = 0, 1, 2
+EC_EXEC_AUTO, EC_EXEC_INTERP, EC_EXEC_COMPILED, EC_EXEC_DENSE = 0, 1, 2, 3
 
 
 class PlanOpts(ctypes.Structure):

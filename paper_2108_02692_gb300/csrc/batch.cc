@@ -5,11 +5,12 @@
 // parallel host threads, Sec. 1 inversion + Sec. 4-6 optimisation), compiles
 // the ones without a compiled form into multi-program modules (one module
 // per plan and input width, NVRTC, in parallel), and lays out in device
-// memory one descriptor per stripe (work items are 512-byte tiles of every
-// strip of a stripe, numbered stripe after stripe).  ec_batch_run then only launches: one
-// persistent launch per module plus one interpreter launch for programs
-// left to the interpreter; it allocates nothing and can be captured in a
-// CUDA graph.  Items are ordered stripe by stripe, largest stripes first
+// memory one descriptor per stripe (work items are tiles of every strip of
+// a stripe, numbered stripe after stripe).  ec_batch_run then only
+// launches: one persistent launch per module plus one launch of the dense
+// bitmatrix executor (the interpreter in batches created with
+// EC_EXEC_INTERP) for programs without a module; it allocates nothing and
+// can be captured in a CUDA graph.  Items are ordered stripe by stripe, largest stripes first
 // inside each launch, and CTAs take them round robin.
 #include <cuda_runtime.h>
 
@@ -50,8 +51,11 @@ int batch_minb_for(int n_in) {
 }
 
 struct Launch {
-  void* mod = nullptr;                 // compiled module, or nullptr = interpreter
-  int threads = 128;                   // threads per CTA; tiles of 4 x threads bytes
+  void* mod = nullptr;                 // compiled module, or nullptr: the dense
+                                       // executor (the interpreter if `interp`)
+  bool interp = false;
+  int threads = 128;                   // threads per CTA that own a column
+  int T = 512;                         // tile bytes per strip
   int stripe_begin = 0, n_stripes = 0; // the launch's stripes in the descriptor array
   long long n_items = 0;
   int max_in = 0, max_slots = 0;
@@ -207,9 +211,26 @@ int plan_module_minb(const ec_plan* p, int n_in) {
   return std::max(1, std::min(p->tuned_minb, 65536 / (p->tuned_threads * floor_cap)));
 }
 
-// Threads per CTA of the launch that runs `prog`: its module's, or the
-// interpreter's default.
-int launch_threads(void* mod) { return mod ? jit_module_threads(mod) : batch_threads(); }
+// Threads per CTA that own a column in a batched launch of `mod`: the
+// module's, or (no module) the dense executor's.
+int launch_threads(void* mod) { return mod ? jit_module_threads(mod) : kDenseThreads; }
+
+// Tile bytes per strip of a batched launch: 4 x threads for modules and the
+// interpreter (interp: a batch created with EC_EXEC_INTERP), the dense
+// executor's words per thread otherwise.
+int launch_tile(void* mod, bool interp, int threads) {
+  return mod || interp ? 4 * threads : 4 * dense_words() * kDenseThreads;
+}
+
+// One batched launch on its target.
+bool batch_launch(void* mod, bool interp, const xk::BatchParams& bp, int threads, int grid,
+                  size_t smem, cudaStream_t st) {
+  if (mod) return jit_module_launch(mod, bp, grid, smem, st);
+  if (interp) return launch_interp_batch(bp, threads, grid, smem, st);
+  xk::BatchParams dp = bp;
+  dp.win = kDenseWin;
+  return launch_dense_batch(dp, dense_words(), grid, smem, st);
+}
 
 // A program of one group of rows that the windowed pipeline runs (its
 // modules hold a ring of windows, not a stage of every input strip).
@@ -219,11 +240,11 @@ static bool window_program(const Program* p) {
 }
 
 // Threads that own a column in the module that runs `prog`: the plan's
-// tuned shape, else 128 for windowed programs and the default module shape
-// otherwise.
+// tuned shape, else window_threads(true) for windowed programs and the default
+// module shape otherwise.
 int module_threads(const ec_plan* plan, const Program* prog) {
   if (plan->tuned_threads > 0) return plan->tuned_threads;
-  return window_program(prog) ? 128 : plan_module_threads(plan, prog->n_in);
+  return window_program(prog) ? window_threads(true) : plan_module_threads(plan, prog->n_in);
 }
 
 // Such a module fits one CTA: a ring of windows (windowed programs) or a
@@ -254,7 +275,7 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
   std::vector<Program*> seen;
   for (const auto& w : want) {
     const int threads = module_threads(w.first, w.second);
-    if (!module_fits(w.second, threads, di.smem_optin)) continue;   // interpreter
+    if (!module_fits(w.second, threads, di.smem_optin)) continue;   // dense executor
     std::lock_guard<std::mutex> lk(w.first->mu);
     if ((w.second->mod && jit_module_threads(w.second->mod) == threads) ||
         std::find(seen.begin(), seen.end(), w.second) != seen.end())
@@ -293,7 +314,7 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
         for (size_t j = i; j < mods.size(); ++j) jit_module_release(mods[j]);
         return fail(EC_ECUDA, "module compile failed: " + errs[i]);
       }
-      continue;   // these programs stay with the interpreter
+      continue;   // these programs stay with the dense executor
     }
     plan->modules.push_back(mods[i]);
     for (size_t j = 0; j < to_compile[i].second.size(); ++j) {
@@ -304,11 +325,19 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
   return EC_OK;
 }
 
-// Shared memory and resident CTAs per SM of a batched launch (module or
-// interpreter).
-bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
-                        size_t* smem, int* per_sm) {
+// Shared memory and resident CTAs per SM of a batched launch (module, dense
+// executor, or interpreter).
+bool batch_launch_shape(void* mod, bool interp, int max_in, int max_slots, int threads,
+                        size_t smem_optin, size_t* smem, int* per_sm) {
   const int T = 4 * threads;
+  if (!mod && !interp) {
+    // the dense executor: a ring of windows of kDenseWin strips
+    const int W = dense_words();
+    *smem = dense_smem_bytes(4 * W * kDenseThreads);
+    if (*smem > smem_optin) return false;
+    *per_sm = std::max(1, dense_max_ctas_per_sm(W, true, *smem));
+    return true;
+  }
   int win = 0, n_win = 0;
   if (mod && jit_module_window(mod, &win, &n_win)) {
     *smem = 128 + static_cast<size_t>(xk::kWinRing) * win * T;
@@ -341,11 +370,12 @@ void set_ranges(xk::BatchParams* bp, long long n_items, int n_ranges) {
 // (256 B of each of hundreds of strips): with a single queue all CTAs read
 // neighbouring tiles, which keeps DRAM rows open (RS(100,4) decode: 0.39 of
 // the copy bandwidth with one queue, 0.20 with per-SM ranges).
-// EC_BATCH_RANGES overrides (1 = a single queue).
-int batch_ranges(long long n_items, int sms, int per_sm, int chunk, int max_in) {
+// The dense executor's code is small and shared by every stripe: one
+// queue.  EC_BATCH_RANGES overrides (1 = a single queue).
+int batch_ranges(long long n_items, int sms, int per_sm, int chunk, int max_in, bool dense) {
   const int forced = env_int("EC_BATCH_RANGES", 0);
   if (forced > 0) return std::min(forced, std::max(1, sms));
-  if (max_in > kPreloadMaxInputs) return 1;
+  if (dense || max_in > kPreloadMaxInputs) return 1;
   const long long per_range = 4ll * std::max(1, per_sm) * std::max(1, chunk);
   return n_items >= per_range * sms ? std::max(1, sms) : 1;
 }
@@ -359,7 +389,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   if (!out) return fail(EC_EINVAL, "out is NULL");
   *out = nullptr;
   if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(EC_EINVAL, "bad job list");
-  if (executor < EC_EXEC_AUTO || executor > EC_EXEC_COMPILED) return fail(EC_EINVAL, "bad executor");
+  if (executor < EC_EXEC_AUTO || executor > EC_EXEC_DENSE) return fail(EC_EINVAL, "bad executor");
   const auto t0 = std::chrono::steady_clock::now();
   xorec::DeviceInfo di;
   if (!xorec::device_info(&di)) return EC_ECUDA;
@@ -400,7 +430,8 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   }
 
   // 3. tiers: compile programs without a module (per plan, per input width)
-  bool compiled = executor != EC_EXEC_INTERP && xorec::jit_available();
+  bool compiled =
+      (executor == EC_EXEC_AUTO || executor == EC_EXEC_COMPILED) && xorec::jit_available();
   if (executor == EC_EXEC_COMPILED && !compiled)
     return fail(EC_ENOTSUP, "no run-time compiler available");
   int modules_built = 0;
@@ -411,7 +442,8 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     if (cs != EC_OK) return cs;
   }
 
-  // 4. launches: one per module in use, one for the interpreter
+  // 4. launches: one per module in use, one for the dense executor (or the
+  // interpreter)
   auto b = new ec_batch();
   b->device = di.device;
   b->status = di.status;
@@ -425,7 +457,8 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       it = launch_of.emplace(mod, static_cast<int>(b->launches.size())).first;
       Launch L;
       L.mod = mod;
-      L.threads = xorec::launch_threads(mod);
+      L.interp = !mod && executor == EC_EXEC_INTERP;
+      L.threads = L.interp ? batch_threads() : xorec::launch_threads(mod);
       b->launches.push_back(L);
     }
     e.launch = it->second;
@@ -435,15 +468,17 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   }
   // the interpreter's tile shrinks (down to 32 threads, 128 bytes per strip)
   // until its stage of every input strip and its slots fit one CTA
-  for (auto& L : b->launches)
-    while (!L.mod && L.threads > 32 &&
+  for (auto& L : b->launches) {
+    while (L.interp && L.threads > 32 &&
            xorec::interp_batch_smem_bytes(L.max_in, L.max_slots, 4 * L.threads) > di.smem_optin)
       L.threads /= 2;
+    L.T = xorec::launch_tile(L.mod, L.interp, L.threads);
+  }
   for (auto& e : ents) {
     const Launch& L = b->launches[e.launch];
-    e.tiles = (e.S + 4 * L.threads - 1) / (4 * L.threads);
+    e.tiles = (e.S + L.T - 1) / L.T;
   }
-  // interpreter programs need their streams on the device
+  // programs without a module need their streams and masks on the device
   for (auto& e : ents)
     if (!(compiled && e.prog->mod) && !xorec::ensure_device_code(e.prog)) {
       free_batch(b);
@@ -489,8 +524,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     {
       bool ok = true;
       for (int j = 0; j < d.n_inblk && ok; ++j)
-        ok = xorec::block_tensor_map_allowed(reinterpret_cast<const void*>(e.ptrs[j]), e.S,
-                                             4 * L.threads);
+        ok = xorec::block_tensor_map_allowed(reinterpret_cast<const void*>(e.ptrs[j]), e.S, L.T);
       if (ok) {
         map_at[oi] = static_cast<long long>(maps.size());
         maps.resize(maps.size() + d.n_inblk);
@@ -521,7 +555,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
         current = di.device;
       }
       const Entry& e = ents[order[oi]];
-      const int T = 4 * b->launches[e.launch].threads;
+      const int T = b->launches[e.launch].T;
       for (int j = 0; j < descs[oi].n_inblk; ++j)
         if (!xorec::block_tensor_map(reinterpret_cast<const void*>(e.ptrs[j]), e.S, T,
                                      &maps[map_at[oi] + j]))
@@ -581,17 +615,18 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
   for (auto& L : b->launches) {
     int per_sm = 1;
     if (L.mod) ++n_modules;
-    if (!xorec::batch_launch_shape(L.mod, L.max_in, L.max_slots, L.threads, di.smem_optin, &L.smem,
-                                   &per_sm)) {
+    if (!xorec::batch_launch_shape(L.mod, L.interp, L.max_in, L.max_slots, L.threads,
+                                   di.smem_optin, &L.smem, &per_sm)) {
       free_batch(b);
       return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
     }
     const long long grid = static_cast<long long>(di.sms) * std::max(1, per_sm);
     L.grid = static_cast<int>(std::min<long long>(grid, std::max<long long>(1, L.n_items)));
-    L.n_ranges = xorec::batch_ranges(L.n_items, di.sms, per_sm, b->chunk, L.max_in);
+    L.n_ranges = xorec::batch_ranges(L.n_items, di.sms, per_sm, b->chunk, L.max_in,
+                                     !L.mod && !L.interp);
     if (env_int("XOREC_LOG", 0))
       std::fprintf(stderr, "[xorec] batch launch: %s items=%lld max_in=%d smem=%zu ctas/sm=%d grid=%d regs=%d ranges=%d\n",
-                   L.mod ? "module" : "interp", L.n_items, L.max_in, L.smem, per_sm, L.grid,
+                   L.mod ? "module" : L.interp ? "interp" : "dense", L.n_items, L.max_in, L.smem, per_sm, L.grid,
                    L.mod ? xorec::jit_module_regs(L.mod) : 0, L.n_ranges);
   }
   // largest launches first; lanes for concurrent launches
@@ -667,12 +702,11 @@ ec_status ec_batch_run(ec_batch* b, void* stream) {
     bp.queue = b->d_queues + li * b->queue_stride;
     xorec::set_ranges(&bp, L.n_items, L.n_ranges);
     bp.n_items = L.n_items;
-    bp.T = 4 * L.threads;
+    bp.T = L.T;
     bp.max_in = L.max_in;
     bp.status = b->status;
     bp.local_status = b->d_status;
-    const bool ok = L.mod ? xorec::jit_module_launch(L.mod, bp, L.grid, L.smem, st)
-                          : xorec::launch_interp_batch(bp, L.threads, L.grid, L.smem, st);
+    const bool ok = xorec::batch_launch(L.mod, L.interp, bp, L.threads, L.grid, L.smem, st);
     if (!ok) return EC_ECUDA;
   }
   if (fan) {

@@ -76,18 +76,23 @@ bool device_info(DeviceInfo* out) {
   return true;
 }
 
+// Device buffer of a program: its chunk stream (16-byte chunks), then the
+// dense executor's column masks.
 bool ensure_device_code(Program* p) {
   if (p->d_code) return true;
-  const size_t bytes = std::max<size_t>(8, p->chunks.size()) * sizeof(uint16_t);
+  const size_t code_bytes = p->chunks.size() * sizeof(uint16_t);
+  const size_t mask_bytes = p->masks.size() * sizeof(uint32_t);
+  const size_t bytes = std::max<size_t>(16, code_bytes + mask_bytes);
   uint16_t* d = nullptr;
   if (dev_malloc(&d, bytes) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc of the program failed");
     return false;
   }
-  if (!p->chunks.empty() &&
-      cudaMemcpy(d, p->chunks.data(), p->chunks.size() * sizeof(uint16_t),
-                 cudaMemcpyHostToDevice) != cudaSuccess) {
+  if ((code_bytes && cudaMemcpy(d, p->chunks.data(), code_bytes, cudaMemcpyHostToDevice) !=
+                         cudaSuccess) ||
+      (mask_bytes && cudaMemcpy(reinterpret_cast<uint8_t*>(d) + code_bytes, p->masks.data(),
+                                mask_bytes, cudaMemcpyHostToDevice) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(d);
     set_error("upload of the program failed");
@@ -129,7 +134,22 @@ int program_threads(const Program* p) {
   const int th = env_int("EC_JIT_THREADS", 0);
   if (th > 0) return th;
   // windowed programs keep a ring of a few windows, not a tile of every strip
-  return windowed(*p) ? 128 : tile_threads_for_inputs(p->n_in, 128);
+  return windowed(*p) ? window_threads(false) : tile_threads_for_inputs(p->n_in, 128);
+}
+
+// Consumer threads of a windowed kernel (one 4-byte column each; the
+// producer warp comes on top): a multiple of 32 from 64 to 512.  Single
+// launches take one CTA of 320 per SM, whose warps all run the same phase
+// of the program and so share its instruction-cache lines (encode, 128
+// stripes x 1 MiB, of measured HBM, 128 -> 320 threads: RS(48,4) 0.96 ->
+// 1.03, RS(100,4) 0.97 -> 1.02, RS(128,4) 0.43 -> 0.50).  Batch modules
+// keep three CTAs of 128: their CTAs pop items one by one, and wider CTAs
+// lost (RS(48,4) decode 1.00 -> 0.96, RS(100,4) 0.78 -> 0.73 at 320).
+// EC_WIN_THREADS and EC_WIN_MODULE_THREADS override.
+int window_threads(bool module) {
+  const int dflt = module ? 128 : 320;
+  const int th = env_int(module ? "EC_WIN_MODULE_THREADS" : "EC_WIN_THREADS", dflt);
+  return th >= 64 && th <= 512 && th % 32 == 0 ? th : dflt;
 }
 
 bool compiled_tier_fits(const Program* p, int threads, size_t smem_optin) {
@@ -211,7 +231,8 @@ int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out, 
   const uint64_t base = reinterpret_cast<uint64_t>(io.in_base);
   // strips equally spaced by S across the stripe's blocks; 16-byte rules
   if (n_in < 8 || n_in % 8 != 0 || n_in != 8 * io.n_inblk) return 0;
-  if (T % 16 != 0 || T / 4 < 4 || T / 4 > 256) return 0;
+  const int es = 1 << xk::tmap_elem_shift(T);    // element bytes
+  if (T % 16 != 0 || T / es < 4 || T / es > 256) return 0;
   if (S <= 0 || S % 16 != 0 || base % 16 != 0 || io.in_bstride != 8 * S) return 0;
   const long long plane = static_cast<long long>(n_in) * S;
   const long long sstride = io.n_stripes > 1 ? io.in_sstride : plane;
@@ -232,13 +253,14 @@ int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out, 
     if (box_rows % 8 != 0 || box_rows > 256) return 0;
     rows = box_rows;
   }
-  const cuuint64_t dim[3] = {static_cast<cuuint64_t>(S / 4), static_cast<cuuint64_t>(n_in),
+  const cuuint64_t dim[3] = {static_cast<cuuint64_t>(S / es), static_cast<cuuint64_t>(n_in),
                              static_cast<cuuint64_t>(io.n_stripes)};
   const cuuint64_t stride[2] = {static_cast<cuuint64_t>(S), static_cast<cuuint64_t>(sstride)};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(T / 4), static_cast<cuuint32_t>(rows), 1};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(T / es), static_cast<cuuint32_t>(rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r =
-      enc(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+      enc(reinterpret_cast<CUtensorMap*>(out),
+          es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
           const_cast<uint8_t*>(io.in_base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -249,19 +271,22 @@ bool block_tensor_map_allowed(const void* block, long long S, int T) {
   if (env_int("EC_TMA_TENSOR", 1) == 0) return false;
   const uint64_t base = reinterpret_cast<uint64_t>(block);
   if (!block || base % 16 != 0 || S <= 0 || S % 16 != 0 || S / 4 > 0xffffffffll) return false;
-  if (T % 16 != 0 || T / 4 < 4 || T / 4 > 256) return false;
+  const int es = 1 << xk::tmap_elem_shift(T);
+  if (T % 16 != 0 || T / es < 4 || T / es > 256) return false;
   return tensor_map_encoder() != nullptr;
 }
 
 bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out) {
   if (!block_tensor_map_allowed(block, S, T)) return false;
   const EncodeTiledFn enc = tensor_map_encoder();
-  const cuuint64_t dim[2] = {static_cast<cuuint64_t>(S / 4), 8};
+  const int es = 1 << xk::tmap_elem_shift(T);
+  const cuuint64_t dim[2] = {static_cast<cuuint64_t>(S / es), 8};
   const cuuint64_t stride[1] = {static_cast<cuuint64_t>(S)};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(T / 4), 8};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(T / es), 8};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r =
-      enc(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+      enc(reinterpret_cast<CUtensorMap*>(out),
+          es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
           const_cast<void*>(block), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -274,7 +299,7 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   if (io.n_stripes == 0 || io.S == 0) return true;
   bool compiled = false;
   int threads = 0, nstage = 0;
-  if (executor != EC_EXEC_INTERP) {
+  if (executor == EC_EXEC_AUTO || executor == EC_EXEC_COMPILED) {
     threads = program_threads(p);
     nstage = env_int("EC_JIT_NSTAGE", 1);
     std::string err = "program too large for the compiled tier";
@@ -314,7 +339,23 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
       per_sm = jit_max_ctas_per_sm(p, threads, smem);
     }
   }
-  if (!compiled) {
+  const bool dense = !compiled && executor != EC_EXEC_INTERP;
+  int dense_w = 0;
+  if (dense) {
+    // the dense bitmatrix executor: windows of one block stream through a
+    // ring; all output rows' accumulators in registers, in groups of 32
+    if (!ensure_device_code(p)) return false;
+    dense_w = dense_words();
+    lp.T = 4 * dense_w * kDenseThreads;
+    lp.win = kDenseWin;
+    lp.n_win = p->n_in / kDenseWin;
+    lp.n_phases = lp.n_win * ((p->n_out + 31) / 32);
+    lp.code = p->d_code;
+    lp.code_len = static_cast<int>(p->chunks.size() / 8);
+    nstage = 1;
+    smem = dense_smem_bytes(lp.T);
+    per_sm = dense_max_ctas_per_sm(dense_w, false, smem);
+  } else if (!compiled) {
     if (!ensure_device_code(p)) return false;
     // one stage (more resident CTAs hide more latency than a second stage
     // of the same CTA) and 8 bytes per thread and strip, halving per byte
@@ -351,6 +392,12 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, win ? lp.win : 0);
     return jit_launch(p, lp, lp.tmap ? &tm : nullptr, threads, static_cast<int>(grid), smem,
                       stream);
+  }
+  if (dense) {
+    xk::TensorMap tm;
+    lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, kDenseWin);
+    return launch_dense(lp, lp.tmap ? &tm : nullptr, dense_w, static_cast<int>(grid), smem,
+                        stream);
   }
   xk::TensorMap tm;
   lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, 0);
@@ -528,7 +575,7 @@ ec_status ec_plan_create_ex(int k, int m, int matrix_kind, const uint8_t* matrix
       return fail(EC_EINVAL, "bad opt_level");
     if (opts->sched != EC_SCHED_DFS && opts->sched != EC_SCHED_GREEDY)
       return fail(EC_EINVAL, "bad sched");
-    if (opts->executor < EC_EXEC_AUTO || opts->executor > EC_EXEC_COMPILED)
+    if (opts->executor < EC_EXEC_AUTO || opts->executor > EC_EXEC_DENSE)
       return fail(EC_EINVAL, "bad executor");
     plan->opts.opt_level = opts->opt_level;
     plan->opts.sched = opts->sched;
@@ -591,7 +638,7 @@ ec_status ec_plan_matrix(const ec_plan* plan, uint8_t* out) {
 
 ec_status ec_plan_set_executor(ec_plan* plan, int executor) {
   if (!plan) return fail(EC_EINVAL, "NULL plan");
-  if (executor < EC_EXEC_AUTO || executor > EC_EXEC_COMPILED) return fail(EC_EINVAL, "bad executor");
+  if (executor < EC_EXEC_AUTO || executor > EC_EXEC_DENSE) return fail(EC_EINVAL, "bad executor");
   if (executor == EC_EXEC_COMPILED && !xorec::jit_available())
     return fail(EC_ENOTSUP, "no run-time compiler available");
   plan->executor = executor;

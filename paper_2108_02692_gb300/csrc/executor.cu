@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -31,8 +32,11 @@ __device__ __forceinline__ Words<W> lds(u32 a) {
   Words<W> r;
   if constexpr (W == 1) {
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r.v[0]) : "r"(a));
-  } else {
+  } else if constexpr (W == 2) {
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.v[0]), "=r"(r.v[1]) : "r"(a));
+  } else {
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]) : "r"(a));
   }
   return r;
 }
@@ -50,8 +54,10 @@ template <int W>
 __device__ __forceinline__ void stg(u8* p, const Words<W>& x) {
   if constexpr (W == 1) {
     *reinterpret_cast<u32*>(p) = x.v[0];
-  } else {
+  } else if constexpr (W == 2) {
     *reinterpret_cast<uint2*>(p) = make_uint2(x.v[0], x.v[1]);
+  } else {
+    *reinterpret_cast<uint4*>(p) = make_uint4(x.v[0], x.v[1], x.v[2], x.v[3]);
   }
 }
 
@@ -188,6 +194,130 @@ __global__ void __launch_bounds__(256, 1) interp_batch_kernel(BatchParams p) {
   run_batch_pipeline(p, smem, InterpBatchBody(), slots);
 }
 
+// ------------------------------------------------ dense bitmatrix executor
+// Runs a program without a compiled kernel by evaluating its bitmatrix
+// (Sec. 1, property (ii): output strip r is the XOR of the input strips c
+// whose bit (r, c) is set), the linear map every SLP of the program
+// computes.  On the GPU this beats interpreting the optimised SLP: the
+// interpreter fetches, decodes and addresses every operand, while here the
+// control is one 32-bit column mask per input strip, uniform across the
+// CTA, and each set bit costs one XOR per word held in registers.
+//
+// The inputs stream through the windowed pipeline (tile_pipeline.cuh) in
+// windows of kDenseWin strips (one block); consumers own W 4-byte words of
+// every strip.  Output rows go in groups of up to 32: per group, every
+// window is read once (a group after the first reads them again, from L2)
+// and XORed into the group's accumulators under the mask bits; at the end of
+// the group each accumulator is written to its output strip.  The masks
+// follow the program's chunk stream in its device buffer: group g's mask of
+// input strip c is word g * n_in + c, bit r for output strip 32 g + r.
+using xorec::kDenseThreads;
+using xorec::kDenseWin;
+
+// One group of kRows output rows (rows <= kRows of them real): every window
+// of the item, then the stores.  q: the CTA's phase counter.
+template <int W, int kRows, class OutAddr>
+__device__ __forceinline__ bool dense_group(const WindowView& v, i64& q, int n_win, u32 T,
+                                            int col, bool store, const u32* __restrict__ masks,
+                                            int rows, const OutAddr& out) {
+  Words<W> acc[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[r].v[w] = 0;
+  for (int w = 0; w < n_win; ++w, ++q) {
+    const u8* slot = v.begin(q);
+    if (!slot) return false;
+    const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(masks + kDenseWin * w));
+    const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(masks + kDenseWin * w) + 1);
+    const u32 mk[kDenseWin] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+    const u32 a = smem_addr(slot) + static_cast<u32>(col);
+#pragma unroll
+    for (int c = 0; c < kDenseWin; ++c) {
+      const Words<W> x = lds<W>(a + static_cast<u32>(c) * T);
+#pragma unroll
+      for (int r = 0; r < kRows; ++r)
+        if ((mk[c] >> r) & 1u) xor_in(acc[r], x);
+    }
+    v.end(q);
+  }
+  if (store) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+      if (r < rows) stg<W>(out(r), acc[r]);
+  }
+  return true;
+}
+
+// All groups of one item.  n_in: input strips (a multiple of kDenseWin).
+template <int W, class OutAddr>
+__device__ __forceinline__ bool dense_item(const WindowView& v, i64 q0, int n_in, int n_out, u32 T,
+                                           int col, bool store, const u32* masks,
+                                           const OutAddr& out) {
+  i64 q = q0;
+  const int n_win = n_in / kDenseWin;
+  for (int g = 0; 32 * g < n_out; ++g) {
+    const int rows = n_out - 32 * g < 32 ? n_out - 32 * g : 32;
+    const u32* mg = masks + static_cast<i64>(g) * n_in;
+    auto og = [&](int r) { return out(32 * g + r); };
+    const bool ok = rows <= 8    ? dense_group<W, 8>(v, q, n_win, T, col, store, mg, rows, og)
+                    : rows <= 16 ? dense_group<W, 16>(v, q, n_win, T, col, store, mg, rows, og)
+                                 : dense_group<W, 32>(v, q, n_win, T, col, store, mg, rows, og);
+    if (!ok) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ int dense_groups(int n_out) { return (n_out + 31) / 32; }
+
+template <int W>
+struct DenseBody {
+  __device__ __forceinline__ bool compute(const LaunchParams& p, const WindowView& v, i64 q0,
+                                          i64 s, i64 c0, int len, int col) const {
+    const u32* masks = reinterpret_cast<const u32*>(p.code + 8 * static_cast<i64>(p.code_len));
+    auto out = [&](int r) {
+      return out_block(p.io, s, r >> 3) + static_cast<i64>(r & 7) * p.io.S + c0 + col;
+    };
+    return dense_item<W>(v, q0, p.n_in, p.n_out, static_cast<u32>(p.T), col, col < len, masks,
+                         out);
+  }
+};
+
+template <int W>
+struct DenseBatchBody {
+  u32 T;   // the launch's tile bytes per strip
+  __device__ __forceinline__ int groups(const StripeDesc& d) const {
+    return dense_groups(8 * d.n_outblk);
+  }
+  __device__ __forceinline__ bool compute(const StripeDesc& d, const WindowView& v, i64 q0, i64 c0,
+                                          int len, int col) const {
+    const u32* masks = reinterpret_cast<const u32*>(d.code + 8 * static_cast<i64>(d.code_len));
+    const u64* outs = d.blocks + d.n_inblk;
+    auto out = [&](int r) {
+      return reinterpret_cast<u8*>(outs[r >> 3]) + static_cast<i64>(r & 7) * d.S + c0 + col;
+    };
+    return dense_item<W>(v, q0, 8 * d.n_inblk, 8 * d.n_outblk, T, col, col < len, masks, out);
+  }
+};
+
+// Single launches and batches: kDenseThreads consumer threads and the
+// producer warp; the register cap of three CTAs per SM holds 32
+// accumulators of two words (121 registers), that of two CTAs 32 of four.
+template <int W>
+__global__ void __launch_bounds__(kDenseThreads + 32, W == 4 ? 2 : 3)
+    dense_kernel(LaunchParams p, const __grid_constant__ TensorMap tm) {
+  extern __shared__ __align__(128) u8 smem[];
+  run_window_pipeline<DenseBody<W>, 4 * W>(p, smem, DenseBody<W>(), &tm);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kDenseThreads + 32, W == 4 ? 2 : 3)
+    dense_batch_kernel(BatchParams p) {
+  extern __shared__ __align__(128) u8 smem[];
+  run_batch_window_pipeline<DenseBatchBody<W>, 4 * W, true>(
+      p, smem, DenseBatchBody<W>{static_cast<u32>(p.T)});
+}
+
 // Self-test of the bounded waits: one thread waits, with the pipeline's
 // mbar_wait, on an mbarrier whose phase nothing completes; the wait gives
 // up after its limit, the kernel records the timeout like the pipelines do
@@ -283,6 +413,90 @@ bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int thre
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("interpreter launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+// Dense bitmatrix executor: 128 consumer threads and the producer warp, W
+// words per consumer and strip (EC_DENSE_WORDS: 4 or 2).  Four words halve
+// the mask tests per byte: RS(10,4) encode, 256 stripes x 1 MiB, 0.265 of
+// the measured copy bandwidth with two words, 0.365 with four.
+int dense_words() {
+  const char* v = std::getenv("EC_DENSE_WORDS");
+  return v && *v && std::atoi(v) == 2 ? 2 : 4;
+}
+
+size_t dense_smem_bytes(int T) {
+  return 128 + static_cast<size_t>(xk::kWinRing) * kDenseWin * T;
+}
+
+static const void* dense_kernel_for(int W, bool batch) {
+  if (batch)
+    return W == 4 ? reinterpret_cast<const void*>(&dense_batch_kernel<4>)
+                  : reinterpret_cast<const void*>(&dense_batch_kernel<2>);
+  return W == 4 ? reinterpret_cast<const void*>(&dense_kernel<4>)
+                : reinterpret_cast<const void*>(&dense_kernel<2>);
+}
+
+int dense_max_ctas_per_sm(int W, bool batch, size_t smem) {
+  const void* k = dense_kernel_for(W, batch);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kDenseThreads + 32, smem) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, int grid,
+                  size_t smem, cudaStream_t stream) {
+  if (lp.T != 4 * W * kDenseThreads || lp.win != kDenseWin || lp.n_in % kDenseWin != 0) {
+    set_error("dense executor: bad launch shape");
+    return false;
+  }
+  const void* k = dense_kernel_for(W, false);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess) {
+    set_error("cudaFuncSetAttribute(dense) failed");
+    return false;
+  }
+  xk::TensorMap map;
+  if (tm) map = *tm;
+  else std::memset(&map, 0, sizeof(map));
+  if (W == 4)
+    dense_kernel<4><<<grid, kDenseThreads + 32, smem, stream>>>(lp, map);
+  else
+    dense_kernel<2><<<grid, kDenseThreads + 32, smem, stream>>>(lp, map);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("dense executor launch failed: ") + cudaGetErrorString(e));
+    return false;
+  }
+  return true;
+}
+
+bool launch_dense_batch(const xk::BatchParams& bp, int W, int grid, size_t smem,
+                        cudaStream_t stream) {
+  if (bp.T != 4 * W * kDenseThreads || bp.win != kDenseWin) {
+    set_error("dense executor: bad batch launch shape");
+    return false;
+  }
+  const void* k = dense_kernel_for(W, true);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess) {
+    set_error("cudaFuncSetAttribute(dense batch) failed");
+    return false;
+  }
+  if (W == 4)
+    dense_batch_kernel<4><<<grid, kDenseThreads + 32, smem, stream>>>(bp);
+  else
+    dense_batch_kernel<2><<<grid, kDenseThreads + 32, smem, stream>>>(bp);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("batched dense executor launch failed: ") + cudaGetErrorString(e));
     return false;
   }
   return true;

@@ -118,6 +118,21 @@ int interp_batch_max_ctas_per_sm(int threads, size_t smem);
 bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_t smem,
                          cudaStream_t stream);
 
+// Dense bitmatrix executor (executor.cu): words per consumer thread and
+// strip, shared memory of a launch with tiles of T bytes, resident CTAs,
+// single and batched launches (kDenseThreads consumers, windows of
+// kDenseWin strips; the masks follow the chunk stream in the program's
+// device buffer).
+constexpr int kDenseThreads = 128;
+constexpr int kDenseWin = 8;
+int dense_words();
+size_t dense_smem_bytes(int T);
+int dense_max_ctas_per_sm(int W, bool batch, size_t smem);
+bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, int grid,
+                  size_t smem, cudaStream_t stream);
+bool launch_dense_batch(const xk::BatchParams& bp, int W, int grid, size_t smem,
+                        cudaStream_t stream);
+
 // Compiled tier (jit.cc).
 bool jit_available();
 bool jit_ensure(Program* p, int threads, std::string* err);
@@ -133,6 +148,8 @@ int tile_threads_for_inputs(int n_in, int threads);
 // Threads per CTA of p's compiled tier: the tuned or pinned shape, else
 // EC_JIT_THREADS, else tile_threads_for_inputs(n_in, 128).
 int program_threads(const Program* p);
+// Consumer threads of a windowed single launch, or of a windowed batch module.
+int window_threads(bool module);
 // Resident CTAs per SM (the __launch_bounds__ minimum) that leave each of
 // `threads` threads reg_budget registers of the SM's 65,536.
 int minb_for(int threads, int reg_budget);
@@ -158,12 +175,13 @@ bool window_module(const std::vector<const Program*>& progs, int* win, int* n_wi
 bool jit_module_window(void* mod, int* win, int* n_win);
 bool jit_launch(Program* p, const xk::LaunchParams& lp, const xk::TensorMap* tm, int threads,
                 int grid, size_t smem, cudaStream_t stream);
-// Tensor map of a strided launch's inputs as [stripe][input strip][4-byte
-// word] with a box of one tile of up to 256 input strips; returns the strips
-// per box (a multiple of 8 that divides n_in), or 0 (no map) when the layout
-// or the driver does not allow one.
+// Tensor map of a strided launch's inputs as [stripe][input strip][element]
+// (4-byte elements, 8-byte ones for tiles over 1 KiB: xk::tmap_elem_shift)
+// with a box of one tile of up to 256 input strips; returns the strips per
+// box (a multiple of 8 that divides n_in), or 0 (no map) when the layout or
+// the driver does not allow one.
 int input_tensor_map(const xk::IoDesc& io, int n_in, int T, xk::TensorMap* out, int box_rows);
-// Tensor map of one block as [strip][4-byte word] (8 strips S bytes apart)
+// Tensor map of one block as [strip][element] (8 strips S bytes apart)
 // with a box of one tile of its 8 strips; false when not allowed.
 bool block_tensor_map(const void* block, long long S, int T, xk::TensorMap* out);
 bool block_tensor_map_allowed(const void* block, long long S, int T);
@@ -187,15 +205,18 @@ void host_io_release(xorec_host_io* h);
 ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
                       std::vector<uint64_t>* ptrs);
 int launch_threads(void* mod);
+int launch_tile(void* mod, bool interp, int threads);
+bool batch_launch(void* mod, bool interp, const xk::BatchParams& bp, int threads, int grid,
+                  size_t smem, cudaStream_t st);
 // Launch shape of a plan's batch modules for programs of n_in input strips:
 // the autotuner's (or ec_plan_set_launch's) shape, else the defaults.
 int plan_module_threads(const ec_plan* p, int n_in);
 int plan_module_minb(const ec_plan* p, int n_in);
 ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, bool must,
                           int* built);
-bool batch_launch_shape(void* mod, int max_in, int max_slots, int threads, size_t smem_optin,
-                        size_t* smem, int* per_sm);
-int batch_ranges(long long n_items, int sms, int per_sm, int chunk, int max_in);
+bool batch_launch_shape(void* mod, bool interp, int max_in, int max_slots, int threads,
+                        size_t smem_optin, size_t* smem, int* per_sm);
+int batch_ranges(long long n_items, int sms, int per_sm, int chunk, int max_in, bool dense);
 // Split a launch's items into n_ranges contiguous ranges (BatchParams).
 void set_ranges(xk::BatchParams* bp, long long n_items, int n_ranges);
 

@@ -159,6 +159,10 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   Slp chains = slp_rows_chains(n_in, R, order);
   Program p;
   p.stats.raw = metrics(chains);
+  p.masks.assign(static_cast<size_t>((n_out + 31) / 32) * n_in, 0u);
+  for (int r = 0; r < n_out; ++r)
+    for (int c = 0; c < n_in; ++c)
+      if (R[r].test(c)) p.masks[static_cast<size_t>(r / 32) * n_in + c] |= 1u << (r % 32);
   Slp fused;
   // Two-level program for wide codes (inputs do not fit the registers):
   // groups of partial sums as large as the register budget allows.

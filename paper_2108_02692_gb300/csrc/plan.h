@@ -68,6 +68,10 @@ struct Program {
   std::vector<uint16_t> code;
   std::vector<uint16_t> chunks;
   int interp_slots = 0;      // slots of the stream in `chunks`
+  // column masks of the program's bitmatrix for the dense executor: word
+  // g * n_in + c, bit r is bit (32 g + r, c) (output strip 32 g + r reads
+  // input strip c); ceil(n_out / 32) groups
+  std::vector<uint32_t> masks;
   PipelineStats stats;
   Slp fused;                 // single-assignment fused program
   Schedule sched;            // GPU schedule of `fused`
@@ -76,7 +80,7 @@ struct Program {
   // Empty: inputs preloaded (narrow) or read at every use (wide).
   std::vector<int> load_group;
   uint64_t hash = 0;         // content hash of the fused program
-  // device copy of `code` (owned; freed by the plan)
+  // device copy of `chunks` followed by `masks` (owned; freed by the plan)
   uint16_t* d_code = nullptr;
   // compiled tier (set once a straight-line kernel exists for this program)
   void* jit = nullptr;

@@ -7,7 +7,7 @@
 // earlier batches were on the GPU, writes its stripe descriptors and block
 // table into the pinned staging of a free slot, copies them to the slot's
 // device tables and launches the batched pipeline (one persistent launch
-// per compiled module, the interpreter for programs without one) on the
+// per compiled module, the dense bitmatrix executor for programs without one) on the
 // slot's stream.  Several slots are in flight at once, so their work
 // overlaps on the device; a slot returns to the pool when its completion
 // event fires, which also timestamps every request in it (latency =
@@ -46,7 +46,7 @@ namespace {
 struct Req {
   uint64_t ticket = 0;
   Program* prog = nullptr;
-  void* mod = nullptr;          // compiled module that runs it, or nullptr = interpreter
+  void* mod = nullptr;          // compiled module that runs it, or nullptr = the dense executor
   std::vector<uint64_t> ptrs;
   long long S = 0, tiles = 0;
   size_t bytes = 0;
@@ -167,7 +167,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueued) {
   *enqueued = false;
   xorec::TraceRange trace_("xorec serve dispatch");
-  // group by launch target: compiled module of this block size, or interpreter
+  // group by launch target: compiled module of this block size, or the dense executor
   auto target = [&](const Req& r) -> void* { return r.mod; };
   std::stable_sort(reqs.begin(), reqs.end(),
                    [&](const Req& a, const Req& b) { return target(a) < target(b); });
@@ -186,14 +186,16 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
   auto* d_queues = reinterpret_cast<xk::u64*>(sl.d_tab);
   auto* d_descs = reinterpret_cast<xk::StripeDesc*>(sl.d_tab + desc_off);
   auto* d_blocks = reinterpret_cast<xk::u64*>(sl.d_tab + block_off);
-  struct L { void* mod; int threads, begin, n; long long items; int max_in, max_slots; };
+  struct L { void* mod; int threads, T, begin, n; long long items; int max_in, max_slots; };
   std::vector<L> launches;
   size_t off = 0;
   for (size_t i = 0; i < reqs.size(); ++i) {
     const Req& r = reqs[i];
     void* mod = target(r);
     if (launches.empty() || launches.back().mod != mod)
-      launches.push_back(L{mod, xorec::launch_threads(mod), static_cast<int>(i), 0, 0, 0, 0});
+      launches.push_back(L{mod, xorec::launch_threads(mod),
+                           xorec::launch_tile(mod, false, xorec::launch_threads(mod)),
+                           static_cast<int>(i), 0, 0, 0, 0});
     L& l = launches.back();
     xk::StripeDesc& d = h_descs[i];
     std::memset(&d, 0, sizeof(d));
@@ -230,8 +232,8 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     if (it == sv->shapes.end()) {
       size_t smem = 0;
       int per_sm = 1;
-      if (!xorec::batch_launch_shape(l.mod, l.max_in, l.max_slots, l.threads, sv->di.smem_optin,
-                                     &smem, &per_sm))
+      if (!xorec::batch_launch_shape(l.mod, false, l.max_in, l.max_slots, l.threads,
+                                     sv->di.smem_optin, &smem, &per_sm))
         return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
       it = sv->shapes.emplace(key, std::make_pair(smem, per_sm)).first;
     }
@@ -243,14 +245,14 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     bp.queue = d_queues + li;
     xorec::set_ranges(&bp, l.items, 1);
     bp.n_items = l.items;
-    bp.T = 4 * l.threads;
+    bp.T = l.T;
     bp.max_in = l.max_in;
     bp.status = sv->di.status;
     bp.local_status = sl.d_status;
     const long long full = static_cast<long long>(sv->di.sms) * it->second.second;
     const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(full, l.items)));
-    const bool ok = l.mod ? xorec::jit_module_launch(l.mod, bp, grid, it->second.first, sl.st)
-                          : xorec::launch_interp_batch(bp, l.threads, grid, it->second.first, sl.st);
+    const bool ok =
+        xorec::batch_launch(l.mod, false, bp, l.threads, grid, it->second.first, sl.st);
     if (!ok) return EC_ECUDA;
   }
   if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) {
@@ -373,7 +375,7 @@ void scheduler(ec_server* sv) {
 }
 
 // Compiles, in the background, the programs that requests found without a
-// compiled module; the interpreter runs them meanwhile.  New programs that
+// compiled module; the dense executor runs them meanwhile.  New programs that
 // arrive together are compiled into shared modules.
 void compiler_loop(ec_server* sv) {
   cudaSetDevice(sv->device);
@@ -471,7 +473,7 @@ ec_status ec_server_warm(ec_server* sv, ec_plan* plan, int max_erasures) {
     if (st != EC_OK) return st;
     want.emplace_back(plan, p);
   }
-  if (!xorec::jit_available()) return EC_OK;   // interpreter serves everything
+  if (!xorec::jit_available()) return EC_OK;   // the dense executor serves everything
   return xorec::compile_modules(want, false, nullptr);
 }
 
@@ -484,7 +486,7 @@ ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
   {
     // launch target fixed at submission: the program's compiled module
     // (modules live as long as their plan; a launch takes its module's
-    // block size), else the interpreter
+    // block size), else the dense executor
     std::lock_guard<std::mutex> lk(job->plan->mu);
     r.mod = r.prog->mod;
     if (!r.mod && !xorec::ensure_device_code(r.prog)) return EC_ECUDA;
@@ -497,9 +499,9 @@ ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
     }
   }
   const size_t B = job->block_bytes;
-  const int th = xorec::launch_threads(r.mod);
+  const int T = xorec::launch_tile(r.mod, false, xorec::launch_threads(r.mod));
   r.S = static_cast<long long>(B / 8);
-  r.tiles = (r.S + 4 * th - 1) / (4 * th);
+  r.tiles = (r.S + T - 1) / T;
   r.bytes_in = static_cast<long long>(r.prog->n_in / 8) * static_cast<long long>(B);
   r.bytes_out = static_cast<long long>(r.prog->n_out / 8) * static_cast<long long>(B);
   r.bytes = static_cast<size_t>(r.bytes_in + r.bytes_out);

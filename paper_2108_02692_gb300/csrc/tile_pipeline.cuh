@@ -72,6 +72,14 @@ struct LaunchParams {
 // Window slots in the shared-memory ring of windowed programs.
 constexpr int kWinRing = 4;
 
+// Tensor maps address a strip in 4-byte elements, or in 8-byte elements
+// when a tile is wider than a box dimension (at most 256 elements) of
+// 4-byte elements holds: log2 of the element size for tiles of T bytes.
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+__host__ __device__
+#endif
+constexpr int tmap_elem_shift(int T) { return T > 1024 ? 3 : 2; }
+
 // Batched launches: every stripe has its own program, strip length and
 // blocks.  Work items are (stripe, tile) pairs listed in `items`.
 struct StripeDesc {
@@ -84,8 +92,8 @@ struct StripeDesc {
   int n_inblk, n_outblk;
   int prog;              // program index inside a compiled module
   int pad_;
-  const TensorMap* maps; // n_inblk tensor maps (input block j as [strip][4-byte
-                         // word], box = one tile of its 8 strips), or null:
+  const TensorMap* maps; // n_inblk tensor maps (input block j as [strip][element],
+                         // box = one tile of its 8 strips), or null:
                          // one 1-D copy per strip
 };
 
@@ -214,7 +222,8 @@ __device__ __forceinline__ void issue_item(const LaunchParams& p, const TensorMa
   if (p.tmap == p.n_in) {
     if (lane == 0) {
       mbar_arrive_expect_tx(bar, static_cast<u32>(p.n_in) * static_cast<u32>(p.T));
-      tma_load_3d(smem_addr(dst), tm, static_cast<int>(c0 >> 2), 0, static_cast<int>(s), bar);
+      tma_load_3d(smem_addr(dst), tm, static_cast<int>(c0 >> tmap_elem_shift(p.T)), 0,
+                  static_cast<int>(s), bar);
     }
     return;
   }
@@ -224,7 +233,8 @@ __device__ __forceinline__ void issue_item(const LaunchParams& p, const TensorMa
     if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(p.n_in) * static_cast<u32>(p.T));
     __syncwarp();
     for (int y = lane * p.tmap; y < p.n_in; y += 32 * p.tmap)
-      tma_load_3d(smem_addr(dst + static_cast<i64>(y) * p.T), tm, static_cast<int>(c0 >> 2), y,
+      tma_load_3d(smem_addr(dst + static_cast<i64>(y) * p.T), tm,
+                  static_cast<int>(c0 >> tmap_elem_shift(p.T)), y,
                   static_cast<int>(s), bar);
     return;
   }
@@ -362,7 +372,8 @@ __device__ __forceinline__ void issue_window(const LaunchParams& p, const Tensor
     // one box of `win` strips; rows past n_in are zero-filled and counted
     if (lane == 0) {
       mbar_arrive_expect_tx(bar, static_cast<u32>(p.win) * static_cast<u32>(p.T));
-      tma_load_3d(smem_addr(dst), tm, static_cast<int>(c0 >> 2), y0, static_cast<int>(s), bar);
+      tma_load_3d(smem_addr(dst), tm, static_cast<int>(c0 >> tmap_elem_shift(p.T)), y0,
+                  static_cast<int>(s), bar);
     }
     return;
   }
@@ -378,13 +389,14 @@ __device__ __forceinline__ void issue_window(const LaunchParams& p, const Tensor
   }
 }
 
-// Body (windowed programs):
+// Body (windowed programs; each consumer owns kColBytes bytes of every
+// strip of the tile):
 //   bool compute(const LaunchParams&, const WindowView&, i64 q0, i64 stripe,
 //                i64 c0, int len, int col) const
 // runs the program on column `col` of the item whose first phase is the
 // CTA's phase q0 (col may lie past len: its results are not stored, but it
 // takes part in every phase); false when a wait timed out.
-template <class Body>
+template <class Body, int kColBytes = 4>
 __device__ __forceinline__ void run_window_pipeline(const LaunchParams& p, u8* smem,
                                                     const Body& body, const TensorMap* tm) {
   u64* full = reinterpret_cast<u64*>(smem);
@@ -430,7 +442,7 @@ __device__ __forceinline__ void run_window_pipeline(const LaunchParams& p, u8* s
     }
     return;
   }
-  const int col = (tid - 32) * 4;
+  const int col = (tid - 32) * kColBytes;
   i64 q0 = 0;
   for (i64 item = first; item < p.n_items; item += step, q0 += p.n_phases) {
     const i64 s = item / p.tiles_per_strip;
@@ -511,7 +523,7 @@ __device__ __forceinline__ void prepare_batch_item(const BatchParams& p, i64 ite
   if (nc.maps) {
     // one tiled copy per input block: the full box lands (zero-filled past
     // the end of the strips) and counts in full
-    nc.x = static_cast<int>(c0 >> 2);
+    nc.x = static_cast<int>(c0 >> tmap_elem_shift(p.T));
     nc.bytes = static_cast<u32>(n_in) * static_cast<u32>(p.T);
     return;
   }
@@ -736,12 +748,16 @@ __device__ __forceinline__ void run_batch_pipeline(const BatchParams& p, u8* sme
 // block of the window, or one 1-D copy per strip) and, in the item's first
 // slot, leaves the item's index for the consumers; a last slot holding -1
 // ends the launch.  The consumers take the item from its first slot and run
-// its program window by window.
+// its program window by window.  Each consumer owns kColBytes bytes of
+// every strip of the tile (T = kColBytes x consumers).  With kStripePhases
+// (the dense bitmatrix executor) an item's windows and phases follow its
+// stripe, so one launch mixes codes of any width.
 // Shared memory: [full barriers (0)][empty barriers (64)][slot items (96)],
 // then the ring from byte 128.
 // Body (windowed modules):
 //   bool compute(const StripeDesc&, const WindowView&, i64 q0, i64 c0, int len,
 //                int col) const
+//   int groups(const StripeDesc&) const      (kStripePhases only)
 __device__ __forceinline__ void issue_batch_window(const BatchParams& p, const StripeDesc* d,
                                                    i64 c0, int len, int w, u8* dst, u32 bar) {
   const int lane = threadIdx.x & 31;
@@ -756,7 +772,7 @@ __device__ __forceinline__ void issue_batch_window(const BatchParams& p, const S
     __syncwarp();
     for (int j = lane; j < nb; j += 32)
       tma_load_2d(smem_addr(dst + static_cast<i64>(8 * j) * p.T), d->maps + b0 + j,
-                  static_cast<int>(c0 >> 2), 0, bar);
+                  static_cast<int>(c0 >> tmap_elem_shift(p.T)), 0, bar);
     return;
   }
   if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<u32>(n) * static_cast<u32>(len));
@@ -769,7 +785,21 @@ __device__ __forceinline__ void issue_batch_window(const BatchParams& p, const S
   }
 }
 
-template <class Body>
+// Windows and phases of one item: the launch's (windowed modules), or,
+// with kStripePhases, the stripe's own (windows of p.win strips over its
+// inputs, read once per group of rows: Body::groups(const StripeDesc&)).
+template <bool kStripePhases>
+__device__ __forceinline__ int item_windows(const BatchParams& p, const StripeDesc& d) {
+  return kStripePhases ? (8 * d.n_inblk + p.win - 1) / p.win : p.n_win;
+}
+template <bool kStripePhases, class Body>
+__device__ __forceinline__ int item_phases(const BatchParams& p, const StripeDesc& d,
+                                           const Body& body) {
+  if constexpr (kStripePhases) return item_windows<true>(p, d) * body.groups(d);
+  else return p.n_win;
+}
+
+template <class Body, int kColBytes = 4, bool kStripePhases = false>
 __device__ __forceinline__ void run_batch_window_pipeline(const BatchParams& p, u8* smem,
                                                           const Body& body) {
   u64* full = reinterpret_cast<u64*>(smem);
@@ -808,7 +838,8 @@ __device__ __forceinline__ void run_batch_window_pipeline(const BatchParams& p, 
       i64 c0 = 0;
       int len = 0;
       if (item >= 0) batch_item_geom(p, item, cursor, d, c0, len);
-      const int phases = item >= 0 ? p.n_win : 1;
+      const int phases = item >= 0 ? item_phases<kStripePhases>(p, *d, body) : 1;
+      const int nw = item >= 0 ? item_windows<kStripePhases>(p, *d) : 1;
       for (int ph = 0; ph < phases; ++ph, ++q) {
         const int slot = static_cast<int>(q % kWinRing);
         if (tid == 0)
@@ -826,7 +857,8 @@ __device__ __forceinline__ void run_batch_window_pipeline(const BatchParams& p, 
         }
         if (tid == 0) fence_proxy_async();
         __syncwarp();
-        issue_batch_window(p, d, c0, len, ph, v.ring + slot * v.slot_bytes, smem_addr(&full[slot]));
+        issue_batch_window(p, d, c0, len, ph % nw, v.ring + slot * v.slot_bytes,
+                           smem_addr(&full[slot]));
       }
     }
     if (!ok && tid == 0) {
@@ -839,7 +871,7 @@ __device__ __forceinline__ void run_batch_window_pipeline(const BatchParams& p, 
     }
     return;
   }
-  const int col = (tid - 32) * 4;
+  const int col = (tid - 32) * kColBytes;
   int cursor = 0;
   for (i64 q0 = 0;;) {
     const int slot = static_cast<int>(q0 % kWinRing);
@@ -859,7 +891,7 @@ __device__ __forceinline__ void run_batch_window_pipeline(const BatchParams& p, 
       if (p.local_status) *reinterpret_cast<volatile int*>(p.local_status) = XK_STATUS_TIMEOUT;
       return;
     }
-    q0 += p.n_win;
+    q0 += item_phases<kStripePhases>(p, *d, body);
   }
 }
 

@@ -62,8 +62,8 @@ def check(expect):
             assert np.array_equal(t.cpu().numpy(), r)
 
 
-@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED],
-                         ids=["interp", "compiled"])
+@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED, xo.EC_EXEC_DENSE],
+                         ids=["interp", "compiled", "dense"])
 def test_mixed_batch_matches_oracle(plans, executor):
     jobs, keep, expect = make_jobs(plans, 40, seed=1 + executor)
     b = xo.ec_batch_create(jobs, executor)
@@ -80,8 +80,8 @@ def test_mixed_batch_matches_oracle(plans, executor):
 
 
 @pytest.mark.parametrize("ranges", [2, 7, 152, 4096])
-@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED],
-                         ids=["interp", "compiled"])
+@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED, xo.EC_EXEC_DENSE],
+                         ids=["interp", "compiled", "dense"])
 def test_batch_item_ranges_match_oracle(plans, executor, ranges, monkeypatch):
     """Items split into per-SM ranges (forced here; a batch only chooses them
     when it has enough items): CTAs start on their SM's range and move to the

@@ -57,8 +57,8 @@ def test_empty_batch_runs_and_captures(plan):
     assert xo.ec_device_status() == 0
 
 
-@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED],
-                         ids=["interp", "compiled"])
+@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED, xo.EC_EXEC_DENSE],
+                         ids=["interp", "compiled", "dense"])
 @pytest.mark.parametrize("k", [1, 7, 32])
 def test_single_scaled_parity_is_xor_of_data(k, executor):
     B = 8 * 1040

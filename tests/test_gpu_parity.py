@@ -14,8 +14,8 @@ from paper_2108_02692_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-EXECS = [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED]
-EXEC_IDS = ["interp", "compiled"]
+EXECS = [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED, xo.EC_EXEC_DENSE]
+EXEC_IDS = ["interp", "compiled", "dense"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -189,9 +189,11 @@ def test_decode_rs4_2_every_pattern(executor):
         p.close()
 
 
-def test_decode_rs6_3_every_pattern_interp():
+@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_DENSE],
+                         ids=["interp", "dense"])
+def test_decode_rs6_3_every_pattern(executor):
     k, m, B = 6, 3, 8 * 528
-    p = Plan(k, m, xo.EC_EXEC_INTERP)
+    p = Plan(k, m, executor)
     try:
         blocks = _codeword(k, m, B, 25, 0)
         pats = [e for ne in range(1, 4) for e in itertools.combinations(range(9), ne)]
@@ -213,10 +215,14 @@ def test_decode_rs6_3_sample_compiled():
         p.close()
 
 
-def test_decode_rs10_4_all_1470_patterns_interp():
-    """Every erasure set of 1-4 blocks of RS(10,4) (C(14,<=4) = 1470)."""
-    k, m, B = 10, 4, 256
-    p = Plan(k, m, xo.EC_EXEC_INTERP)
+@pytest.mark.parametrize("executor,B", [(xo.EC_EXEC_INTERP, 256), (xo.EC_EXEC_DENSE, 256),
+                                        (xo.EC_EXEC_DENSE, 8 * 2064)],
+                         ids=["interp", "dense", "dense-3-tiles"])
+def test_decode_rs10_4_all_1470_patterns(executor, B):
+    """Every erasure set of 1-4 blocks of RS(10,4) (C(14,<=4) = 1470); with
+    strips of 2064 B the dense executor's 1 KiB tiles end in a ragged one."""
+    k, m = 10, 4
+    p = Plan(k, m, executor)
     try:
         pats = synth.all_erasure_patterns(14, 4)
         assert len(pats) == 1470

@@ -51,8 +51,8 @@ def test_two_level_strided_encode_matches_oracle(k, m):
     assert xo.ec_device_status() == 0
 
 
-@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED],
-                         ids=["interp", "compiled"])
+@pytest.mark.parametrize("executor", [xo.EC_EXEC_INTERP, xo.EC_EXEC_COMPILED, xo.EC_EXEC_DENSE],
+                         ids=["interp", "compiled", "dense"])
 def test_two_level_decode_patterns(executor):
     torch.cuda.set_device(0)
     k, m, B = 16, 4, 8 * 1040
