@@ -28,6 +28,7 @@
 #include "internal.h"
 
 using xorec::Program;
+using xorec::kDenseThreads;
 
 namespace {
 
@@ -54,6 +55,8 @@ struct Launch {
   void* mod = nullptr;                 // compiled module, or nullptr: the dense
                                        // executor (the interpreter if `interp`)
   bool interp = false;
+  int dense_w = 4;                     // the dense executor's words per column
+  bool dense_tbl = true;               // and form
   int threads = 128;                   // threads per CTA that own a column
   int T = 512;                         // tile bytes per strip
   int stripe_begin = 0, n_stripes = 0; // the launch's stripes in the descriptor array
@@ -222,14 +225,15 @@ int launch_tile(void* mod, bool interp, int threads) {
   return mod || interp ? 4 * threads : 4 * dense_words() * kDenseThreads;
 }
 
-// One batched launch on its target.
+// One batched launch on its target (dense_w, dense_tbl: the dense
+// executor's form its shape was computed for).
 bool batch_launch(void* mod, bool interp, const xk::BatchParams& bp, int threads, int grid,
-                  size_t smem, cudaStream_t st) {
+                  size_t smem, cudaStream_t st, int dense_w, bool dense_tbl) {
   if (mod) return jit_module_launch(mod, bp, grid, smem, st);
   if (interp) return launch_interp_batch(bp, threads, grid, smem, st);
   xk::BatchParams dp = bp;
   dp.win = kDenseWin;
-  return launch_dense_batch(dp, dense_words(), grid, smem, st);
+  return launch_dense_batch(dp, dense_w, dense_tbl, grid, smem, st);
 }
 
 // A program of one group of rows that the windowed pipeline runs (its
@@ -328,14 +332,15 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
 // Shared memory and resident CTAs per SM of a batched launch (module, dense
 // executor, or interpreter).
 bool batch_launch_shape(void* mod, bool interp, int max_in, int max_slots, int threads,
-                        size_t smem_optin, size_t* smem, int* per_sm) {
+                        size_t smem_optin, size_t* smem, int* per_sm, int dense_w,
+                        bool dense_tbl) {
   const int T = 4 * threads;
   if (!mod && !interp) {
-    // the dense executor: a ring of windows of kDenseWin strips
-    const int W = dense_words();
-    *smem = dense_smem_bytes(4 * W * kDenseThreads);
+    // the dense executor: a ring of windows of kDenseWin strips (and its
+    // tables)
+    *smem = dense_smem_bytes(4 * dense_w * kDenseThreads, dense_tbl);
     if (*smem > smem_optin) return false;
-    *per_sm = std::max(1, dense_max_ctas_per_sm(W, true, *smem));
+    *per_sm = std::max(1, dense_max_ctas_per_sm(dense_w, dense_tbl, true, *smem));
     return true;
   }
   int win = 0, n_win = 0;
@@ -458,6 +463,8 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       Launch L;
       L.mod = mod;
       L.interp = !mod && executor == EC_EXEC_INTERP;
+      L.dense_w = xorec::dense_words();
+      L.dense_tbl = xorec::dense_table();
       L.threads = L.interp ? batch_threads() : xorec::launch_threads(mod);
       b->launches.push_back(L);
     }
@@ -472,7 +479,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     while (L.interp && L.threads > 32 &&
            xorec::interp_batch_smem_bytes(L.max_in, L.max_slots, 4 * L.threads) > di.smem_optin)
       L.threads /= 2;
-    L.T = xorec::launch_tile(L.mod, L.interp, L.threads);
+    L.T = L.mod || L.interp ? 4 * L.threads : 4 * L.dense_w * kDenseThreads;
   }
   for (auto& e : ents) {
     const Launch& L = b->launches[e.launch];
@@ -616,7 +623,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     int per_sm = 1;
     if (L.mod) ++n_modules;
     if (!xorec::batch_launch_shape(L.mod, L.interp, L.max_in, L.max_slots, L.threads,
-                                   di.smem_optin, &L.smem, &per_sm)) {
+                                   di.smem_optin, &L.smem, &per_sm, L.dense_w, L.dense_tbl)) {
       free_batch(b);
       return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
     }
@@ -706,7 +713,8 @@ ec_status ec_batch_run(ec_batch* b, void* stream) {
     bp.max_in = L.max_in;
     bp.status = b->status;
     bp.local_status = b->d_status;
-    const bool ok = xorec::batch_launch(L.mod, L.interp, bp, L.threads, L.grid, L.smem, st);
+    const bool ok = xorec::batch_launch(L.mod, L.interp, bp, L.threads, L.grid, L.smem, st,
+                                        L.dense_w, L.dense_tbl);
     if (!ok) return EC_ECUDA;
   }
   if (fan) {

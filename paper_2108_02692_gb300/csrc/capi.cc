@@ -77,12 +77,13 @@ bool device_info(DeviceInfo* out) {
 }
 
 // Device buffer of a program: its chunk stream (16-byte chunks), then the
-// dense executor's column masks.
+// dense executor's control words (column masks, then row words).
 bool ensure_device_code(Program* p) {
   if (p->d_code) return true;
   const size_t code_bytes = p->chunks.size() * sizeof(uint16_t);
   const size_t mask_bytes = p->masks.size() * sizeof(uint32_t);
-  const size_t bytes = std::max<size_t>(16, code_bytes + mask_bytes);
+  const size_t row_bytes = p->rowbits.size() * sizeof(uint32_t);
+  const size_t bytes = std::max<size_t>(16, code_bytes + mask_bytes + row_bytes);
   uint16_t* d = nullptr;
   if (dev_malloc(&d, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -92,7 +93,10 @@ bool ensure_device_code(Program* p) {
   if ((code_bytes && cudaMemcpy(d, p->chunks.data(), code_bytes, cudaMemcpyHostToDevice) !=
                          cudaSuccess) ||
       (mask_bytes && cudaMemcpy(reinterpret_cast<uint8_t*>(d) + code_bytes, p->masks.data(),
-                                mask_bytes, cudaMemcpyHostToDevice) != cudaSuccess)) {
+                                mask_bytes, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (row_bytes && cudaMemcpy(reinterpret_cast<uint8_t*>(d) + code_bytes + mask_bytes,
+                               p->rowbits.data(), row_bytes, cudaMemcpyHostToDevice) !=
+                        cudaSuccess)) {
     cudaGetLastError();
     cudaFree(d);
     set_error("upload of the program failed");
@@ -341,11 +345,13 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   }
   const bool dense = !compiled && executor != EC_EXEC_INTERP;
   int dense_w = 0;
+  bool dense_tbl = false;
   if (dense) {
     // the dense bitmatrix executor: windows of one block stream through a
     // ring; all output rows' accumulators in registers, in groups of 32
     if (!ensure_device_code(p)) return false;
     dense_w = dense_words();
+    dense_tbl = dense_table();
     lp.T = 4 * dense_w * kDenseThreads;
     lp.win = kDenseWin;
     lp.n_win = p->n_in / kDenseWin;
@@ -353,8 +359,8 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     lp.code = p->d_code;
     lp.code_len = static_cast<int>(p->chunks.size() / 8);
     nstage = 1;
-    smem = dense_smem_bytes(lp.T);
-    per_sm = dense_max_ctas_per_sm(dense_w, false, smem);
+    smem = dense_smem_bytes(lp.T, dense_tbl);
+    per_sm = dense_max_ctas_per_sm(dense_w, dense_tbl, false, smem);
   } else if (!compiled) {
     if (!ensure_device_code(p)) return false;
     // one stage (more resident CTAs hide more latency than a second stage
@@ -396,8 +402,8 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   if (dense) {
     xk::TensorMap tm;
     lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, kDenseWin);
-    return launch_dense(lp, lp.tmap ? &tm : nullptr, dense_w, static_cast<int>(grid), smem,
-                        stream);
+    return launch_dense(lp, lp.tmap ? &tm : nullptr, dense_w, dense_tbl, static_cast<int>(grid),
+                        smem, stream);
   }
   xk::TensorMap tm;
   lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, 0);

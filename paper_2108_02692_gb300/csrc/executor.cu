@@ -35,6 +35,7 @@ __device__ __forceinline__ Words<W> lds(u32 a) {
   } else if constexpr (W == 2) {
     asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.v[0]), "=r"(r.v[1]) : "r"(a));
   } else {
+    static_assert(W == 4, "one, two or four words");
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]) : "r"(a));
   }
@@ -45,8 +46,13 @@ template <int W>
 __device__ __forceinline__ void sts(u32 a, const Words<W>& x) {
   if constexpr (W == 1) {
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(x.v[0]) : "memory");
-  } else {
+  } else if constexpr (W == 2) {
     asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(x.v[0]), "r"(x.v[1]) : "memory");
+  } else {
+    static_assert(W == 4, "one, two or four words");
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x.v[0]), "r"(x.v[1]),
+                 "r"(x.v[2]), "r"(x.v[3])
+                 : "memory");
   }
 }
 
@@ -57,6 +63,7 @@ __device__ __forceinline__ void stg(u8* p, const Words<W>& x) {
   } else if constexpr (W == 2) {
     *reinterpret_cast<uint2*>(p) = make_uint2(x.v[0], x.v[1]);
   } else {
+    static_assert(W == 4, "one, two or four words");
     *reinterpret_cast<uint4*>(p) = make_uint4(x.v[0], x.v[1], x.v[2], x.v[3]);
   }
 }
@@ -200,46 +207,100 @@ __global__ void __launch_bounds__(256, 1) interp_batch_kernel(BatchParams p) {
 // whose bit (r, c) is set), the linear map every SLP of the program
 // computes.  On the GPU this beats interpreting the optimised SLP: the
 // interpreter fetches, decodes and addresses every operand, while here the
-// control is one 32-bit column mask per input strip, uniform across the
-// CTA, and each set bit costs one XOR per word held in registers.
+// control is a few uniform words per window and every input word is read
+// from shared memory once.
 //
 // The inputs stream through the windowed pipeline (tile_pipeline.cuh) in
 // windows of kDenseWin strips (one block); consumers own W 4-byte words of
 // every strip.  Output rows go in groups of up to 32: per group, every
 // window is read once (a group after the first reads them again, from L2)
-// and XORed into the group's accumulators under the mask bits; at the end of
-// the group each accumulator is written to its output strip.  The masks
-// follow the program's chunk stream in its device buffer: group g's mask of
-// input strip c is word g * n_in + c, bit r for output strip 32 g + r.
+// and XORed into the group's register accumulators; at the end of the group
+// each accumulator is written to its output strip.  Two forms:
+//   masks: per input strip, XOR it into the accumulators of the rows whose
+//     bit is set (a uniform test and W XORs per row and strip);
+//   tables (the method of four Russians, Arlazarov, Dinic, Kronrod and
+//     Faradzev): per window, each consumer writes the XORs of all 16 subsets
+//     of strips 0-3 and of strips 4-7 of its column into two tables in
+//     shared memory (15 XORs each, in Gray-code order so one entry is live at
+//     a time); a row then takes two table entries, chosen by its 8 bits of
+//     the window.  A quarter of the table reads per row and strip, and about
+//     a third of the integer work of the masks.
+// Control words follow the program's chunk stream in its device buffer:
+// n_groups * n_in masks (group g's mask of input strip c is word g*n_in + c,
+// bit r for output strip 32 g + r), then as many row words (group g, window
+// w: words g*n_in + 8 w + j hold the window's bits of rows 4j .. 4j+3, one
+// byte per row, bit i for strip 8 w + i).
 using xorec::kDenseThreads;
 using xorec::kDenseWin;
 
+template <int W, bool kTable>
+struct DenseForm {
+  static constexpr u32 T = 4u * W * kDenseThreads;   // tile bytes per strip
+};
+
 // One group of kRows output rows (rows <= kRows of them real): every window
-// of the item, then the stores.  q: the CTA's phase counter.
-template <int W, int kRows, class OutAddr>
-__device__ __forceinline__ bool dense_group(const WindowView& v, i64& q, int n_win, u32 T,
-                                            int col, bool store, const u32* __restrict__ masks,
+// of the item, then the stores.  q: the CTA's phase counter; ctrl: the
+// group's masks (mask form) or row words (table form); tbl: shared address
+// of this consumer's column in entry 0 of table 0 (entries T bytes apart).
+template <int W, bool kTable, int kRows, class OutAddr>
+__device__ __forceinline__ bool dense_group(const WindowView& v, i64& q, int n_win, int col,
+                                            bool store, const u32* __restrict__ ctrl, u32 tbl,
                                             int rows, const OutAddr& out) {
+  constexpr u32 T = DenseForm<W, kTable>::T;
   Words<W> acc[kRows];
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[r].v[w] = 0;
+  if constexpr (kTable) {
+    Words<W> z;
+#pragma unroll
+    for (int w = 0; w < W; ++w) z.v[w] = 0;
+    sts<W>(tbl, z);
+    sts<W>(tbl + 16 * T, z);
+  }
   for (int w = 0; w < n_win; ++w, ++q) {
     const u8* slot = v.begin(q);
     if (!slot) return false;
-    const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(masks + kDenseWin * w));
-    const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(masks + kDenseWin * w) + 1);
-    const u32 mk[kDenseWin] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+    const uint4 c0 = __ldg(reinterpret_cast<const uint4*>(ctrl + kDenseWin * w));
+    const uint4 c1 = __ldg(reinterpret_cast<const uint4*>(ctrl + kDenseWin * w) + 1);
+    const u32 cw[kDenseWin] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
     const u32 a = smem_addr(slot) + static_cast<u32>(col);
+    if constexpr (!kTable) {
 #pragma unroll
-    for (int c = 0; c < kDenseWin; ++c) {
-      const Words<W> x = lds<W>(a + static_cast<u32>(c) * T);
+      for (int c = 0; c < kDenseWin; ++c) {
+        const Words<W> x = lds<W>(a + static_cast<u32>(c) * T);
 #pragma unroll
-      for (int r = 0; r < kRows; ++r)
-        if ((mk[c] >> r) & 1u) xor_in(acc[r], x);
+        for (int r = 0; r < kRows; ++r)
+          if ((cw[c] >> r) & 1u) xor_in(acc[r], x);
+      }
+      v.end(q);
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        Words<W> x[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = lds<W>(a + static_cast<u32>(4 * h + i) * T);
+        Words<W> cur = x[0];
+        sts<W>(tbl + (16 * h + 1) * T, cur);
+#pragma unroll
+        for (int i = 2; i < 16; ++i) {
+          // Gray code i ^ (i >> 1) differs from the previous one in the
+          // lowest set bit of i
+          xor_in(cur, x[(i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : 3]);
+          sts<W>(tbl + (16 * h + (i ^ (i >> 1))) * T, cur);
+        }
+      }
+      v.end(q);   // the window now lives in this consumer's tables
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const u32 b = (cw[r >> 2] >> (8 * (r & 3))) & 0xffu;
+        const Words<W> lo = lds<W>(tbl + (b & 15u) * T);
+        const Words<W> hi = lds<W>(tbl + (16u + (b >> 4)) * T);
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[r].v[k] ^= lo.v[k] ^ hi.v[k];
+      }
     }
-    v.end(q);
   }
   if (store) {
 #pragma unroll
@@ -249,28 +310,34 @@ __device__ __forceinline__ bool dense_group(const WindowView& v, i64& q, int n_w
   return true;
 }
 
-// All groups of one item.  n_in: input strips (a multiple of kDenseWin).
-template <int W, class OutAddr>
-__device__ __forceinline__ bool dense_item(const WindowView& v, i64 q0, int n_in, int n_out, u32 T,
+__device__ __forceinline__ int dense_groups(int n_out) { return (n_out + 31) / 32; }
+
+// All groups of one item.  n_in: input strips (a multiple of kDenseWin);
+// masks: the program's control words.
+template <int W, bool kTable, class OutAddr>
+__device__ __forceinline__ bool dense_item(const WindowView& v, i64 q0, int n_in, int n_out,
                                            int col, bool store, const u32* masks,
                                            const OutAddr& out) {
+  constexpr u32 T = DenseForm<W, kTable>::T;
   i64 q = q0;
   const int n_win = n_in / kDenseWin;
+  const u32* ctrl = kTable ? masks + static_cast<i64>(dense_groups(n_out)) * n_in : masks;
+  const u32 tbl = smem_addr(v.ring) + static_cast<u32>(xk::kWinRing * kDenseWin) * T +
+                  static_cast<u32>(col);
   for (int g = 0; 32 * g < n_out; ++g) {
     const int rows = n_out - 32 * g < 32 ? n_out - 32 * g : 32;
-    const u32* mg = masks + static_cast<i64>(g) * n_in;
+    const u32* cg = ctrl + static_cast<i64>(g) * n_in;
     auto og = [&](int r) { return out(32 * g + r); };
-    const bool ok = rows <= 8    ? dense_group<W, 8>(v, q, n_win, T, col, store, mg, rows, og)
-                    : rows <= 16 ? dense_group<W, 16>(v, q, n_win, T, col, store, mg, rows, og)
-                                 : dense_group<W, 32>(v, q, n_win, T, col, store, mg, rows, og);
+    const bool ok =
+        rows <= 8    ? dense_group<W, kTable, 8>(v, q, n_win, col, store, cg, tbl, rows, og)
+        : rows <= 16 ? dense_group<W, kTable, 16>(v, q, n_win, col, store, cg, tbl, rows, og)
+                     : dense_group<W, kTable, 32>(v, q, n_win, col, store, cg, tbl, rows, og);
     if (!ok) return false;
   }
   return true;
 }
 
-__device__ __forceinline__ int dense_groups(int n_out) { return (n_out + 31) / 32; }
-
-template <int W>
+template <int W, bool kTable>
 struct DenseBody {
   __device__ __forceinline__ bool compute(const LaunchParams& p, const WindowView& v, i64 q0,
                                           i64 s, i64 c0, int len, int col) const {
@@ -278,14 +345,12 @@ struct DenseBody {
     auto out = [&](int r) {
       return out_block(p.io, s, r >> 3) + static_cast<i64>(r & 7) * p.io.S + c0 + col;
     };
-    return dense_item<W>(v, q0, p.n_in, p.n_out, static_cast<u32>(p.T), col, col < len, masks,
-                         out);
+    return dense_item<W, kTable>(v, q0, p.n_in, p.n_out, col, col < len, masks, out);
   }
 };
 
-template <int W>
+template <int W, bool kTable>
 struct DenseBatchBody {
-  u32 T;   // the launch's tile bytes per strip
   __device__ __forceinline__ int groups(const StripeDesc& d) const {
     return dense_groups(8 * d.n_outblk);
   }
@@ -296,26 +361,27 @@ struct DenseBatchBody {
     auto out = [&](int r) {
       return reinterpret_cast<u8*>(outs[r >> 3]) + static_cast<i64>(r & 7) * d.S + c0 + col;
     };
-    return dense_item<W>(v, q0, 8 * d.n_inblk, 8 * d.n_outblk, T, col, col < len, masks, out);
+    return dense_item<W, kTable>(v, q0, 8 * d.n_inblk, 8 * d.n_outblk, col, col < len, masks,
+                                 out);
   }
 };
 
 // Single launches and batches: kDenseThreads consumer threads and the
-// producer warp; the register cap of three CTAs per SM holds 32
-// accumulators of two words (121 registers), that of two CTAs 32 of four.
-template <int W>
+// producer warp.  Register caps: three CTAs per SM hold 32 accumulators of
+// two words (about 120 registers), two CTAs 32 of four.
+template <int W, bool kTable>
 __global__ void __launch_bounds__(kDenseThreads + 32, W == 4 ? 2 : 3)
     dense_kernel(LaunchParams p, const __grid_constant__ TensorMap tm) {
   extern __shared__ __align__(128) u8 smem[];
-  run_window_pipeline<DenseBody<W>, 4 * W>(p, smem, DenseBody<W>(), &tm);
+  run_window_pipeline<DenseBody<W, kTable>, 4 * W>(p, smem, DenseBody<W, kTable>(), &tm);
 }
 
-template <int W>
+template <int W, bool kTable>
 __global__ void __launch_bounds__(kDenseThreads + 32, W == 4 ? 2 : 3)
     dense_batch_kernel(BatchParams p) {
   extern __shared__ __align__(128) u8 smem[];
-  run_batch_window_pipeline<DenseBatchBody<W>, 4 * W, true>(
-      p, smem, DenseBatchBody<W>{static_cast<u32>(p.T)});
+  run_batch_window_pipeline<DenseBatchBody<W, kTable>, 4 * W, true>(p, smem,
+                                                                    DenseBatchBody<W, kTable>());
 }
 
 // Self-test of the bounded waits: one thread waits, with the pipeline's
@@ -418,29 +484,47 @@ bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int thre
   return true;
 }
 
-// Dense bitmatrix executor: 128 consumer threads and the producer warp, W
-// words per consumer and strip (EC_DENSE_WORDS: 4 or 2).  Four words halve
-// the mask tests per byte: RS(10,4) encode, 256 stripes x 1 MiB, 0.265 of
-// the measured copy bandwidth with two words, 0.365 with four.
+// Dense bitmatrix executor: 128 consumer threads and the producer warp, the
+// table form (EC_DENSE_KIND=mask: the mask form) and W words per consumer
+// and strip (EC_DENSE_WORDS: 2 or 4).  RS(10,4) encode, 256 stripes x 1 MiB,
+// fraction of the measured copy bandwidth: tables 0.521 with two words (3
+// CTAs per SM, bound by shared-memory bandwidth), 0.387 with four (their
+// tables leave room for one CTA per SM); masks 0.265 with two words, 0.366
+// with four (bound by the integer pipe: four words halve the tests per
+// byte).
+bool dense_table() {
+  const char* v = std::getenv("EC_DENSE_KIND");
+  return !(v && std::strcmp(v, "mask") == 0);
+}
+
 int dense_words() {
   const char* v = std::getenv("EC_DENSE_WORDS");
-  return v && *v && std::atoi(v) == 2 ? 2 : 4;
+  if (v && *v) return std::atoi(v) == 2 ? 2 : 4;
+  return dense_table() ? 2 : 4;
 }
 
-size_t dense_smem_bytes(int T) {
-  return 128 + static_cast<size_t>(xk::kWinRing) * kDenseWin * T;
+size_t dense_smem_bytes(int T, bool table) {
+  return 128 + static_cast<size_t>(xk::kWinRing) * kDenseWin * T +
+         (table ? static_cast<size_t>(32) * T : 0);
 }
 
-static const void* dense_kernel_for(int W, bool batch) {
-  if (batch)
-    return W == 4 ? reinterpret_cast<const void*>(&dense_batch_kernel<4>)
-                  : reinterpret_cast<const void*>(&dense_batch_kernel<2>);
-  return W == 4 ? reinterpret_cast<const void*>(&dense_kernel<4>)
-                : reinterpret_cast<const void*>(&dense_kernel<2>);
+static const void* dense_kernel_for(int W, bool table, bool batch) {
+  if (batch) {
+    if (table)
+      return W == 4 ? reinterpret_cast<const void*>(&dense_batch_kernel<4, true>)
+                    : reinterpret_cast<const void*>(&dense_batch_kernel<2, true>);
+    return W == 4 ? reinterpret_cast<const void*>(&dense_batch_kernel<4, false>)
+                  : reinterpret_cast<const void*>(&dense_batch_kernel<2, false>);
+  }
+  if (table)
+    return W == 4 ? reinterpret_cast<const void*>(&dense_kernel<4, true>)
+                  : reinterpret_cast<const void*>(&dense_kernel<2, true>);
+  return W == 4 ? reinterpret_cast<const void*>(&dense_kernel<4, false>)
+                : reinterpret_cast<const void*>(&dense_kernel<2, false>);
 }
 
-int dense_max_ctas_per_sm(int W, bool batch, size_t smem) {
-  const void* k = dense_kernel_for(W, batch);
+int dense_max_ctas_per_sm(int W, bool table, bool batch, size_t smem) {
+  const void* k = dense_kernel_for(W, table, batch);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return 0;
@@ -451,13 +535,14 @@ int dense_max_ctas_per_sm(int W, bool batch, size_t smem) {
   return n;
 }
 
-bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, int grid,
-                  size_t smem, cudaStream_t stream) {
-  if (lp.T != 4 * W * kDenseThreads || lp.win != kDenseWin || lp.n_in % kDenseWin != 0) {
+bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, bool table,
+                  int grid, size_t smem, cudaStream_t stream) {
+  if (lp.T != 4 * W * kDenseThreads || lp.win != kDenseWin || lp.n_in % kDenseWin != 0 ||
+      smem < dense_smem_bytes(lp.T, table)) {
     set_error("dense executor: bad launch shape");
     return false;
   }
-  const void* k = dense_kernel_for(W, false);
+  const void* k = dense_kernel_for(W, table, false);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     set_error("cudaFuncSetAttribute(dense) failed");
@@ -466,10 +551,14 @@ bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, in
   xk::TensorMap map;
   if (tm) map = *tm;
   else std::memset(&map, 0, sizeof(map));
-  if (W == 4)
-    dense_kernel<4><<<grid, kDenseThreads + 32, smem, stream>>>(lp, map);
-  else
-    dense_kernel<2><<<grid, kDenseThreads + 32, smem, stream>>>(lp, map);
+  const dim3 block(kDenseThreads + 32);
+  if (table) {
+    if (W == 4) dense_kernel<4, true><<<grid, block, smem, stream>>>(lp, map);
+    else dense_kernel<2, true><<<grid, block, smem, stream>>>(lp, map);
+  } else {
+    if (W == 4) dense_kernel<4, false><<<grid, block, smem, stream>>>(lp, map);
+    else dense_kernel<2, false><<<grid, block, smem, stream>>>(lp, map);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("dense executor launch failed: ") + cudaGetErrorString(e));
@@ -478,22 +567,26 @@ bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, in
   return true;
 }
 
-bool launch_dense_batch(const xk::BatchParams& bp, int W, int grid, size_t smem,
+bool launch_dense_batch(const xk::BatchParams& bp, int W, bool table, int grid, size_t smem,
                         cudaStream_t stream) {
-  if (bp.T != 4 * W * kDenseThreads || bp.win != kDenseWin) {
+  if (bp.T != 4 * W * kDenseThreads || bp.win != kDenseWin || smem < dense_smem_bytes(bp.T, table)) {
     set_error("dense executor: bad batch launch shape");
     return false;
   }
-  const void* k = dense_kernel_for(W, true);
+  const void* k = dense_kernel_for(W, table, true);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     set_error("cudaFuncSetAttribute(dense batch) failed");
     return false;
   }
-  if (W == 4)
-    dense_batch_kernel<4><<<grid, kDenseThreads + 32, smem, stream>>>(bp);
-  else
-    dense_batch_kernel<2><<<grid, kDenseThreads + 32, smem, stream>>>(bp);
+  const dim3 block(kDenseThreads + 32);
+  if (table) {
+    if (W == 4) dense_batch_kernel<4, true><<<grid, block, smem, stream>>>(bp);
+    else dense_batch_kernel<2, true><<<grid, block, smem, stream>>>(bp);
+  } else {
+    if (W == 4) dense_batch_kernel<4, false><<<grid, block, smem, stream>>>(bp);
+    else dense_batch_kernel<2, false><<<grid, block, smem, stream>>>(bp);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("batched dense executor launch failed: ") + cudaGetErrorString(e));

@@ -159,10 +159,18 @@ bool build_program(int rows, int cols, const uint8_t* A, const PlanOptions& o,
   Slp chains = slp_rows_chains(n_in, R, order);
   Program p;
   p.stats.raw = metrics(chains);
+  // the dense executor's control words (plan.h): bit (r, c) of the
+  // bitmatrix, by input strip and by output strip
   p.masks.assign(static_cast<size_t>((n_out + 31) / 32) * n_in, 0u);
+  p.rowbits.assign(p.masks.size(), 0u);
   for (int r = 0; r < n_out; ++r)
     for (int c = 0; c < n_in; ++c)
-      if (R[r].test(c)) p.masks[static_cast<size_t>(r / 32) * n_in + c] |= 1u << (r % 32);
+      if (R[r].test(c)) {
+        const size_t g = static_cast<size_t>(r / 32) * n_in;
+        const int rr = r % 32;
+        p.masks[g + c] |= 1u << rr;
+        p.rowbits[g + 8 * (c / 8) + rr / 4] |= 1u << (8 * (rr % 4) + c % 8);
+      }
   Slp fused;
   // Two-level program for wide codes (inputs do not fit the registers):
   // groups of partial sums as large as the register budget allows.

@@ -72,6 +72,10 @@ struct Program {
   // g * n_in + c, bit r is bit (32 g + r, c) (output strip 32 g + r reads
   // input strip c); ceil(n_out / 32) groups
   std::vector<uint32_t> masks;
+  // row words of the dense executor's table form: word g * n_in + 8 w + j
+  // holds the bits of window w (input strips 8 w .. 8 w + 7, bit i for strip
+  // 8 w + i) of output strips 32 g + 4 j .. 32 g + 4 j + 3, one byte each
+  std::vector<uint32_t> rowbits;
   PipelineStats stats;
   Slp fused;                 // single-assignment fused program
   Schedule sched;            // GPU schedule of `fused`
@@ -80,7 +84,8 @@ struct Program {
   // Empty: inputs preloaded (narrow) or read at every use (wide).
   std::vector<int> load_group;
   uint64_t hash = 0;         // content hash of the fused program
-  // device copy of `chunks` followed by `masks` (owned; freed by the plan)
+  // device copy of `chunks` followed by `masks` and `rowbits` (owned; freed
+  // by the plan)
   uint16_t* d_code = nullptr;
   // compiled tier (set once a straight-line kernel exists for this program)
   void* jit = nullptr;

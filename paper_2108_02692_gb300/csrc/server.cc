@@ -49,6 +49,7 @@ struct Req {
   void* mod = nullptr;          // compiled module that runs it, or nullptr = the dense executor
   std::vector<uint64_t> ptrs;
   long long S = 0, tiles = 0;
+  int T = 0;                    // tile bytes per strip its items were counted in
   size_t bytes = 0;
   long long bytes_in = 0, bytes_out = 0;
   Clock::time_point t0;
@@ -102,7 +103,8 @@ struct ec_server {
   int error = EC_OK;
   std::thread th;
   ec_server_stats stats{};
-  std::map<std::tuple<void*, int, int>, std::pair<size_t, int>> shapes;
+  // launch shapes by (module, max_in, max_slots, dense words, dense tables)
+  std::map<std::tuple<void*, int, int, int, bool>, std::pair<size_t, int>> shapes;
   // background compilation of programs that arrive without a compiled module
   bool background_compile = true;
   std::thread compiler;
@@ -167,8 +169,9 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueued) {
   *enqueued = false;
   xorec::TraceRange trace_("xorec serve dispatch");
-  // group by launch target: compiled module of this block size, or the dense executor
-  auto target = [&](const Req& r) -> void* { return r.mod; };
+  // group by launch target: compiled module of this block size, or the dense
+  // executor (by the tile its items were counted in)
+  auto target = [&](const Req& r) { return std::make_pair(r.mod, r.T); };
   std::stable_sort(reqs.begin(), reqs.end(),
                    [&](const Req& a, const Req& b) { return target(a) < target(b); });
   size_t n_blocks = 0, n_launches = 0;
@@ -176,6 +179,7 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     n_blocks += reqs[i].ptrs.size();
     if (i == 0 || target(reqs[i]) != target(reqs[i - 1])) ++n_launches;
   }
+  const bool dense_tbl = xorec::dense_table();
   const size_t desc_off = align_up(n_launches * sizeof(xk::u64), 64);
   const size_t block_off = desc_off + reqs.size() * sizeof(xk::StripeDesc);
   const size_t bytes = block_off + n_blocks * sizeof(xk::u64);
@@ -191,11 +195,9 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
   size_t off = 0;
   for (size_t i = 0; i < reqs.size(); ++i) {
     const Req& r = reqs[i];
-    void* mod = target(r);
-    if (launches.empty() || launches.back().mod != mod)
-      launches.push_back(L{mod, xorec::launch_threads(mod),
-                           xorec::launch_tile(mod, false, xorec::launch_threads(mod)),
-                           static_cast<int>(i), 0, 0, 0, 0});
+    void* mod = r.mod;
+    if (launches.empty() || launches.back().mod != mod || launches.back().T != r.T)
+      launches.push_back(L{mod, xorec::launch_threads(mod), r.T, static_cast<int>(i), 0, 0, 0, 0});
     L& l = launches.back();
     xk::StripeDesc& d = h_descs[i];
     std::memset(&d, 0, sizeof(d));
@@ -227,13 +229,14 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     return EC_ECUDA;
   for (size_t li = 0; li < launches.size(); ++li) {
     const L& l = launches[li];
-    auto key = std::make_tuple(l.mod, l.max_in, l.max_slots);
+    const int dense_w = l.T / (4 * xorec::kDenseThreads);
+    auto key = std::make_tuple(l.mod, l.max_in, l.max_slots, dense_w, dense_tbl);
     auto it = sv->shapes.find(key);
     if (it == sv->shapes.end()) {
       size_t smem = 0;
       int per_sm = 1;
       if (!xorec::batch_launch_shape(l.mod, false, l.max_in, l.max_slots, l.threads,
-                                     sv->di.smem_optin, &smem, &per_sm))
+                                     sv->di.smem_optin, &smem, &per_sm, dense_w, dense_tbl))
         return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
       it = sv->shapes.emplace(key, std::make_pair(smem, per_sm)).first;
     }
@@ -251,8 +254,8 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     bp.local_status = sl.d_status;
     const long long full = static_cast<long long>(sv->di.sms) * it->second.second;
     const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(full, l.items)));
-    const bool ok =
-        xorec::batch_launch(l.mod, false, bp, l.threads, grid, it->second.first, sl.st);
+    const bool ok = xorec::batch_launch(l.mod, false, bp, l.threads, grid, it->second.first,
+                                        sl.st, dense_w, dense_tbl);
     if (!ok) return EC_ECUDA;
   }
   if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) {
@@ -499,9 +502,9 @@ ec_status ec_server_submit(ec_server* sv, const ec_job* job, uint64_t* ticket) {
     }
   }
   const size_t B = job->block_bytes;
-  const int T = xorec::launch_tile(r.mod, false, xorec::launch_threads(r.mod));
+  r.T = xorec::launch_tile(r.mod, false, xorec::launch_threads(r.mod));
   r.S = static_cast<long long>(B / 8);
-  r.tiles = (r.S + T - 1) / T;
+  r.tiles = (r.S + r.T - 1) / r.T;
   r.bytes_in = static_cast<long long>(r.prog->n_in / 8) * static_cast<long long>(B);
   r.bytes_out = static_cast<long long>(r.prog->n_out / 8) * static_cast<long long>(B);
   r.bytes = static_cast<size_t>(r.bytes_in + r.bytes_out);

@@ -1,8 +1,9 @@
 """The dense bitmatrix executor (EC_EXEC_DENSE, and EC_EXEC_AUTO's tier for
 programs without a compiled kernel) against the oracle, bit for bit: output
 strip r is the XOR of the input strips whose bit (r, c) of the bitmatrix is
-set (Sec. 1, property (ii)).  Covers both widths of a consumer's column
-(two and four words), more than 32 output strips (groups of rows), inputs
+set (Sec. 1, property (ii)).  Covers both forms (column masks, and subset
+tables of four strips), both widths of a consumer's column (two and four
+words), more than 32 output strips (groups of rows), inputs
 streamed by tensor copies and by per-strip copies, single launches, batches
 of mixed codes, the serving loop before any module exists, and a code of
 1024 input strips."""
@@ -38,14 +39,16 @@ def _codeword(k, m, B, cfg, stripe=0):
     return data + oracle.encode(oracle.cauchy(k, m), data)
 
 
+@pytest.mark.parametrize("kind", ["mask", "table"])
 @pytest.mark.parametrize("words", ["2", "4"])
 @pytest.mark.parametrize("tensor", ["1", "0"], ids=["tensor-copies", "strip-copies"])
 @pytest.mark.parametrize("k,m", [(10, 4), (3, 5), (24, 8)])
-def test_strided_encode(k, m, words, tensor, monkeypatch):
+def test_strided_encode(k, m, words, tensor, kind, monkeypatch):
     """ec_encode_strided: windows of one block by one tiled tensor copy (8- or
     4-byte elements) or by eight 1-D copies; strips of 2064 B end in a ragged
     tile; RS(3,5) and RS(24,8) have 40 and 64 output strips (two groups)."""
     monkeypatch.setenv("EC_DENSE_WORDS", words)
+    monkeypatch.setenv("EC_DENSE_KIND", kind)
     monkeypatch.setenv("EC_TMA_TENSOR", tensor)
     B, n = 8 * 2064, 3
     data = np.stack([np.stack([synth.block_bytes(111, s, j, B) for j in range(k)])
@@ -67,11 +70,13 @@ def test_strided_encode(k, m, words, tensor, monkeypatch):
         xo.ec_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("kind", ["mask", "table"])
 @pytest.mark.parametrize("words", ["2", "4"])
-def test_decode_more_than_32_rows(words, monkeypatch):
+def test_decode_more_than_32_rows(words, kind, monkeypatch):
     """RS(12,8): every set of 5 to 8 erasures among a spread sample (40 to 64
     output strips, two groups of rows), block pointer tables."""
     monkeypatch.setenv("EC_DENSE_WORDS", words)
+    monkeypatch.setenv("EC_DENSE_KIND", kind)
     k, m, B = 12, 8, 8 * 1040
     blocks = _codeword(k, m, B, 112)
     d = [torch.from_numpy(b).cuda() for b in blocks]
@@ -91,10 +96,12 @@ def test_decode_more_than_32_rows(words, monkeypatch):
         xo.ec_plan_destroy(plan)
 
 
-def test_every_rs6_3_pattern_four_words(monkeypatch):
+@pytest.mark.parametrize("kind", ["mask", "table"])
+def test_every_rs6_3_pattern_four_words(kind, monkeypatch):
     """All 129 erasure sets of RS(6,3) with four words per column (2 KiB
     tiles): strips of 4224 B give two full tiles and a ragged one."""
     monkeypatch.setenv("EC_DENSE_WORDS", "4")
+    monkeypatch.setenv("EC_DENSE_KIND", kind)
     k, m, B = 6, 3, 8 * 4224
     blocks = _codeword(k, m, B, 113)
     d = [torch.from_numpy(b).cuda() for b in blocks]
@@ -113,13 +120,15 @@ def test_every_rs6_3_pattern_four_words(monkeypatch):
         xo.ec_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("kind", ["mask", "table"])
 @pytest.mark.parametrize("words", ["2", "4"])
 @pytest.mark.parametrize("tensor", ["1", "0"], ids=["tensor-copies", "strip-copies"])
-def test_batch_of_mixed_codes(words, tensor, monkeypatch):
+def test_batch_of_mixed_codes(words, tensor, kind, monkeypatch):
     """One batch with EC_EXEC_DENSE: encodes and decodes of four codes (8 to
     64 output strips) and five block sizes in one launch, each item's windows
     and groups following its stripe; run twice (the queue resets)."""
     monkeypatch.setenv("EC_DENSE_WORDS", words)
+    monkeypatch.setenv("EC_DENSE_KIND", kind)
     monkeypatch.setenv("EC_TMA_TENSOR", tensor)
     codes = [(4, 2), (10, 4), (3, 5), (12, 8)]
     plans = {c: xo.ec_plan_create(*c) for c in codes}
