@@ -56,7 +56,7 @@ struct Launch {
                                        // executor (the interpreter if `interp`)
   bool interp = false;
   int dense_w = 4;                     // the dense executor's words per column
-  bool dense_tbl = true;               // and form
+  int dense_form = 1;                  // and form (table)
   int threads = 128;                   // threads per CTA that own a column
   int T = 512;                         // tile bytes per strip
   int stripe_begin = 0, n_stripes = 0; // the launch's stripes in the descriptor array
@@ -225,15 +225,15 @@ int launch_tile(void* mod, bool interp, int threads) {
   return mod || interp ? 4 * threads : 4 * dense_words() * kDenseThreads;
 }
 
-// One batched launch on its target (dense_w, dense_tbl: the dense
+// One batched launch on its target (dense_w, dense_form: the dense
 // executor's form its shape was computed for).
 bool batch_launch(void* mod, bool interp, const xk::BatchParams& bp, int threads, int grid,
-                  size_t smem, cudaStream_t st, int dense_w, bool dense_tbl) {
+                  size_t smem, cudaStream_t st, int dense_w, int dense_form) {
   if (mod) return jit_module_launch(mod, bp, grid, smem, st);
   if (interp) return launch_interp_batch(bp, threads, grid, smem, st);
   xk::BatchParams dp = bp;
   dp.win = kDenseWin;
-  return launch_dense_batch(dp, dense_w, dense_tbl, grid, smem, st);
+  return launch_dense_batch(dp, dense_w, dense_form, grid, smem, st);
 }
 
 // A program of one group of rows that the windowed pipeline runs (its
@@ -333,14 +333,14 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
 // executor, or interpreter).
 bool batch_launch_shape(void* mod, bool interp, int max_in, int max_slots, int threads,
                         size_t smem_optin, size_t* smem, int* per_sm, int dense_w,
-                        bool dense_tbl) {
+                        int dense_form) {
   const int T = 4 * threads;
   if (!mod && !interp) {
     // the dense executor: a ring of windows of kDenseWin strips (and its
     // tables)
-    *smem = dense_smem_bytes(4 * dense_w * kDenseThreads, dense_tbl);
+    *smem = dense_smem_bytes(4 * dense_w * kDenseThreads, dense_form);
     if (*smem > smem_optin) return false;
-    *per_sm = std::max(1, dense_max_ctas_per_sm(dense_w, dense_tbl, true, *smem));
+    *per_sm = std::max(1, dense_max_ctas_per_sm(dense_w, dense_form, true, *smem));
     return true;
   }
   int win = 0, n_win = 0;
@@ -464,7 +464,7 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
       L.mod = mod;
       L.interp = !mod && executor == EC_EXEC_INTERP;
       L.dense_w = xorec::dense_words();
-      L.dense_tbl = xorec::dense_table();
+      L.dense_form = xorec::dense_form();
       L.threads = L.interp ? batch_threads() : xorec::launch_threads(mod);
       b->launches.push_back(L);
     }
@@ -623,7 +623,8 @@ ec_status ec_batch_create(const ec_job* jobs, int n_jobs, int executor, ec_batch
     int per_sm = 1;
     if (L.mod) ++n_modules;
     if (!xorec::batch_launch_shape(L.mod, L.interp, L.max_in, L.max_slots, L.threads,
-                                   di.smem_optin, &L.smem, &per_sm, L.dense_w, L.dense_tbl)) {
+                                   di.smem_optin, &L.smem, &per_sm, L.dense_w,
+                                   L.dense_form)) {
       free_batch(b);
       return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
     }
@@ -714,7 +715,7 @@ ec_status ec_batch_run(ec_batch* b, void* stream) {
     bp.status = b->status;
     bp.local_status = b->d_status;
     const bool ok = xorec::batch_launch(L.mod, L.interp, bp, L.threads, L.grid, L.smem, st,
-                                        L.dense_w, L.dense_tbl);
+                                        L.dense_w, L.dense_form);
     if (!ok) return EC_ECUDA;
   }
   if (fan) {

@@ -345,13 +345,13 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   }
   const bool dense = !compiled && executor != EC_EXEC_INTERP;
   int dense_w = 0;
-  bool dense_tbl = false;
+  int dense_form = 0;
   if (dense) {
     // the dense bitmatrix executor: windows of one block stream through a
     // ring; all output rows' accumulators in registers, in groups of 32
     if (!ensure_device_code(p)) return false;
     dense_w = dense_words();
-    dense_tbl = dense_table();
+    dense_form = xorec::dense_form();
     lp.T = 4 * dense_w * kDenseThreads;
     lp.win = kDenseWin;
     lp.n_win = p->n_in / kDenseWin;
@@ -359,8 +359,8 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
     lp.code = p->d_code;
     lp.code_len = static_cast<int>(p->chunks.size() / 8);
     nstage = 1;
-    smem = dense_smem_bytes(lp.T, dense_tbl);
-    per_sm = dense_max_ctas_per_sm(dense_w, dense_tbl, false, smem);
+    smem = dense_smem_bytes(lp.T, dense_form);
+    per_sm = dense_max_ctas_per_sm(dense_w, dense_form, false, smem);
   } else if (!compiled) {
     if (!ensure_device_code(p)) return false;
     // one stage (more resident CTAs hide more latency than a second stage
@@ -402,7 +402,8 @@ bool launch_program(Program* p, const xk::IoDesc& io, int executor, cudaStream_t
   if (dense) {
     xk::TensorMap tm;
     lp.tmap = input_tensor_map(io, p->n_in, lp.T, &tm, kDenseWin);
-    return launch_dense(lp, lp.tmap ? &tm : nullptr, dense_w, dense_tbl, static_cast<int>(grid),
+    return launch_dense(lp, lp.tmap ? &tm : nullptr, dense_w, dense_form,
+                        static_cast<int>(grid),
                         smem, stream);
   }
   xk::TensorMap tm;

@@ -233,26 +233,34 @@ __global__ void __launch_bounds__(256, 1) interp_batch_kernel(BatchParams p) {
 using xorec::kDenseThreads;
 using xorec::kDenseWin;
 
-template <int W, bool kTable>
-struct DenseForm {
+// Forms (a third, tables for 24 rows of a group and masks for 8, so that
+// the masks' integer work would run beside the tables' shared-memory
+// traffic, measured 0.417 against 0.521 for tables alone and was dropped).
+enum { kMaskForm = 0, kTableForm = 1 };
+
+template <int W>
+struct DenseTile {
   static constexpr u32 T = 4u * W * kDenseThreads;   // tile bytes per strip
 };
 
 // One group of kRows output rows (rows <= kRows of them real): every window
-// of the item, then the stores.  q: the CTA's phase counter; ctrl: the
-// group's masks (mask form) or row words (table form); tbl: shared address
-// of this consumer's column in entry 0 of table 0 (entries T bytes apart).
-template <int W, bool kTable, int kRows, class OutAddr>
+// of the item, then the stores.  q: the CTA's phase counter; masks, rowb: the
+// group's masks and row words; tbl: shared address of this consumer's column
+// in entry 0 of table 0 (entries T bytes apart).
+template <int W, int kForm, int kRows, class OutAddr>
 __device__ __forceinline__ bool dense_group(const WindowView& v, i64& q, int n_win, int col,
-                                            bool store, const u32* __restrict__ ctrl, u32 tbl,
-                                            int rows, const OutAddr& out) {
-  constexpr u32 T = DenseForm<W, kTable>::T;
+                                            bool store, const u32* __restrict__ masks,
+                                            const u32* __restrict__ rowb, u32 tbl, int rows,
+                                            const OutAddr& out) {
+  constexpr u32 T = DenseTile<W>::T;
+  // rows [0, kTab) from the tables, [kTab, kRows) from the masks
+  constexpr int kTab = kForm == kMaskForm ? 0 : kRows;
   Words<W> acc[kRows];
 #pragma unroll
   for (int r = 0; r < kRows; ++r)
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[r].v[w] = 0;
-  if constexpr (kTable) {
+  if constexpr (kTab > 0) {
     Words<W> z;
 #pragma unroll
     for (int w = 0; w < W; ++w) z.v[w] = 0;
@@ -262,45 +270,51 @@ __device__ __forceinline__ bool dense_group(const WindowView& v, i64& q, int n_w
   for (int w = 0; w < n_win; ++w, ++q) {
     const u8* slot = v.begin(q);
     if (!slot) return false;
-    const uint4 c0 = __ldg(reinterpret_cast<const uint4*>(ctrl + kDenseWin * w));
-    const uint4 c1 = __ldg(reinterpret_cast<const uint4*>(ctrl + kDenseWin * w) + 1);
-    const u32 cw[kDenseWin] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    u32 mk[kDenseWin], rb[kDenseWin];
+    if constexpr (kTab < kRows) {
+      const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(masks + kDenseWin * w));
+      const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(masks + kDenseWin * w) + 1);
+      mk[0] = m0.x; mk[1] = m0.y; mk[2] = m0.z; mk[3] = m0.w;
+      mk[4] = m1.x; mk[5] = m1.y; mk[6] = m1.z; mk[7] = m1.w;
+    }
+    if constexpr (kTab > 0) {
+      const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(rowb + kDenseWin * w));
+      const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(rowb + kDenseWin * w) + 1);
+      rb[0] = r0.x; rb[1] = r0.y; rb[2] = r0.z; rb[3] = r0.w;
+      rb[4] = r1.x; rb[5] = r1.y; rb[6] = r1.z; rb[7] = r1.w;
+    }
     const u32 a = smem_addr(slot) + static_cast<u32>(col);
-    if constexpr (!kTable) {
+    Words<W> x[kDenseWin];
 #pragma unroll
-      for (int c = 0; c < kDenseWin; ++c) {
-        const Words<W> x = lds<W>(a + static_cast<u32>(c) * T);
-#pragma unroll
-        for (int r = 0; r < kRows; ++r)
-          if ((cw[c] >> r) & 1u) xor_in(acc[r], x);
-      }
-      v.end(q);
-    } else {
+    for (int c = 0; c < kDenseWin; ++c) x[c] = lds<W>(a + static_cast<u32>(c) * T);
+    v.end(q);   // the window now lives in registers (and the tables)
+    if constexpr (kTab > 0) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        Words<W> x[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) x[i] = lds<W>(a + static_cast<u32>(4 * h + i) * T);
-        Words<W> cur = x[0];
+        Words<W> cur = x[4 * h];
         sts<W>(tbl + (16 * h + 1) * T, cur);
 #pragma unroll
         for (int i = 2; i < 16; ++i) {
           // Gray code i ^ (i >> 1) differs from the previous one in the
           // lowest set bit of i
-          xor_in(cur, x[(i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : 3]);
+          xor_in(cur, x[4 * h + ((i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : 3)]);
           sts<W>(tbl + (16 * h + (i ^ (i >> 1))) * T, cur);
         }
       }
-      v.end(q);   // the window now lives in this consumer's tables
 #pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const u32 b = (cw[r >> 2] >> (8 * (r & 3))) & 0xffu;
+      for (int r = 0; r < kTab; ++r) {
+        const u32 b = (rb[r >> 2] >> (8 * (r & 3))) & 0xffu;
         const Words<W> lo = lds<W>(tbl + (b & 15u) * T);
         const Words<W> hi = lds<W>(tbl + (16u + (b >> 4)) * T);
 #pragma unroll
         for (int k = 0; k < W; ++k) acc[r].v[k] ^= lo.v[k] ^ hi.v[k];
       }
     }
+#pragma unroll
+    for (int c = 0; c < kDenseWin; ++c)
+#pragma unroll
+      for (int r = kTab; r < kRows; ++r)
+        if ((mk[c] >> r) & 1u) xor_in(acc[r], x[c]);
   }
   if (store) {
 #pragma unroll
@@ -313,31 +327,35 @@ __device__ __forceinline__ bool dense_group(const WindowView& v, i64& q, int n_w
 __device__ __forceinline__ int dense_groups(int n_out) { return (n_out + 31) / 32; }
 
 // All groups of one item.  n_in: input strips (a multiple of kDenseWin);
-// masks: the program's control words.
-template <int W, bool kTable, class OutAddr>
+// masks: the program's control words (masks, then row words).
+template <int W, int kForm, class OutAddr>
 __device__ __forceinline__ bool dense_item(const WindowView& v, i64 q0, int n_in, int n_out,
                                            int col, bool store, const u32* masks,
                                            const OutAddr& out) {
-  constexpr u32 T = DenseForm<W, kTable>::T;
+  constexpr u32 T = DenseTile<W>::T;
   i64 q = q0;
   const int n_win = n_in / kDenseWin;
-  const u32* ctrl = kTable ? masks + static_cast<i64>(dense_groups(n_out)) * n_in : masks;
+  const u32* rowb = masks + static_cast<i64>(dense_groups(n_out)) * n_in;
   const u32 tbl = smem_addr(v.ring) + static_cast<u32>(xk::kWinRing * kDenseWin) * T +
                   static_cast<u32>(col);
   for (int g = 0; 32 * g < n_out; ++g) {
     const int rows = n_out - 32 * g < 32 ? n_out - 32 * g : 32;
-    const u32* cg = ctrl + static_cast<i64>(g) * n_in;
+    const i64 off = static_cast<i64>(g) * n_in;
     auto og = [&](int r) { return out(32 * g + r); };
     const bool ok =
-        rows <= 8    ? dense_group<W, kTable, 8>(v, q, n_win, col, store, cg, tbl, rows, og)
-        : rows <= 16 ? dense_group<W, kTable, 16>(v, q, n_win, col, store, cg, tbl, rows, og)
-                     : dense_group<W, kTable, 32>(v, q, n_win, col, store, cg, tbl, rows, og);
+        rows <= 8 ? dense_group<W, kForm, 8>(v, q, n_win, col, store, masks + off, rowb + off, tbl,
+                                             rows, og)
+        : rows <= 16
+            ? dense_group<W, kForm, 16>(v, q, n_win, col, store, masks + off, rowb + off, tbl,
+                                        rows, og)
+            : dense_group<W, kForm, 32>(v, q, n_win, col, store, masks + off, rowb + off, tbl,
+                                        rows, og);
     if (!ok) return false;
   }
   return true;
 }
 
-template <int W, bool kTable>
+template <int W, int kForm>
 struct DenseBody {
   __device__ __forceinline__ bool compute(const LaunchParams& p, const WindowView& v, i64 q0,
                                           i64 s, i64 c0, int len, int col) const {
@@ -345,11 +363,11 @@ struct DenseBody {
     auto out = [&](int r) {
       return out_block(p.io, s, r >> 3) + static_cast<i64>(r & 7) * p.io.S + c0 + col;
     };
-    return dense_item<W, kTable>(v, q0, p.n_in, p.n_out, col, col < len, masks, out);
+    return dense_item<W, kForm>(v, q0, p.n_in, p.n_out, col, col < len, masks, out);
   }
 };
 
-template <int W, bool kTable>
+template <int W, int kForm>
 struct DenseBatchBody {
   __device__ __forceinline__ int groups(const StripeDesc& d) const {
     return dense_groups(8 * d.n_outblk);
@@ -361,27 +379,27 @@ struct DenseBatchBody {
     auto out = [&](int r) {
       return reinterpret_cast<u8*>(outs[r >> 3]) + static_cast<i64>(r & 7) * d.S + c0 + col;
     };
-    return dense_item<W, kTable>(v, q0, 8 * d.n_inblk, 8 * d.n_outblk, col, col < len, masks,
-                                 out);
+    return dense_item<W, kForm>(v, q0, 8 * d.n_inblk, 8 * d.n_outblk, col, col < len, masks,
+                                out);
   }
 };
 
 // Single launches and batches: kDenseThreads consumer threads and the
 // producer warp.  Register caps: three CTAs per SM hold 32 accumulators of
 // two words (about 120 registers), two CTAs 32 of four.
-template <int W, bool kTable>
+template <int W, int kForm>
 __global__ void __launch_bounds__(kDenseThreads + 32, W == 4 ? 2 : 3)
     dense_kernel(LaunchParams p, const __grid_constant__ TensorMap tm) {
   extern __shared__ __align__(128) u8 smem[];
-  run_window_pipeline<DenseBody<W, kTable>, 4 * W>(p, smem, DenseBody<W, kTable>(), &tm);
+  run_window_pipeline<DenseBody<W, kForm>, 4 * W>(p, smem, DenseBody<W, kForm>(), &tm);
 }
 
-template <int W, bool kTable>
+template <int W, int kForm>
 __global__ void __launch_bounds__(kDenseThreads + 32, W == 4 ? 2 : 3)
     dense_batch_kernel(BatchParams p) {
   extern __shared__ __align__(128) u8 smem[];
-  run_batch_window_pipeline<DenseBatchBody<W, kTable>, 4 * W, true>(p, smem,
-                                                                    DenseBatchBody<W, kTable>());
+  run_batch_window_pipeline<DenseBatchBody<W, kForm>, 4 * W, true>(p, smem,
+                                                                   DenseBatchBody<W, kForm>());
 }
 
 // Self-test of the bounded waits: one thread waits, with the pipeline's
@@ -485,48 +503,53 @@ bool launch_interp(const xk::LaunchParams& lp, const xk::TensorMap* tm, int thre
 }
 
 // Dense bitmatrix executor: 128 consumer threads and the producer warp, the
-// table form (EC_DENSE_KIND=mask: the mask form) and W words per consumer
-// and strip (EC_DENSE_WORDS: 2 or 4).  RS(10,4) encode, 256 stripes x 1 MiB,
+// form (EC_DENSE_KIND: table or mask) and W words per consumer and
+// strip (EC_DENSE_WORDS: 2 or 4).  RS(10,4) encode, 256 stripes x 1 MiB,
 // fraction of the measured copy bandwidth: tables 0.521 with two words (3
 // CTAs per SM, bound by shared-memory bandwidth), 0.387 with four (their
 // tables leave room for one CTA per SM); masks 0.265 with two words, 0.366
 // with four (bound by the integer pipe: four words halve the tests per
 // byte).
-bool dense_table() {
+int dense_form() {
   const char* v = std::getenv("EC_DENSE_KIND");
-  return !(v && std::strcmp(v, "mask") == 0);
+  return v && std::strcmp(v, "mask") == 0 ? kMaskForm : kTableForm;
 }
 
 int dense_words() {
   const char* v = std::getenv("EC_DENSE_WORDS");
   if (v && *v) return std::atoi(v) == 2 ? 2 : 4;
-  return dense_table() ? 2 : 4;
+  return dense_form() == kMaskForm ? 4 : 2;
 }
 
-size_t dense_smem_bytes(int T, bool table) {
+size_t dense_smem_bytes(int T, int form) {
   return 128 + static_cast<size_t>(xk::kWinRing) * kDenseWin * T +
-         (table ? static_cast<size_t>(32) * T : 0);
+         (form != kMaskForm ? static_cast<size_t>(32) * T : 0);
 }
 
-static const void* dense_kernel_for(int W, bool table, bool batch) {
-  if (batch) {
-    if (table)
-      return W == 4 ? reinterpret_cast<const void*>(&dense_batch_kernel<4, true>)
-                    : reinterpret_cast<const void*>(&dense_batch_kernel<2, true>);
-    return W == 4 ? reinterpret_cast<const void*>(&dense_batch_kernel<4, false>)
-                  : reinterpret_cast<const void*>(&dense_batch_kernel<2, false>);
-  }
-  if (table)
-    return W == 4 ? reinterpret_cast<const void*>(&dense_kernel<4, true>)
-                  : reinterpret_cast<const void*>(&dense_kernel<2, true>);
-  return W == 4 ? reinterpret_cast<const void*>(&dense_kernel<4, false>)
-                : reinterpret_cast<const void*>(&dense_kernel<2, false>);
+namespace {
+
+template <int W, int kForm>
+struct DenseEntry {
+  static const void* single() { return reinterpret_cast<const void*>(&dense_kernel<W, kForm>); }
+  static const void* batch() { return reinterpret_cast<const void*>(&dense_batch_kernel<W, kForm>); }
+};
+
+const void* dense_kernel_for(int W, int form, bool batch) {
+  static const void* const table[2][2][2] = {
+      {{DenseEntry<2, kMaskForm>::single(), DenseEntry<2, kMaskForm>::batch()},
+       {DenseEntry<2, kTableForm>::single(), DenseEntry<2, kTableForm>::batch()}},
+      {{DenseEntry<4, kMaskForm>::single(), DenseEntry<4, kMaskForm>::batch()},
+       {DenseEntry<4, kTableForm>::single(), DenseEntry<4, kTableForm>::batch()}}};
+  if (form != kMaskForm && form != kTableForm) return nullptr;
+  return table[W == 4 ? 1 : 0][form][batch ? 1 : 0];
 }
 
-int dense_max_ctas_per_sm(int W, bool table, bool batch, size_t smem) {
-  const void* k = dense_kernel_for(W, table, batch);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess)
+}  // namespace
+
+int dense_max_ctas_per_sm(int W, int form, bool batch, size_t smem) {
+  const void* k = dense_kernel_for(W, form, batch);
+  if (!k || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem)) != cudaSuccess)
     return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kDenseThreads + 32, smem) !=
@@ -535,14 +558,14 @@ int dense_max_ctas_per_sm(int W, bool table, bool batch, size_t smem) {
   return n;
 }
 
-bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, bool table,
+bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, int form,
                   int grid, size_t smem, cudaStream_t stream) {
-  if (lp.T != 4 * W * kDenseThreads || lp.win != kDenseWin || lp.n_in % kDenseWin != 0 ||
-      smem < dense_smem_bytes(lp.T, table)) {
+  const void* k = dense_kernel_for(W, form, false);
+  if (!k || lp.T != 4 * W * kDenseThreads || lp.win != kDenseWin || lp.n_in % kDenseWin != 0 ||
+      smem < dense_smem_bytes(lp.T, form)) {
     set_error("dense executor: bad launch shape");
     return false;
   }
-  const void* k = dense_kernel_for(W, table, false);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     set_error("cudaFuncSetAttribute(dense) failed");
@@ -551,44 +574,37 @@ bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, bo
   xk::TensorMap map;
   if (tm) map = *tm;
   else std::memset(&map, 0, sizeof(map));
-  const dim3 block(kDenseThreads + 32);
-  if (table) {
-    if (W == 4) dense_kernel<4, true><<<grid, block, smem, stream>>>(lp, map);
-    else dense_kernel<2, true><<<grid, block, smem, stream>>>(lp, map);
-  } else {
-    if (W == 4) dense_kernel<4, false><<<grid, block, smem, stream>>>(lp, map);
-    else dense_kernel<2, false><<<grid, block, smem, stream>>>(lp, map);
-  }
-  const cudaError_t e = cudaGetLastError();
+  xk::LaunchParams lpc = lp;
+  void* args[] = {&lpc, &map};
+  const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kDenseThreads + 32), args, smem,
+                                         stream);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     set_error(std::string("dense executor launch failed: ") + cudaGetErrorString(e));
     return false;
   }
   return true;
 }
 
-bool launch_dense_batch(const xk::BatchParams& bp, int W, bool table, int grid, size_t smem,
+bool launch_dense_batch(const xk::BatchParams& bp, int W, int form, int grid, size_t smem,
                         cudaStream_t stream) {
-  if (bp.T != 4 * W * kDenseThreads || bp.win != kDenseWin || smem < dense_smem_bytes(bp.T, table)) {
+  const void* k = dense_kernel_for(W, form, true);
+  if (!k || bp.T != 4 * W * kDenseThreads || bp.win != kDenseWin ||
+      smem < dense_smem_bytes(bp.T, form)) {
     set_error("dense executor: bad batch launch shape");
     return false;
   }
-  const void* k = dense_kernel_for(W, table, true);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess) {
     set_error("cudaFuncSetAttribute(dense batch) failed");
     return false;
   }
-  const dim3 block(kDenseThreads + 32);
-  if (table) {
-    if (W == 4) dense_batch_kernel<4, true><<<grid, block, smem, stream>>>(bp);
-    else dense_batch_kernel<2, true><<<grid, block, smem, stream>>>(bp);
-  } else {
-    if (W == 4) dense_batch_kernel<4, false><<<grid, block, smem, stream>>>(bp);
-    else dense_batch_kernel<2, false><<<grid, block, smem, stream>>>(bp);
-  }
-  const cudaError_t e = cudaGetLastError();
+  xk::BatchParams bpc = bp;
+  void* args[] = {&bpc};
+  const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kDenseThreads + 32), args, smem,
+                                         stream);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     set_error(std::string("batched dense executor launch failed: ") + cudaGetErrorString(e));
     return false;
   }

@@ -126,12 +126,12 @@ bool launch_interp_batch(const xk::BatchParams& bp, int threads, int grid, size_
 constexpr int kDenseThreads = 128;
 constexpr int kDenseWin = 8;
 int dense_words();
-bool dense_table();
-size_t dense_smem_bytes(int T, bool table);
-int dense_max_ctas_per_sm(int W, bool table, bool batch, size_t smem);
-bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, bool table,
+int dense_form();
+size_t dense_smem_bytes(int T, int form);
+int dense_max_ctas_per_sm(int W, int form, bool batch, size_t smem);
+bool launch_dense(const xk::LaunchParams& lp, const xk::TensorMap* tm, int W, int form,
                   int grid, size_t smem, cudaStream_t stream);
-bool launch_dense_batch(const xk::BatchParams& bp, int W, bool table, int grid, size_t smem,
+bool launch_dense_batch(const xk::BatchParams& bp, int W, int form, int grid, size_t smem,
                         cudaStream_t stream);
 
 // Compiled tier (jit.cc).
@@ -208,7 +208,7 @@ ec_status resolve_job(const ec_job& j, Program** prog, std::vector<int>* er,
 int launch_threads(void* mod);
 int launch_tile(void* mod, bool interp, int threads);
 bool batch_launch(void* mod, bool interp, const xk::BatchParams& bp, int threads, int grid,
-                  size_t smem, cudaStream_t st, int dense_w, bool dense_tbl);
+                  size_t smem, cudaStream_t st, int dense_w, int dense_form);
 // Launch shape of a plan's batch modules for programs of n_in input strips:
 // the autotuner's (or ec_plan_set_launch's) shape, else the defaults.
 int plan_module_threads(const ec_plan* p, int n_in);
@@ -217,7 +217,7 @@ ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want
                           int* built);
 bool batch_launch_shape(void* mod, bool interp, int max_in, int max_slots, int threads,
                         size_t smem_optin, size_t* smem, int* per_sm, int dense_w,
-                        bool dense_tbl);
+                        int dense_form);
 int batch_ranges(long long n_items, int sms, int per_sm, int chunk, int max_in, bool dense);
 // Split a launch's items into n_ranges contiguous ranges (BatchParams).
 void set_ranges(xk::BatchParams* bp, long long n_items, int n_ranges);

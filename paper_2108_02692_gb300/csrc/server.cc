@@ -103,8 +103,8 @@ struct ec_server {
   int error = EC_OK;
   std::thread th;
   ec_server_stats stats{};
-  // launch shapes by (module, max_in, max_slots, dense words, dense tables)
-  std::map<std::tuple<void*, int, int, int, bool>, std::pair<size_t, int>> shapes;
+  // launch shapes by (module, max_in, max_slots, dense words, dense form)
+  std::map<std::tuple<void*, int, int, int, int>, std::pair<size_t, int>> shapes;
   // background compilation of programs that arrive without a compiled module
   bool background_compile = true;
   std::thread compiler;
@@ -179,7 +179,7 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     n_blocks += reqs[i].ptrs.size();
     if (i == 0 || target(reqs[i]) != target(reqs[i - 1])) ++n_launches;
   }
-  const bool dense_tbl = xorec::dense_table();
+  const int dense_form = xorec::dense_form();
   const size_t desc_off = align_up(n_launches * sizeof(xk::u64), 64);
   const size_t block_off = desc_off + reqs.size() * sizeof(xk::StripeDesc);
   const size_t bytes = block_off + n_blocks * sizeof(xk::u64);
@@ -230,13 +230,13 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
   for (size_t li = 0; li < launches.size(); ++li) {
     const L& l = launches[li];
     const int dense_w = l.T / (4 * xorec::kDenseThreads);
-    auto key = std::make_tuple(l.mod, l.max_in, l.max_slots, dense_w, dense_tbl);
+    auto key = std::make_tuple(l.mod, l.max_in, l.max_slots, dense_w, dense_form);
     auto it = sv->shapes.find(key);
     if (it == sv->shapes.end()) {
       size_t smem = 0;
       int per_sm = 1;
       if (!xorec::batch_launch_shape(l.mod, false, l.max_in, l.max_slots, l.threads,
-                                     sv->di.smem_optin, &smem, &per_sm, dense_w, dense_tbl))
+                                     sv->di.smem_optin, &smem, &per_sm, dense_w, dense_form))
         return fail(EC_ENOTSUP, "a program needs more shared memory than one CTA can hold");
       it = sv->shapes.emplace(key, std::make_pair(smem, per_sm)).first;
     }
@@ -255,7 +255,7 @@ ec_status dispatch(ec_server* sv, Slot& sl, std::vector<Req>& reqs, bool* enqueu
     const long long full = static_cast<long long>(sv->di.sms) * it->second.second;
     const int grid = static_cast<int>(std::max<long long>(1, std::min<long long>(full, l.items)));
     const bool ok = xorec::batch_launch(l.mod, false, bp, l.threads, grid, it->second.first,
-                                        sl.st, dense_w, dense_tbl);
+                                        sl.st, dense_w, dense_form);
     if (!ok) return EC_ECUDA;
   }
   if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) {
