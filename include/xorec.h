@@ -365,13 +365,16 @@ typedef struct {
 
 /* Build the programs the jobs need (decode programs in parallel host
  * threads), compile those without a compiled form into multi-program
- * modules owned by their plan (executor EC_EXEC_AUTO / EC_EXEC_COMPILED),
+ * modules owned by their plan (executor EC_EXEC_AUTO / EC_EXEC_COMPILED;
+ * with EC_EXEC_DENSE or EC_EXEC_INTERP every program runs on that tier),
  * and upload the stripe descriptors and work-item list (device memory owned
  * by the batch).  Block pointers are captured; the buffers must stay valid
  * while the batch runs. */
 ec_status ec_batch_create(const ec_job *jobs, int n_jobs, int executor, ec_batch **out);
 /* Enqueue the batch on `stream`: one persistent launch per module plus at
- * most one interpreter launch.  Allocates nothing (capturable).  Large
+ * most one launch for the programs without a module (the dense bitmatrix
+ * executor; the interpreter in batches created with EC_EXEC_INTERP).
+ * Allocates nothing (capturable).  Large
  * launches split their work items into one contiguous range per SM; the
  * CTAs of an SM start on its range and then help with the others, so each
  * SM runs few distinct programs at a time. */
@@ -407,8 +410,8 @@ typedef struct {
                             (0 = 1000 us; < 0 = sleep at once).  Polling costs
                             one host core and spares each request the wake-up */
   int no_background_compile; /* nonzero: a request whose program has no compiled
-                            kernel always runs on the interpreter.  Default:
-                            it runs on the interpreter while a background
+                            kernel always runs on the dense bitmatrix
+                            executor.  Default: it runs there while a background
                             thread compiles the program, and later requests
                             use the compiled kernel.  Plans used with a server
                             must then stay alive until ec_server_destroy
