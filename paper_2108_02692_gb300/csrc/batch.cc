@@ -264,14 +264,17 @@ static bool module_fits(const Program* prog, int threads, size_t smem_optin) {
 // shape into multi-program modules (per plan and input width, NVRTC, in
 // parallel host threads).  Modules belong to their plan.  Each group is cut
 // into as few modules as keep every module within EC_BATCH_MODULE_SIZE
-// programs (default 128) and about 128 K memory operations of straight-line
-// code, programs spread evenly over them: a batch then runs few long
+// programs (default 256) and EC_BATCH_MODULE_MEM memory operations of
+// straight-line code (default 256 K), programs spread evenly over them: a batch then runs few long
 // launches (every launch starts each SM on a program whose code is not yet
-// in its instruction cache), at the price of fewer, longer compiles.
+// in its instruction cache), at the price of fewer, longer compiles
+// (RS(10,4) decode over 231 erasure sets: two modules of at most 128
+// programs, 0.936 of the measured copy bandwidth, batch built in 12.5 s; one
+// module, 0.954, 26.5 s).
 ec_status compile_modules(const std::vector<std::pair<ec_plan*, Program*>>& want, bool must,
                           int* built) {
-  const long module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 128));
-  const long module_mem = 131072;
+  const long module_size = std::max(1, env_int("EC_BATCH_MODULE_SIZE", 256));
+  const long module_mem = std::max(1024, env_int("EC_BATCH_MODULE_MEM", 262144));
   DeviceInfo di;
   if (!device_info(&di)) return EC_ECUDA;
   // modules per plan, input width and pipeline (windowed or not)
