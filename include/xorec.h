@@ -219,6 +219,17 @@ ec_status ec_plan_module_source(ec_plan *plan, const int *sets, const int *count
 ec_status ec_plan_program(ec_plan *plan, const int *erasures, int n_erasures, uint16_t *buf,
                           size_t len, size_t *need);
 
+/* Copy the dense bitmatrix executor's control words of the encoder's
+ * program (erasures == NULL) or of a decoder's into buf (len 32-bit words);
+ * *need receives their number, 2 * G * n_in with G = ceil(n_out / 32) groups
+ * of output strips.  They encode the program's bitmatrix (Sec. 1, property
+ * (ii): output strip r reads input strip c where bit (r, c) is set) twice:
+ * first G * n_in column masks (word g * n_in + c, bit i: bit (32 g + i, c)),
+ * then G * n_in row words (word g * n_in + 8 w + j, bit 8 q + i: bit
+ * (32 g + 4 j + q, 8 w + i)).  For inspection and host-side checks. */
+ec_status ec_plan_dense_words(ec_plan *plan, const int *erasures, int n_erasures, uint32_t *buf,
+                              size_t len, size_t *need);
+
 /* Encode one stripe: parity_i = sum_j P[i][j] data_j (Sec. 1).
  * data[k], parity[m]: device pointers to blocks of block_bytes bytes
  * (block_bytes % 128 == 0, 16-byte aligned).  Enqueued on `stream`

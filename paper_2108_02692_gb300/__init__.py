@@ -145,6 +145,19 @@ def ec_plan_program(plan: int, erasures=None) -> np.ndarray:
     return out
 
 
+def ec_plan_dense_words(plan: int, erasures=None) -> np.ndarray:
+    """The dense executor's control words: column masks, then row words."""
+    need = ctypes.c_size_t()
+    er = _int_array(erasures) if erasures is not None else None
+    ne = len(erasures) if erasures is not None else 0
+    _check(lib().ec_plan_dense_words(plan, er, ne, None, 0, ctypes.byref(need)))
+    out = np.zeros(need.value, np.uint32)
+    _check(lib().ec_plan_dense_words(plan, er, ne,
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                     need.value, None))
+    return out
+
+
 def ec_plan_kernel_source(plan: int, erasures=None) -> str:
     """CUDA source of the compiled tier's kernel for the encoder or a decoder."""
     need = ctypes.c_size_t()

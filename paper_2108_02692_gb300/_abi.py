@@ -98,6 +98,8 @@ SIGNATURES = {
                                       ctypes.POINTER(c_size)]),
     "ec_plan_program": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ctypes.c_uint16), c_size,
                                 ctypes.POINTER(c_size)]),
+    "ec_plan_dense_words": (c_int, [c_vp, intp, c_int, ctypes.POINTER(ctypes.c_uint32), c_size,
+                                    ctypes.POINTER(c_size)]),
     "ec_plan_kernel_source": (c_int, [c_vp, intp, c_int, ctypes.c_char_p, c_size,
                                       ctypes.POINTER(c_size)]),
     "ec_encode": (c_int, [c_vp, vpp, vpp, c_size, c_vp]),

@@ -707,6 +707,28 @@ ec_status ec_plan_program(ec_plan* plan, const int* erasures, int n_erasures, ui
   return EC_OK;
 }
 
+ec_status ec_plan_dense_words(ec_plan* plan, const int* erasures, int n_erasures, uint32_t* buf,
+                              size_t len, size_t* need) {
+  if (!plan) return fail(EC_EINVAL, "NULL plan");
+  Program* p = plan->enc.get();
+  if (erasures) {
+    std::vector<int> er;
+    ec_status s = canon_erasures(plan, erasures, n_erasures, &er);
+    if (s != EC_OK) return s;
+    s = get_decode_program(plan, er, &p);
+    if (s != EC_OK) return s;
+  }
+  const size_t n = p->masks.size() + p->rowbits.size();
+  if (need) *need = n;
+  if (buf) {
+    const size_t a = std::min(len, p->masks.size());
+    std::memcpy(buf, p->masks.data(), a * sizeof(uint32_t));
+    if (len > a)
+      std::memcpy(buf + a, p->rowbits.data(), std::min(len - a, p->rowbits.size()) * sizeof(uint32_t));
+  }
+  return EC_OK;
+}
+
 ec_status ec_plan_kernel_source(ec_plan* plan, const int* erasures, int n_erasures, char* buf,
                                 size_t len, size_t* need) {
   if (!plan) return fail(EC_EINVAL, "NULL plan");
