@@ -1,5 +1,6 @@
-// GPU executors compiled into the library: the SLP interpreter and the
-// synthetic input generator.
+// GPU executors compiled into the library: the SLP interpreter, the dense
+// bitmatrix executor (programs without a compiled kernel) and the synthetic
+// input generator.
 //
 // The interpreter runs the instruction stream of a scheduled, fused SLP
 // (Sec. 4-6 of the paper; the stream format is described in plan.h) over
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(256, 1) interp_batch_kernel(BatchParams p) {
 //     of strips 0-3 and of strips 4-7 of its column into two tables in
 //     shared memory (15 XORs each, in Gray-code order so one entry is live at
 //     a time); a row then takes two table entries, chosen by its 8 bits of
-//     the window.  A quarter of the table reads per row and strip, and about
-//     a third of the integer work of the masks.
+//     the window: per row and strip, a quarter of a table read and about a
+//     third of the masks' integer work.
 // Control words follow the program's chunk stream in its device buffer:
 // n_groups * n_in masks (group g's mask of input strip c is word g*n_in + c,
 // bit r for output strip 32 g + r), then as many row words (group g, window
@@ -233,9 +234,10 @@ __global__ void __launch_bounds__(256, 1) interp_batch_kernel(BatchParams p) {
 using xorec::kDenseThreads;
 using xorec::kDenseWin;
 
-// Forms (a third, tables for 24 rows of a group and masks for 8, so that
-// the masks' integer work would run beside the tables' shared-memory
-// traffic, measured 0.417 against 0.521 for tables alone and was dropped).
+// Forms.  A third form, tables for 24 rows of a group and masks for 8 (the
+// masks' integer work beside the tables' shared-memory traffic), ran RS(10,4)
+// encode at 0.417 of the copy bandwidth against 0.521 for tables alone and
+// was dropped.
 enum { kMaskForm = 0, kTableForm = 1 };
 
 template <int W>
