@@ -242,3 +242,46 @@ def test_server_runs_windowed_modules():
         xo.ec_server_destroy(sv)
         xo.ec_plan_destroy(plan)
     assert xo.ec_device_status() == 0
+
+
+def _wide_decode_batch(k, sets, B, n_stripes, seed):
+    m = 4
+    plan = xo.ec_plan_create(k, m)
+    P = oracle.cauchy(k, m)
+    jobs, outs, want, keep = [], [], [], []
+    for s in range(n_stripes):
+        data = [synth.block_bytes(seed, s, j, B) for j in range(k)]
+        blocks = data + oracle.encode(P, data)
+        d = [torch.from_numpy(x).cuda() for x in blocks]
+        keep += d
+        er = sets[s % len(sets)]
+        o = [torch.full((B,), 0x4B, dtype=torch.uint8, device="cuda") for _ in er]
+        jobs.append({"plan": plan, "op": xo.EC_OP_DECODE, "erasures": er,
+                     "blocks": [None if i in er else d[i].data_ptr() for i in range(k + m)],
+                     "out": [t.data_ptr() for t in o], "block_bytes": B})
+        outs += o
+        want += [blocks[e] for e in er]
+    return plan, jobs, outs, want, keep
+
+
+@pytest.mark.parametrize("k", [100, 128])
+def test_wide_decoders_of_one_module(k):
+    """RS(100,4) and RS(128,4) decoders of 1, 3 and 4 erasures (8 to 32
+    output strips, about 1.9 K to 11.5 K XORs) in one windowed module, with
+    a ragged tile; bit-exact."""
+    torch.cuda.set_device(0)
+    sets = [[0, 7, 50, k + 1], [5], [3, k - 1, k + 2], [k, k + 1, k + 2, k + 3]]
+    plan, jobs, outs, want, keep = _wide_decode_batch(k, sets, 8 * 1040, 8, 121 + k)
+    try:
+        b = xo.ec_batch_create(jobs, xo.EC_EXEC_COMPILED)
+        try:
+            assert xo.ec_batch_info_get(b)["programs"] == len(sets)
+            xo.ec_batch_run(b, stream())
+            torch.cuda.synchronize()
+            for t, w in zip(outs, want):
+                assert np.array_equal(t.cpu().numpy(), w)
+        finally:
+            xo.ec_batch_destroy(b)
+    finally:
+        xo.ec_plan_destroy(plan)
+    assert xo.ec_device_status() == 0
