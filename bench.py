@@ -81,6 +81,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-decode", action="store_true")
+    ap.add_argument("--no-dense", action="store_true",
+                    help="skip the dense executor's encode (the tier without a compiled kernel)")
     ap.add_argument("--decode-stripes", type=int, default=N_STRIPES,
                     help="stripes of the decode measurement")
     ap.add_argument("--decode-patterns", type=int, default=0,
@@ -400,6 +402,9 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e and n == N_STRIPES:
         e2e = run_e2e(args, xo, plan, data, par, stream, torch)
+    dense = None
+    if not args.no_dense and n == N_STRIPES and kind == "compiled":
+        dense = run_dense(args, xo, data, par, stream, torch, peak)
     decode = None
     if not args.no_decode and (n == N_STRIPES or args.decode_patterns > 0 or args.decode_erasures
                                or args.decode_stripes != N_STRIPES):
@@ -441,6 +446,7 @@ def run_ours(args):
                      "traffic": traffic_from_profiles(kind)},
         "e2e": e2e,
         "decode": decode,
+        "dense": dense,
         "batched": batched,
         "served": served,
         "gpu_launches": K,
@@ -1094,6 +1100,47 @@ def batched_parity(mix, where, arena, n, samples=24, L=64):
             got = blk[k:]
         ok &= all(np.array_equal(a, b) for a, b in zip(got, ref))
     return "bit-exact on sampled windows" if ok else "MISMATCH"
+
+
+def run_dense(args, xo, data, par, stream, torch, peak):
+    """The same encode on the dense bitmatrix executor (the tier that runs
+    programs without a compiled kernel): one launch over the 256 stripes,
+    timed with CUDA events on the launching stream; its parity is compared
+    byte for byte with the compiled kernel's, which the headline checks
+    against the oracle."""
+    k, m, B, n = K_DATA, M_PAR, BLOCK, N_STRIPES
+    plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, args.matrix),
+                                executor=xo.EC_EXEC_DENSE)
+    try:
+        out = torch.empty_like(par)
+        sp = stream.cuda_stream
+
+        def launch():
+            xo.ec_encode_strided(plan, data.data_ptr(), k * B, B, out.data_ptr(), m * B, B, n, B, sp)
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                launch()
+            torch.cuda.synchronize()
+            reps = 5
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(reps):
+                launch()
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        same = bool(torch.equal(out, par))
+        del out
+        return {"value": round(n * k * B / (ms / 1e3) / 1e9, 1), "unit": "GB/s",
+                "frac": round(n * (k + m) * B / (ms / 1e3) / 1e9 / peak, 4),
+                "ms_per_launch": round(ms, 4), "launches": reps,
+                "kernel": "dense_kernel (%s form)" % os.environ.get("EC_DENSE_KIND", "table"),
+                "parity": "identical to the compiled kernel's parity, all 256 stripes" if same
+                          else "MISMATCH"}
+    finally:
+        xo.ec_plan_destroy(plan)
 
 
 def run_e2e(args, xo, plan, data, par, stream, torch):
