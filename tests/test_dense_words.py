@@ -43,8 +43,19 @@ def _decode_words(words, n_in, n_out):
     (12, 8, [0, 3, 5, 9, 12, 19]),
 ])
 def test_dense_words_are_the_bitmatrix(k, m, erasures):
-    P = oracle.cauchy(k, m)
-    plan = xo.ec_plan_create(k, m)
+    _check(k, m, erasures, oracle.cauchy(k, m), None)
+
+
+@pytest.mark.parametrize("erasures", [None, [2, 4, 5, 6]])
+def test_dense_words_of_the_papers_matrix(erasures):
+    """The paper's RS(10,4) matrix [2^(r j)] (Sec. 7.5: P_enc, and P_dec with
+    blocks 2, 4, 5 and 6 erased)."""
+    _check(10, 4, erasures, oracle.power(10, 4), xo.EC_MATRIX_POWER)
+
+
+def _check(k, m, erasures, P, kind):
+    plan = xo.ec_plan_create(k, m) if kind is None else \
+        xo.ec_plan_create_ex(k, m, matrix_kind=kind)
     try:
         words = xo.ec_plan_dense_words(plan, erasures)
     finally:
