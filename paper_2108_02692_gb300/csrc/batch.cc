@@ -10,8 +10,8 @@
 // launches: one persistent launch per module plus one launch of the dense
 // bitmatrix executor (the interpreter in batches created with
 // EC_EXEC_INTERP) for programs without a module; it allocates nothing and
-// can be captured in a CUDA graph.  Items are ordered stripe by stripe, largest stripes first
-// inside each launch, and CTAs take them round robin.
+// can be captured in a CUDA graph.  Items are ordered stripe by stripe,
+// largest stripes first inside each launch, and CTAs take them round robin.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -265,9 +265,10 @@ static bool module_fits(const Program* prog, int threads, size_t smem_optin) {
 // parallel host threads).  Modules belong to their plan.  Each group is cut
 // into as few modules as keep every module within EC_BATCH_MODULE_SIZE
 // programs (default 256) and EC_BATCH_MODULE_MEM memory operations of
-// straight-line code (default 256 K), programs spread evenly over them: a batch then runs few long
-// launches (every launch starts each SM on a program whose code is not yet
-// in its instruction cache), at the price of fewer, longer compiles
+// straight-line code (default 256 K), programs spread evenly over them: a
+// batch then runs few long launches (every launch starts each SM on a
+// program whose code is not yet in its instruction cache), at the price of
+// fewer, longer compiles
 // (RS(10,4) decode over 231 erasure sets: two modules of at most 128
 // programs, 0.936 of the measured copy bandwidth, batch built in 12.5 s; one
 // module, 0.954, 26.5 s).
