@@ -501,9 +501,14 @@ def run_decode(args, xo, torch, stream, peak):
                              0, sp)
     stream.synchronize()
     plan = xo.ec_plan_create_ex(k, m, matrix_kind=matrix_kind(xo, args.matrix))
+    tune = None
     if args.decode_launch:
         th, rb = (int(x) for x in args.decode_launch.split(","))
         xo.ec_plan_set_launch(plan, th, rb)
+    elif not args.no_tune:
+        # the plan's launch shape from the autotuner (timed on the encoder);
+        # the decoders and their batch modules are built with it
+        tune = xo.ec_plan_autotune(plan, B, 32, sp)
     jobs, calls = [], []
     for s, er in enumerate(pats):
         ids = [i for i in range(k + m) if i not in er][:k]
@@ -591,6 +596,7 @@ def run_decode(args, xo, torch, stream, peak):
         "batched_over_plain": round(ms_plain / ms_batch, 2),
         "distinct_patterns": len(set(pats)),
         "launches_per_step": binfo["launches"],
+        "autotune": tune,
         "prepare_s": round(prep_s, 2), "plain_compile_s": round(compile_s, 2),
         "parity": (f"bit-exact on sampled windows of 6 stripes and on all of stripes {whole} "
                    "(one per erasure count)") if ok else "MISMATCH",
